@@ -1,0 +1,248 @@
+"""CPU oracle for the Whirlwind MCF unwrapper hot path.
+
+TEST INFRASTRUCTURE ONLY.  A plain, slow, single-threaded C++ restatement of
+the paper's definitions (Sec. II: Eq. 1 residues, Eqs. 4-7 costs, Eq. 2 MCF by
+successive shortest paths, integer integration).  Only the tests, the smoke
+check and the benchmark's CPU-baseline leg use it; the product path never does.
+It shares no code with the CUDA library.
+
+Pinned functions and their pins (see tests/test_oracle_*.py):
+  residues        vortex, noise-free Itoh field, charge balance, brute recount
+  phase (CORDIC)  numpy arctan2 within 2 ulp, exact axis cases
+  costs/indices   hand-evaluated index formula, probe tables, masks, steep rule
+  MCF             exhaustive enumeration (<= 5x5), certificate, max-flow
+  integration     rewrap identity, Itoh integration on sub-Nyquist fields
+  Lee pdf         mpmath hypergeometric closed form, single-look closed form,
+                  normalisation, Monte Carlo looks
+  Touzi pdf       mpmath hypergeometric, gamma=0 closed form, normalisation,
+                  Monte Carlo looks
+  sigma_alpha     pi/sqrt(3) for a uniform pdf (the limit stated in Sec. II-B)
+  P0/P+/costs     P0+P+ +P- = 1, costs >= 0, the orderings stated in Sec. II-B
+Parity unpinned: the absolute LUT values (the paper prints no table), and
+sigma_alpha's formula away from gamma -> 0 (the paper gives only the limit).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SOURCES = ["wwo_grid.cpp", "wwo_mcf.cpp", "wwo_lut.cpp"]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with plain g++ (-O2, no FP contraction)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "wwo.h")])
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp] + srcs
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        i32 = ctypes.c_int32
+        d = ctypes.c_double
+        f = ctypes.c_float
+        L.wwo_phase_from_complex.argtypes = [P, i64, P]
+        L.wwo_prepare.argtypes = [P, P, P, P, i64, i64, P, P, P]
+        L.wwo_residues.argtypes = [P, i64, i64, P, P]
+        L.wwo_alpha_hat.argtypes = [P, P, i64, i64, i32, P]
+        L.wwo_costs.argtypes = [P, P, P, i64, i64, P, i32, f, i32, P]
+        L.wwo_costs.restype = i64
+        L.wwo_integrate.argtypes = [P, P, P, i64, i64, P, P]
+        L.wwo_solve_mcf.argtypes = [P, i32, P, i64, i64, P, P, P]
+        L.wwo_solve_mcf.restype = ctypes.c_int
+        L.wwo_check_certificate.argtypes = [P, i32, P, i64, i64, P, P, P, P]
+        L.wwo_check_certificate.restype = ctypes.c_int
+        L.wwo_flow_cost.argtypes = [P, i64, i64, P]
+        L.wwo_flow_cost.restype = i64
+        L.wwo_brute_force.argtypes = [P, P, i64, i64]
+        L.wwo_brute_force.restype = i64
+        L.wwo_feasible.argtypes = [P, i32, i64, i64]
+        L.wwo_feasible.restype = ctypes.c_int
+        L.wwo_lee_pdf.argtypes = [d, d, d]
+        L.wwo_lee_pdf.restype = d
+        L.wwo_touzi_pdf.argtypes = [d, d, d]
+        L.wwo_touzi_pdf.restype = d
+        L.wwo_marginal_pdf.argtypes = [d, d, i32, i32, P]
+        L.wwo_marginal_pdf.restype = ctypes.c_int
+        L.wwo_sigma_from_pdf.argtypes = [P, i32]
+        L.wwo_sigma_from_pdf.restype = d
+        L.wwo_probabilities.argtypes = [P, i32, d, P, P, P, P]
+        L.wwo_lut_build.argtypes = [d, i32, i32, P, P]
+        L.wwo_lut_build.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def phase_from_complex(ifg: np.ndarray) -> np.ndarray:
+    z = np.ascontiguousarray(ifg, dtype=np.complex64)
+    out = np.empty(z.shape, np.float32)
+    lib().wwo_phase_from_complex(_p(z), z.size, _p(out))
+    return out
+
+
+def prepare(coh, mask, phase=None, ifg=None):
+    """-> (psi, coh, valid) with masked/non-finite pixels zeroed (psi=0, coh=0)."""
+    coh = np.ascontiguousarray(coh, np.float32)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    m, n = coh.shape
+    psi = np.empty((m, n), np.float32)
+    co = np.empty((m, n), np.float32)
+    valid = np.empty((m, n), np.uint8)
+    if ifg is not None:
+        z = np.ascontiguousarray(ifg, np.complex64)
+        lib().wwo_prepare(None, _p(z), _p(coh), _p(mask), m, n, _p(psi), _p(co), _p(valid))
+    else:
+        ph = np.ascontiguousarray(phase, np.float32)
+        lib().wwo_prepare(_p(ph), None, _p(coh), _p(mask), m, n, _p(psi), _p(co), _p(valid))
+    return psi, co, valid
+
+
+def residues(psi: np.ndarray):
+    psi = np.ascontiguousarray(psi, np.float32)
+    m, n = psi.shape
+    r = np.empty((m - 1, n - 1), np.int8)
+    g = np.zeros(1, np.int32)
+    lib().wwo_residues(_p(psi), m, n, _p(r), _p(g))
+    return r, int(g[0])
+
+
+def alpha_hat(psi, valid, half_width=2):
+    psi = np.ascontiguousarray(psi, np.float32)
+    valid = np.ascontiguousarray(valid, np.uint8)
+    m, n = psi.shape
+    out = np.empty((2, m, n), np.float32)
+    lib().wwo_alpha_hat(_p(psi), _p(valid), m, n, half_width, _p(out))
+    return out
+
+
+def costs(psi, coh, valid, table, half_width=2, steep_rad=1.0, steep_cap_ppm=30000):
+    psi = np.ascontiguousarray(psi, np.float32)
+    coh = np.ascontiguousarray(coh, np.float32)
+    valid = np.ascontiguousarray(valid, np.uint8)
+    table = np.ascontiguousarray(table, np.int16)
+    assert table.size == 128 * 256
+    m, n = psi.shape
+    out = np.empty((4, m, n), np.int16)
+    nsteep = lib().wwo_costs(_p(psi), _p(coh), _p(valid), m, n, _p(table), half_width,
+                             float(steep_rad), int(steep_cap_ppm), _p(out))
+    return out, int(nsteep)
+
+
+def integrate(psi, valid, flows):
+    psi = np.ascontiguousarray(psi, np.float32)
+    valid = np.ascontiguousarray(valid, np.uint8)
+    flows = np.ascontiguousarray(flows, np.int8)
+    m, n = psi.shape
+    unw = np.empty((m, n), np.float32)
+    cyc = np.empty((m, n), np.int32)
+    lib().wwo_integrate(_p(psi), _p(valid), _p(flows), m, n, _p(unw), _p(cyc))
+    return unw, cyc
+
+
+def solve_mcf(res, ground, costs_planes):
+    res = np.ascontiguousarray(res, np.int8)
+    c = np.ascontiguousarray(costs_planes, np.int16)
+    _, m, n = c.shape
+    flows = np.zeros((2, m, n), np.int8)
+    pot = np.zeros((m - 1) * (n - 1) + 1, np.int64)
+    tc = np.zeros(1, np.int64)
+    st = lib().wwo_solve_mcf(_p(res), int(ground), _p(c), m, n, _p(flows), _p(pot), _p(tc))
+    return st, flows, pot, int(tc[0])
+
+
+def check_certificate(res, ground, costs_planes, flows, potentials):
+    """-> (code, total_cost, bad_index); code 0 = optimal flow with valid potentials."""
+    res = np.ascontiguousarray(res, np.int8)
+    c = np.ascontiguousarray(costs_planes, np.int16)
+    fl = np.ascontiguousarray(flows, np.int8)
+    pot = np.ascontiguousarray(potentials, np.int64)
+    _, m, n = c.shape
+    tc = np.zeros(1, np.int64)
+    bad = np.zeros(1, np.int64)
+    code = lib().wwo_check_certificate(_p(res), int(ground), _p(c), m, n, _p(fl), _p(pot), _p(tc), _p(bad))
+    return code, int(tc[0]), int(bad[0])
+
+
+def flow_cost(costs_planes, flows):
+    c = np.ascontiguousarray(costs_planes, np.int16)
+    fl = np.ascontiguousarray(flows, np.int8)
+    _, m, n = c.shape
+    return int(lib().wwo_flow_cost(_p(c), m, n, _p(fl)))
+
+
+def brute_force(psi, costs_planes):
+    psi = np.ascontiguousarray(psi, np.float32)
+    c = np.ascontiguousarray(costs_planes, np.int16)
+    m, n = psi.shape
+    assert m * n <= 30
+    return int(lib().wwo_brute_force(_p(psi), _p(c), m, n))
+
+
+def feasible(res, ground):
+    res = np.ascontiguousarray(res, np.int8)
+    m, n = res.shape[0] + 1, res.shape[1] + 1
+    return bool(lib().wwo_feasible(_p(res), int(ground), m, n))
+
+
+def lee_pdf(eta, gamma, L):
+    return float(lib().wwo_lee_pdf(float(eta), float(gamma), float(L)))
+
+
+def touzi_pdf(gh, gamma, L):
+    return float(lib().wwo_touzi_pdf(float(gh), float(gamma), float(L)))
+
+
+def marginal_pdf(L, gh, nh=512, lambda_panels=8):
+    f = np.empty(2 * nh + 1, np.float64)
+    st = lib().wwo_marginal_pdf(float(L), float(gh), nh, lambda_panels, _p(f))
+    assert st == 0
+    return f
+
+
+def sigma_from_pdf(f):
+    f = np.ascontiguousarray(f, np.float64)
+    nh = (f.size - 1) // 2
+    return float(lib().wwo_sigma_from_pdf(_p(f), nh))
+
+
+def probabilities(f, alpha_hat_value):
+    f = np.ascontiguousarray(f, np.float64)
+    nh = (f.size - 1) // 2
+    out = np.zeros(4, np.float64)
+    o = [out[i:i + 1] for i in range(4)]
+    lib().wwo_probabilities(_p(f), nh, float(alpha_hat_value), _p(o[0]), _p(o[1]), _p(o[2]), _p(o[3]))
+    return dict(p0=out[0], pplus=out[1], pminus=out[2], sigma=out[3])
+
+
+def lut_build(L, nh=8192, lambda_panels=8):
+    """-> (cost100 float64 [128,256], table int16 [128,256]); slow (tens of seconds at the default)."""
+    c = np.empty((128, 256), np.float64)
+    t = np.empty((128, 256), np.int16)
+    st = lib().wwo_lut_build(float(L), nh, lambda_panels, _p(c), _p(t))
+    assert st == 0
+    return c, t

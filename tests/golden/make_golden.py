@@ -1,0 +1,54 @@
+"""Write the oracle's FP64 cost tables used by the LUT and cost parity tests.
+
+Calls only the CPU oracle (oracle/).  For each number of looks L it stores
+100*c (Eq. 4, before flooring) and the floored int16 table on the 128 (coherence)
+x 256 (slope) bin-centre grid, built with a 4096-interval half grid in phase and
+two Gauss-Legendre panels per unit of -log(1-gamma).  Run:
+
+    python tests/golden/make_golden.py            # all L
+    python tests/golden/make_golden.py 9 50       # selected L
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+from multiprocessing import get_context
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+LOOKS = [4.0, 6.0, 9.0, 16.0, 50.0]
+NH = 4096
+LAMBDA_PANELS = 2
+
+
+def path_for(L: float) -> str:
+    return os.path.join(HERE, f"lut_oracle_L{L:g}.npz")
+
+
+def _one(L: float):
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    t = time.time()
+    cost100, table = oracle.lut_build(L, nh=NH, lambda_panels=LAMBDA_PANELS)
+    np.savez_compressed(path_for(L), cost100=cost100, table=table, nlooks=L, nh=NH,
+                        lambda_panels=LAMBDA_PANELS)
+    return L, time.time() - t
+
+
+def main(argv):
+    looks = [float(a) for a in argv] or LOOKS
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    oracle.build()
+    with get_context("spawn").Pool(len(looks)) as pool:
+        for L, dt in pool.imap_unordered(_one, looks):
+            print(f"L={L:g}: {dt:.0f} s -> {path_for(L)}", flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

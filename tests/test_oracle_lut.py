@@ -1,0 +1,162 @@
+"""Pins for the oracle's FP64 cost model (Sec. II-B, Eqs. 4-7)."""
+import os
+
+import mpmath
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2609_36267_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def lee_closed_form(eta, g, L):
+    """Lee et al. 1994 L-look phase pdf (the hypergeometric form), evaluated with
+    enough digits that the two terms' cancellation is resolved."""
+    prev = None
+    for dps in (40, 120, 300, 600):
+        mpmath.mp.dps = dps
+        e, gg = mpmath.mpf(eta), mpmath.mpf(g)
+        b = gg * mpmath.cos(e)
+        t1 = mpmath.gamma(L + 0.5) * (1 - gg ** 2) ** L * b / (
+            2 * mpmath.sqrt(mpmath.pi) * mpmath.gamma(L) * (1 - b ** 2) ** (L + 0.5))
+        t2 = (1 - gg ** 2) ** L / (2 * mpmath.pi) * mpmath.hyp2f1(L, 1, 0.5, b ** 2)
+        v = t1 + t2
+        if prev is not None and v != 0 and abs(v / prev - 1) < mpmath.mpf(10) ** -20:
+            return float(v)
+        prev = v
+    return float(prev)
+
+
+def touzi_closed_form(gh, g, L):
+    mpmath.mp.dps = 60
+    gh, g = mpmath.mpf(gh), mpmath.mpf(g)
+    return float(2 * (L - 1) * (1 - g ** 2) ** L * gh * (1 - gh ** 2) ** (L - 2)
+                 * mpmath.hyp2f1(L, L, 1, g ** 2 * gh ** 2))
+
+
+@pytest.mark.parametrize("eta,g,L", [
+    (0.3, 0.5, 4), (2.0, 0.8, 9), (0.0, 0.95, 50), (3.0, 0.6, 6.5), (1.0, 0.99, 16),
+    (0.1, 0.999, 2.5), (3.1, 0.999, 50), (1.5, 0.3, 1.5), (2.7, 0.9, 6), (0.5, 0.0, 9)])
+def test_lee_pdf_matches_hypergeometric_form(eta, g, L):
+    a = oracle.lee_pdf(eta, g, L)
+    b = lee_closed_form(eta, g, L)
+    assert a == pytest.approx(b, rel=1e-11)
+
+
+@pytest.mark.parametrize("g", [0.0, 0.2, 0.7, 0.95, 0.999])
+def test_lee_single_look_closed_form(g):
+    for eta in np.linspace(-3.1, 3.1, 23):
+        b = g * np.cos(eta)
+        ref = (1 - g * g) / (2 * np.pi * (1 - b * b)) * (1 + b * np.arccos(-b) / np.sqrt(1 - b * b))
+        assert oracle.lee_pdf(eta, g, 1.0) == pytest.approx(ref, rel=1e-11)
+
+
+@pytest.mark.parametrize("g,L", [(0.0, 3), (0.5, 4), (0.9, 9), (0.97, 50), (0.3, 1.7)])
+def test_lee_pdf_normalised(g, L):
+    v, err = integrate.quad(lambda e: oracle.lee_pdf(e, g, L), -np.pi, np.pi, limit=400,
+                            points=[0.0], epsabs=1e-13, epsrel=1e-12)
+    assert v == pytest.approx(1.0, abs=1e-9)
+
+
+@pytest.mark.parametrize("gh,g,L", [(0.3, 0.5, 4), (0.9, 0.8, 9), (0.99, 0.99, 50), (0.5, 0.0, 6.5),
+                                    (0.05, 0.3, 16), (0.95, 0.2, 2.5)])
+def test_touzi_matches_hypergeometric(gh, g, L):
+    assert oracle.touzi_pdf(gh, g, L) == pytest.approx(touzi_closed_form(gh, g, L), rel=1e-11)
+
+
+def test_touzi_zero_coherence_closed_form():
+    for L in (2.0, 4.0, 9.0, 50.0, 3.3):
+        for gh in np.linspace(0.01, 0.99, 17):
+            ref = 2 * (L - 1) * gh * (1 - gh * gh) ** (L - 2)
+            assert oracle.touzi_pdf(gh, 0.0, L) == pytest.approx(ref, rel=1e-13)
+
+
+@pytest.mark.parametrize("g,L", [(0.0, 4), (0.6, 4), (0.9, 9), (0.98, 16), (0.5, 2.5)])
+def test_touzi_normalised(g, L):
+    v, _ = integrate.quad(lambda x: oracle.touzi_pdf(x, g, L), 0, 1, limit=400, epsabs=1e-13)
+    assert v == pytest.approx(1.0, abs=1e-9)
+
+
+@pytest.mark.parametrize("g,L", [(0.6, 4), (0.85, 9), (0.3, 2)])
+def test_densities_against_monte_carlo_looks(g, L):
+    """Phase of sum z1 z2^* and the Eq. (3) sample coherence from simulated looks."""
+    rng = np.random.Generator(np.random.PCG64(123))
+    count = 300000
+    ph, co = synth.brute_force_looks(rng, g, L, count)
+    edges = np.linspace(-np.pi, np.pi, 41)
+    obs, _ = np.histogram(ph, edges)
+    exp = np.array([integrate.quad(lambda e: oracle.lee_pdf(e, g, L), a, b)[0]
+                    for a, b in zip(edges[:-1], edges[1:])]) * count
+    z = (obs - exp) / np.sqrt(np.maximum(exp, 1.0))
+    assert np.all(np.abs(z) < 5.0)
+    edges = np.linspace(0, 1, 41)
+    obs, _ = np.histogram(co, edges)
+    exp = np.array([integrate.quad(lambda x: oracle.touzi_pdf(x, g, L), a, b)[0]
+                    for a, b in zip(edges[:-1], edges[1:])]) * count
+    z = (obs - exp) / np.sqrt(np.maximum(exp, 1.0))
+    assert np.all(np.abs(z) < 5.0)
+
+
+def test_sigma_alpha_limit_uniform_pdf():
+    """Sec. II-B: sigma_alpha -> pi/sqrt(3) as coherence falls to zero (uniform phase)."""
+    nh = 512
+    f = np.full(2 * nh + 1, 1.0 / (2 * np.pi))
+    assert oracle.sigma_from_pdf(f) == pytest.approx(np.pi / np.sqrt(3), rel=1e-8)
+
+
+@pytest.mark.parametrize("L,gh", [(4, 0.1), (9, 0.6), (16, 0.95), (50, 0.5)])
+def test_marginal_pdf_and_probabilities(L, gh):
+    nh = 256
+    f = oracle.marginal_pdf(L, gh, nh=nh, lambda_panels=2)
+    x = np.linspace(-np.pi, np.pi, 2 * nh + 1)
+    assert np.allclose(f, f[::-1], rtol=1e-13)
+    assert integrate.simpson(f, x=x) == pytest.approx(1.0, abs=1e-6)
+    assert np.all(f > 0)
+    # more coherence -> more mass near zero phase
+    for ah in (-2.5, -0.4, 0.0, 1.3, 3.0):
+        p = oracle.probabilities(f, ah)
+        assert p["p0"] + p["pplus"] + p["pminus"] == pytest.approx(1.0, abs=1e-9)
+        assert 0 < p["pplus"] < 1 and 0 < p["p0"] <= 1
+        q = oracle.probabilities(f, -ah)
+        assert q["pplus"] == pytest.approx(p["pminus"], rel=1e-6)  # P-(a) = P+(-a)
+
+
+def test_marginal_pdf_sharpens_with_coherence():
+    lo = oracle.marginal_pdf(9, 0.2, nh=128, lambda_panels=2)
+    hi = oracle.marginal_pdf(9, 0.9, nh=128, lambda_panels=2)
+    assert hi[128] > lo[128] and hi[0] < lo[0]
+
+
+@pytest.mark.parametrize("L", [4, 6, 9, 16, 50])
+def test_golden_table_properties(L):
+    """Sec. II-B orderings: costs >= 0; cheaper +1 correction as alpha-hat grows;
+    near -pi a negative correction is cheaper than a positive one (and the
+    reverse near +pi); a gradient near zero costs more at higher coherence."""
+    path = os.path.join(GOLDEN, f"lut_oracle_L{L:g}.npz")
+    if not os.path.exists(path):
+        pytest.skip("golden table not generated")
+    z = np.load(path)
+    c, t = z["cost100"], z["table"]
+    assert np.all(c >= 0) and t.min() >= 0
+    assert np.all(np.diff(c, axis=1) <= 1e-9)
+    assert np.all(c[:, :128] >= c[:, 255:127:-1] - 1e-9)
+    mid = c[:, 127:129].mean(axis=1)
+    assert np.all(np.diff(mid) >= -1e-9)
+    fl = np.minimum(np.floor(c), 32767).astype(np.int16)
+    assert np.array_equal(fl, t)
+
+
+def test_oracle_table_grid_convergence():
+    """The tabulation error shrinks ~h^4: one row at nh=256/512/1024 (100*c units)."""
+    ah = -np.pi + (np.arange(0, 256, 8) + 0.5) * 2 * np.pi / 256
+    rows = []
+    for nh in (256, 512, 1024):
+        f = oracle.marginal_pdf(9, 0.8, nh=nh, lambda_panels=2)
+        rows.append(np.array([-100 * np.log(p["pplus"] / p["p0"]) for p in
+                              (oracle.probabilities(f, a) for a in ah)]))
+    e1 = np.max(np.abs(rows[0] - rows[2]))
+    e2 = np.max(np.abs(rows[1] - rows[2]))
+    assert e2 < e1 / 8 and e2 < 0.05
