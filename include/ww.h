@@ -1,0 +1,184 @@
+/* ww.h — C-ABI of the B300 Whirlwind MCF phase-unwrapping library (libww.so).
+ *
+ * The library implements the hot path of the minimum-cost-flow (MCF) 2D phase
+ * unwrapper of Staniewicz et al., "A Probabilistic-Cost Algorithm for
+ * Large-Scale 2D Phase Unwrapping" (arxiv 2609.36267), Sec. II:
+ *   1. residues of the wrapped phase (Sec. II-A, Eq. 1),
+ *   2. integer likelihood-ratio arc costs from a compact lookup table
+ *      (Sec. II-B, Eqs. 4-7),
+ *   3. the MCF solve (Sec. II-A Eq. 2) by successive shortest paths with node
+ *      potentials and one augmentation per shortest-path tree (Sec. II-C),
+ *   4. integration of the flows into integer cycle counts (Sec. II-A, II-C).
+ * Every step runs as CUDA kernels on the caller's stream; no torch types appear
+ * here and the library never falls back to the CPU.
+ *
+ * Array conventions (all row-major, m rows x n columns of pixels, m,n >= 2):
+ *   Pixel edge h(i,j) joins (i,j)->(i,j+1); v(i,j) joins (i,j)->(i+1,j).  Edge
+ *   arrays are m x n planes (the unused last column of h / last row of v is
+ *   written as 0).
+ *   Dual node p=(i,j), 0<=i<m-1, 0<=j<n-1, is the 2x2 loop whose top-left pixel
+ *   is (i,j); node arrays hold (m-1)*(n-1) entries, index i*(n-1)+j.  The ground
+ *   node G (the image's outer ring, Sec. II-A, collapsed into one node) follows
+ *   as index (m-1)*(n-1) where a node array carries it.
+ *   h(i,j) separates node (i-1,j) [above] from (i,j) [below]; v(i,j) separates
+ *   node (i,j-1) [left] from (i,j) [right]; neighbours outside the grid are G.
+ *   Costs: int16 planes [4][m][n]: 0 = arc above->below across h (adds +1 to the
+ *   cycle difference dk_h), 1 = below->above (dk_h -1), 2 = right->left across v
+ *   (dk_v +1), 3 = left->right (dk_v -1).
+ *   Flows: int8 planes [2][m][n] holding dk_h, dk_v in {-1,0,1}.
+ *   Wrap count n_e = [dpsi > PI_F] - [dpsi <= -PI_F] for dpsi = psi_v - psi_u in
+ *   fp32 (PI_F = fp32 nearest pi); the residue of node (i,j) is
+ *   r = -(n_h(i,j) + n_v(i,j+1) - n_h(i+1,j) - n_v(i,j)) and r_G = -sum(r).
+ *   Cycle counts: K(0,0)=0, K_v = K_u + dk_e - n_e; unwrapped
+ *   phi = (float)((double)psi + (double)K * 2pi), NaN at invalid pixels.
+ *
+ * Input validity: a pixel is valid iff mask != 0 (mask may be NULL = all valid)
+ * and its phase (or both complex parts) and coherence are finite.  Invalid
+ * pixels are treated as phase 0, coherence 0; arcs of edges touching them cost
+ * 0 (Sec. II-B).  A complex64 input (interleaved re, im) is converted to phase
+ * by the library's own fixed-point CORDIC atan2 (30 iterations, angle unit
+ * 2^-29 rad), identical on every device.
+ *
+ * Pointers: unless stated, array arguments are DEVICE pointers owned by the
+ * caller, and calls are asynchronous on `stream` (0 = legacy default stream).
+ * Host-side argument checks return a status immediately; device-side failures
+ * of the solver are written to its device status word.
+ */
+#ifndef WW_H
+#define WW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ww_status;
+#define WW_OK 0
+#define WW_ERR_INVALID_ARG (-1)   /* bad pointer, size or parameter */
+#define WW_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define WW_ERR_OOM (-3)           /* device or host allocation failed */
+#define WW_ERR_INFEASIBLE (-4)    /* supplies cannot be routed with unit capacities */
+#define WW_ERR_TIMEOUT (-5)       /* a bounded device loop hit its limit; state resumable */
+#define WW_ERR_OVERFLOW (-6)      /* a 32-bit distance or reduced cost overflowed */
+#define WW_ERR_NOT_IMPLEMENTED (-7)
+#define WW_ERR_INTERNAL (-8)      /* an invariant check failed (e.g. negative reduced cost) */
+
+typedef void* ww_stream;  /* a cudaStream_t */
+
+/* Human-readable name of a status code (static string). */
+const char* ww_status_string(ww_status s);
+
+/* Parameters.  ww_params_default fills the paper's values (Sec. II-B, II-C). */
+typedef struct ww_params {
+  int32_t box_half_width;   /* slope-estimate window half width; 2 = 5x5 (Sec. II-B) */
+  float steep_rad;          /* unsmoothed |gradient| above which an edge costs 0: 1.0 (Sec. II-B) */
+  int32_t steep_cap_ppm;    /* cap on zeroed steep edges, per million valid edges: 30000 = 3% */
+  int32_t max_passes;       /* solver pass limit -> WW_ERR_TIMEOUT (default 100000) */
+  int32_t max_sweeps;       /* tile-sweep limit per shortest-path search (default 1000000) */
+  int32_t tile_rows;        /* search tile height in nodes (0 = auto) */
+  int32_t radius_policy;    /* 0 = full search each pass (default) */
+  int32_t reserved[9];
+} ww_params;
+void ww_params_default(ww_params* p);
+
+/* ---- Cost lookup table (Sec. II-B, Eqs. 4-7) ----
+ * A table holds floor(100 c) as int16 (saturated at 32767) for c of Eq. 4 on a
+ * 128 (coherence) x 256 (slope) grid of bin centres gamma_k = (k+1/2)/128,
+ * alpha_j = -pi + (j+1/2) 2pi/256, for one number of looks L.  Edge lookup:
+ * j = clamp(floor((a + PI_F) * fp32(256/2pi)), 0, 255),
+ * k = clamp(floor(gamma_e * 128), 0, 127) in fp32 with no fused operations,
+ * gamma_e = min of the endpoint coherences, a = box-filtered slope estimate. */
+typedef struct ww_lut ww_lut;
+
+/* Build the table in FP64 on the host (coherence-marginalised L-look phase
+ * noise, Eq. 5; edge-noise convolution; Eq. 6 tail probabilities; Gaussian
+ * slope marginalisation over +-8 sigma, Eq. 7).  nlooks must be > 1.  Takes a
+ * few seconds of host time; the result is cached per nlooks inside the library
+ * and the returned handle shares it.  *out is owned by the caller (ww_lut_free). */
+ww_status ww_build_lut(double nlooks, ww_lut** out);
+/* Wrap a caller-supplied host table (128*256 int16, row = coherence bin). */
+ww_status ww_lut_from_table(double nlooks, const int16_t* host_table, ww_lut** out);
+/* Copy out the host table (128*256) and, for built tables, 100*c in FP64
+ * before flooring (cost100 may be NULL). */
+ww_status ww_lut_table(const ww_lut* lut, int16_t* host_table, double* cost100);
+void ww_lut_free(ww_lut* lut);
+
+/* ---- Workspace: library-owned device scratch for one request at a time ----
+ * Sized for grids up to max_rows x max_cols; allocated with cudaMalloc on the
+ * current device.  One workspace must not be used by two calls that overlap
+ * on the GPU. */
+typedef struct ww_workspace ww_workspace;
+ww_status ww_workspace_create(int64_t max_rows, int64_t max_cols, ww_workspace** out);
+void ww_workspace_free(ww_workspace* ws);
+/* Bytes of device memory a workspace for m x n takes. */
+int64_t ww_workspace_bytes(int64_t m, int64_t n);
+
+/* ---- Step 1: residues (Sec. II-A, Eq. 1) ----
+ * ifg: float32 phase [m][n] (is_complex=0) or interleaved complex64 [m][n][2]
+ * (is_complex=1).  coh (may be NULL) and mask (may be NULL) only decide
+ * validity here.  residues: int8 [(m-1)(n-1)]; ground: device int32[1], r_G. */
+ww_status ww_residues(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask,
+                      int64_t m, int64_t n, int8_t* residues, int32_t* ground, ww_stream stream);
+
+/* ---- Step 2: arc costs (Sec. II-B) ----
+ * Writes costs [4][m][n] int16 as described above, including the steep-edge
+ * bound (at most steep_cap_ppm of valid edges with |d| > steep_rad get cost 0,
+ * largest |d| first, ties by edge index with h before v).  ws provides scratch
+ * for the steep selection. */
+ww_status ww_costs(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask,
+                   int64_t m, int64_t n, const ww_lut* lut, const ww_params* params,
+                   ww_workspace* ws, int16_t* costs, ww_stream stream);
+
+/* ---- Step 3: MCF solve (Sec. II-A Eq. 2, Sec. II-C) ----
+ * Exact successive-shortest-path solve of Eq. 2 with unit capacities.
+ * Outputs: flows [2][m][n] (dk in {-1,0,1}), potentials int64 [(m-1)(n-1)+1]
+ * (the last entry is G) certifying optimality: every residual arc has reduced
+ * cost c - p(tail) + p(head) >= 0; total_cost: device int64[1] = sum c_a x_a;
+ * dev_status: device int32[1] (WW_OK, WW_ERR_INFEASIBLE, WW_ERR_TIMEOUT,
+ * WW_ERR_OVERFLOW, WW_ERR_INTERNAL).  The host drives the pass loop, so the
+ * call returns when the solve has finished (the stream is synchronised); the
+ * returned status equals *dev_status. */
+ww_status ww_solve_mcf(const int8_t* residues, const int32_t* ground, const int16_t* costs,
+                       int64_t m, int64_t n, const ww_params* params, ww_workspace* ws,
+                       int8_t* flows, int64_t* potentials, int64_t* total_cost,
+                       int32_t* dev_status, ww_stream stream);
+
+/* Solver statistics of the last ww_solve_mcf on this workspace (host struct). */
+typedef struct ww_solve_stats {
+  int64_t passes, augmentations, search_iterations, tile_visits;
+  int64_t residues, ground_net;
+  double ms_search;      /* host wall time in the search loops */
+  double ms_other;       /* host wall time in select/augment/update */
+  double ms_search_gpu;  /* device time of the search kernel launches (CUDA events) */
+} ww_solve_stats;
+ww_status ww_get_solve_stats(const ww_workspace* ws, ww_solve_stats* out);
+
+/* ---- Step 4: integration (Sec. II-A, II-C) ----
+ * unwrapped: float32 [m][n]; cycles: int32 [m][n]. */
+ww_status ww_integrate(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask,
+                       const int8_t* flows, int64_t m, int64_t n, float* unwrapped, int32_t* cycles,
+                       ww_stream stream);
+
+/* ---- Whole path ----
+ * Residues, costs (table for nlooks, cached), MCF, integration.  total_cost is
+ * a HOST int64* (may be NULL).  Synchronises the stream; returns the solver's
+ * status.  Scratch for residues, costs, flows and potentials comes from ws. */
+ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, double nlooks,
+                    const uint8_t* mask, int64_t m, int64_t n, const ww_params* params,
+                    ww_workspace* ws, float* unwrapped, int32_t* cycles, int64_t* total_cost,
+                    ww_stream stream);
+
+/* ---- Harness: optimality certificate on the GPU ----
+ * Counts violations into counts (device int64[4]): [0] |dk|>1 or flow on a
+ * non-existent edge, [1] nodes (G included) whose out-in flow differs from the
+ * supply, [2] residual arcs with negative reduced cost, [3] total cost. */
+ww_status ww_certificate(const int8_t* residues, const int32_t* ground, const int16_t* costs,
+                         const int8_t* flows, const int64_t* potentials, int64_t m, int64_t n,
+                         int64_t* counts, ww_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WW_H */

@@ -1,0 +1,302 @@
+"""B300-native hot path of the Whirlwind MCF phase unwrapper (arxiv 2609.36267).
+
+Thin ctypes binding over libww.so (include/ww.h).  Every step of the path runs
+in the library's CUDA kernels; this module only passes device pointers, sizes
+and the current torch stream.  There is no CPU fallback: if libww.so is missing
+or fails to load, every call raises.
+
+    import torch, paper_2609_36267_b300 as ww
+    ws = ww.Workspace(m, n)
+    unw, K, cost = ww.unwrap(ifg, coh, nlooks, mask, ws=ws)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libww.so")
+
+WW_OK = 0
+WW_ERR_INVALID_ARG = -1
+WW_ERR_CUDA = -2
+WW_ERR_OOM = -3
+WW_ERR_INFEASIBLE = -4
+WW_ERR_TIMEOUT = -5
+WW_ERR_OVERFLOW = -6
+WW_ERR_NOT_IMPLEMENTED = -7
+WW_ERR_INTERNAL = -8
+
+N_GAMMA, N_ALPHA = 128, 256
+
+
+class WWError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("box_half_width", ctypes.c_int32), ("steep_rad", ctypes.c_float),
+                ("steep_cap_ppm", ctypes.c_int32), ("max_passes", ctypes.c_int32),
+                ("max_sweeps", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("radius_policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int64), ("augmentations", ctypes.c_int64),
+                ("search_iterations", ctypes.c_int64), ("tile_visits", ctypes.c_int64),
+                ("residues", ctypes.c_int64), ("ground_net", ctypes.c_int64),
+                ("ms_search", ctypes.c_double), ("ms_other", ctypes.c_double),
+                ("ms_search_gpu", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libww.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libww.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        i64, i32, d = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        L.ww_status_string.argtypes = [i32]
+        L.ww_status_string.restype = ctypes.c_char_p
+        L.ww_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.ww_build_lut.argtypes = [d, ctypes.POINTER(P)]
+        L.ww_lut_from_table.argtypes = [d, P, ctypes.POINTER(P)]
+        L.ww_lut_table.argtypes = [P, P, P]
+        L.ww_lut_free.argtypes = [P]
+        L.ww_workspace_create.argtypes = [i64, i64, ctypes.POINTER(P)]
+        L.ww_workspace_free.argtypes = [P]
+        L.ww_workspace_bytes.argtypes = [i64, i64]
+        L.ww_workspace_bytes.restype = i64
+        L.ww_residues.argtypes = [P, i32, P, P, i64, i64, P, P, P]
+        L.ww_costs.argtypes = [P, i32, P, P, i64, i64, P, ctypes.POINTER(Params), P, P, P]
+        L.ww_solve_mcf.argtypes = [P, P, P, i64, i64, ctypes.POINTER(Params), P, P, P, P, P, P]
+        L.ww_get_solve_stats.argtypes = [P, ctypes.POINTER(SolveStats)]
+        L.ww_integrate.argtypes = [P, i32, P, P, P, i64, i64, P, P, P]
+        L.ww_unwrap.argtypes = [P, i32, P, d, P, i64, i64, ctypes.POINTER(Params), P, P, P,
+                                ctypes.POINTER(i64), P]
+        L.ww_certificate.argtypes = [P, P, P, P, P, i64, i64, P, P]
+        for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
+                  "ww_costs", "ww_solve_mcf", "ww_get_solve_stats", "ww_integrate", "ww_unwrap",
+                  "ww_certificate"):
+            getattr(L, f).restype = i32
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().ww_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != WW_OK:
+        raise WWError(status, what)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().ww_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Lut:
+    """A cost table for one number of looks (library-owned, cached per nlooks)."""
+
+    def __init__(self, handle, nlooks):
+        self._h = ctypes.c_void_p(handle)
+        self.nlooks = nlooks
+
+    @classmethod
+    def build(cls, nlooks: float) -> "Lut":
+        h = ctypes.c_void_p()
+        _check(lib().ww_build_lut(float(nlooks), ctypes.byref(h)), "ww_build_lut")
+        return cls(h.value, nlooks)
+
+    @classmethod
+    def from_table(cls, nlooks: float, table: np.ndarray) -> "Lut":
+        t = np.ascontiguousarray(table, np.int16)
+        assert t.size == N_GAMMA * N_ALPHA
+        h = ctypes.c_void_p()
+        _check(lib().ww_lut_from_table(float(nlooks), t.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)),
+               "ww_lut_from_table")
+        return cls(h.value, nlooks)
+
+    def table(self) -> np.ndarray:
+        t = np.empty((N_GAMMA, N_ALPHA), np.int16)
+        _check(lib().ww_lut_table(self._h, t.ctypes.data_as(ctypes.c_void_p), None), "ww_lut_table")
+        return t
+
+    def cost100(self) -> np.ndarray:
+        c = np.empty((N_GAMMA, N_ALPHA), np.float64)
+        _check(lib().ww_lut_table(self._h, None, c.ctypes.data_as(ctypes.c_void_p)), "ww_lut_table")
+        return c
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.ww_lut_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+class Workspace:
+    """Device scratch for one request of up to rows x cols (not shared by overlapping calls)."""
+
+    def __init__(self, rows: int, cols: int):
+        h = ctypes.c_void_p()
+        _check(lib().ww_workspace_create(int(rows), int(cols), ctypes.byref(h)), "ww_workspace_create")
+        self._h = h
+        self.rows, self.cols = rows, cols
+
+    @staticmethod
+    def bytes(rows, cols) -> int:
+        return int(lib().ww_workspace_bytes(int(rows), int(cols)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        s = SolveStats()
+        _check(lib().ww_get_solve_stats(self._h, ctypes.byref(s)), "ww_get_solve_stats")
+        return s.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().ww_workspace_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------- tensor marshalling ----------------
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ifg(ifg):
+    torch = _torch()
+    if ifg.dtype == torch.complex64:
+        return _ptr(ifg), 1
+    assert ifg.dtype == torch.float32, "phase must be float32 or complex64"
+    return _ptr(ifg), 0
+
+
+def residues(ifg, coh=None, mask=None):
+    """-> (residues int8 [(m-1),(n-1)], ground int32 [1]) on the device."""
+    torch = _torch()
+    m, n = ifg.shape
+    r = torch.empty((m - 1, n - 1), dtype=torch.int8, device=ifg.device)
+    g = torch.empty(1, dtype=torch.int32, device=ifg.device)
+    p, c = _ifg(ifg)
+    _check(lib().ww_residues(p, c, _ptr(coh), _ptr(mask), m, n, _ptr(r), _ptr(g), _stream()), "ww_residues")
+    return r, g
+
+
+def costs(ifg, coh, lut: Lut, ws: Workspace, mask=None, params: Params | None = None):
+    """-> costs int16 [4, m, n] on the device."""
+    torch = _torch()
+    m, n = ifg.shape
+    out = torch.empty((4, m, n), dtype=torch.int16, device=ifg.device)
+    p, c = _ifg(ifg)
+    prm = params or default_params()
+    _check(lib().ww_costs(p, c, _ptr(coh), _ptr(mask), m, n, lut.handle, ctypes.byref(prm), ws.handle,
+                          _ptr(out), _stream()), "ww_costs")
+    return out
+
+
+def solve_mcf(res, ground, cost_planes, ws: Workspace, params: Params | None = None, check=True):
+    """-> (flows int8 [2,m,n], potentials int64 [(m-1)(n-1)+1], total_cost int64 [1], status int)."""
+    torch = _torch()
+    _, m, n = cost_planes.shape
+    dev = cost_planes.device
+    flows = torch.empty((2, m, n), dtype=torch.int8, device=dev)
+    pot = torch.empty((m - 1) * (n - 1) + 1, dtype=torch.int64, device=dev)
+    tc = torch.empty(1, dtype=torch.int64, device=dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    prm = params or default_params()
+    status = lib().ww_solve_mcf(_ptr(res), _ptr(ground), _ptr(cost_planes), m, n, ctypes.byref(prm), ws.handle,
+                                _ptr(flows), _ptr(pot), _ptr(tc), _ptr(st), _stream())
+    if check:
+        _check(status, "ww_solve_mcf")
+    return flows, pot, tc, status
+
+
+def integrate(ifg, flows, coh=None, mask=None):
+    """-> (unwrapped float32 [m,n], cycles int32 [m,n])."""
+    torch = _torch()
+    m, n = ifg.shape
+    unw = torch.empty((m, n), dtype=torch.float32, device=ifg.device)
+    cyc = torch.empty((m, n), dtype=torch.int32, device=ifg.device)
+    p, c = _ifg(ifg)
+    _check(lib().ww_integrate(p, c, _ptr(coh), _ptr(mask), _ptr(flows), m, n, _ptr(unw), _ptr(cyc), _stream()),
+           "ww_integrate")
+    return unw, cyc
+
+
+def unwrap(ifg, coh, nlooks: float, mask=None, ws: Workspace | None = None, params: Params | None = None,
+           out=None):
+    """Whole path.  -> (unwrapped float32 [m,n], cycles int32 [m,n], total_cost int)."""
+    torch = _torch()
+    m, n = ifg.shape
+    if ws is None:
+        ws = Workspace(m, n)
+    if out is None:
+        unw = torch.empty((m, n), dtype=torch.float32, device=ifg.device)
+        cyc = torch.empty((m, n), dtype=torch.int32, device=ifg.device)
+    else:
+        unw, cyc = out
+    p, c = _ifg(ifg)
+    tc = ctypes.c_int64(0)
+    prm = params or default_params()
+    _check(lib().ww_unwrap(p, c, _ptr(coh), float(nlooks), _ptr(mask), m, n, ctypes.byref(prm), ws.handle,
+                           _ptr(unw), _ptr(cyc), ctypes.byref(tc), _stream()), "ww_unwrap")
+    return unw, cyc, tc.value
+
+
+def certificate(res, ground, cost_planes, flows, potentials):
+    """GPU certificate counts: (capacity violations, conservation violations,
+    negative reduced costs, total cost)."""
+    torch = _torch()
+    _, m, n = cost_planes.shape
+    counts = torch.zeros(4, dtype=torch.int64, device=cost_planes.device)
+    _check(lib().ww_certificate(_ptr(res), _ptr(ground), _ptr(cost_planes), _ptr(flows), _ptr(potentials), m, n,
+                                _ptr(counts), _stream()), "ww_certificate")
+    return tuple(int(x) for x in counts.cpu())

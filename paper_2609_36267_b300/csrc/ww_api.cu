@@ -1,0 +1,310 @@
+// C-ABI entry points (include/ww.h): argument checks, the cost-table cache,
+// workspaces and the whole-path orchestration.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+
+#include "ww_internal.cuh"
+
+namespace {
+
+struct LutData {
+  double nlooks = 0.0;
+  int16_t table[ww::kNGamma * ww::kNAlpha];
+  double cost100[ww::kNGamma * ww::kNAlpha];
+  bool has_cost100 = false;
+  std::mutex mu;
+  int16_t* dev[64] = {nullptr};
+  ~LutData() {
+    for (auto* p : dev)
+      if (p) cudaFree(p);
+  }
+};
+
+std::mutex g_cache_mu;
+std::map<uint64_t, std::shared_ptr<LutData>> g_cache;
+
+uint64_t key_of(double L) {
+  uint64_t k;
+  std::memcpy(&k, &L, 8);
+  return k;
+}
+
+std::shared_ptr<LutData>& data_of(const ww_lut* lut) {
+  return *reinterpret_cast<std::shared_ptr<LutData>*>(lut->shared);
+}
+
+bool grid_ok(int64_t m, int64_t n) {
+  return m >= 2 && n >= 2 && m <= (1ll << 30) && n <= (1ll << 30) && (m - 1) * (n - 1) < (1ll << 31) &&
+         m * n < (1ll << 40);
+}
+
+bool params_ok(const ww_params* p) {
+  return p && p->box_half_width >= 0 && p->box_half_width <= 3 && p->steep_cap_ppm >= 0 &&
+         p->steep_cap_ppm <= 1000000 && p->max_passes > 0 && p->max_sweeps > 0 && std::isfinite(p->steep_rad);
+}
+
+}  // namespace
+
+namespace ww {
+
+const int16_t* lut_device_table(const ww_lut* lut, cudaStream_t, ww_status* st) {
+  auto& d = data_of(lut);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *st = WW_ERR_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(d->mu);
+  if (!d->dev[dev]) {
+    int16_t* p = nullptr;
+    if (cudaMalloc(&p, sizeof(d->table)) != cudaSuccess) {
+      *st = WW_ERR_OOM;
+      return nullptr;
+    }
+    if (cudaMemcpy(p, d->table, sizeof(d->table), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(p);
+      *st = WW_ERR_CUDA;
+      return nullptr;
+    }
+    d->dev[dev] = p;
+  }
+  *st = WW_OK;
+  return d->dev[dev];
+}
+
+}  // namespace ww
+
+extern "C" {
+
+const char* ww_status_string(ww_status s) {
+  switch (s) {
+    case WW_OK: return "ok";
+    case WW_ERR_INVALID_ARG: return "invalid argument";
+    case WW_ERR_CUDA: return "CUDA error";
+    case WW_ERR_OOM: return "out of memory";
+    case WW_ERR_INFEASIBLE: return "infeasible: supplies cannot be routed within unit capacities";
+    case WW_ERR_TIMEOUT: return "iteration limit reached";
+    case WW_ERR_OVERFLOW: return "32-bit distance overflow";
+    case WW_ERR_NOT_IMPLEMENTED: return "not implemented";
+    case WW_ERR_INTERNAL: return "internal invariant violated";
+    default: return "unknown status";
+  }
+}
+
+void ww_params_default(ww_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->box_half_width = 2;
+  p->steep_rad = 1.0f;
+  p->steep_cap_ppm = 30000;
+  p->max_passes = 100000;
+  p->max_sweeps = 1000000;
+  p->tile_rows = 0;
+  p->radius_policy = 0;
+}
+
+ww_status ww_build_lut(double nlooks, ww_lut** out) {
+  if (!out || !(nlooks > 1.0) || !std::isfinite(nlooks)) return WW_ERR_INVALID_ARG;
+  std::shared_ptr<LutData> d;
+  {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    auto it = g_cache.find(key_of(nlooks));
+    if (it != g_cache.end()) d = it->second;
+  }
+  if (!d) {
+    auto nd = std::make_shared<LutData>();
+    nd->nlooks = nlooks;
+    int st = ww::lut_build_host(nlooks, nd->table, nd->cost100);
+    if (st != WW_OK) return st;
+    nd->has_cost100 = true;
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    auto it = g_cache.find(key_of(nlooks));
+    if (it != g_cache.end())
+      d = it->second;
+    else
+      d = g_cache[key_of(nlooks)] = nd;
+  }
+  ww_lut* l = new (std::nothrow) ww_lut;
+  if (!l) return WW_ERR_OOM;
+  l->nlooks = nlooks;
+  l->shared = new std::shared_ptr<LutData>(d);
+  *out = l;
+  return WW_OK;
+}
+
+ww_status ww_lut_from_table(double nlooks, const int16_t* host_table, ww_lut** out) {
+  if (!out || !host_table || !(nlooks > 0.0)) return WW_ERR_INVALID_ARG;
+  auto d = std::make_shared<LutData>();
+  d->nlooks = nlooks;
+  std::memcpy(d->table, host_table, sizeof(d->table));
+  ww_lut* l = new (std::nothrow) ww_lut;
+  if (!l) return WW_ERR_OOM;
+  l->nlooks = nlooks;
+  l->shared = new std::shared_ptr<LutData>(d);
+  *out = l;
+  return WW_OK;
+}
+
+ww_status ww_lut_table(const ww_lut* lut, int16_t* host_table, double* cost100) {
+  if (!lut) return WW_ERR_INVALID_ARG;
+  auto& d = data_of(lut);
+  if (host_table) std::memcpy(host_table, d->table, sizeof(d->table));
+  if (cost100) {
+    if (!d->has_cost100) return WW_ERR_INVALID_ARG;
+    std::memcpy(cost100, d->cost100, sizeof(d->cost100));
+  }
+  return WW_OK;
+}
+
+void ww_lut_free(ww_lut* lut) {
+  if (!lut) return;
+  delete reinterpret_cast<std::shared_ptr<LutData>*>(lut->shared);
+  delete lut;
+}
+
+int64_t ww_workspace_bytes(int64_t m, int64_t n) {
+  if (!grid_ok(m, n)) return -1;
+  int64_t P = m * n, N = (m - 1) * (n - 1);
+  int64_t grid = N /*residues*/ + 4 * P * 2 /*costs*/ + 2 * P /*flows*/ + (N + 1) * 8 /*potentials*/ + 64;
+  int64_t steep = 65536 * 4 + 64 + ((2 * P + 1023) / 1024) * 4;
+  return grid + steep + ww::solver_bytes(m, n);
+}
+
+ww_status ww_workspace_create(int64_t max_rows, int64_t max_cols, ww_workspace** out) {
+  if (!out || !grid_ok(max_rows, max_cols)) return WW_ERR_INVALID_ARG;
+  ww_workspace* ws = new (std::nothrow) ww_workspace;
+  if (!ws) return WW_ERR_OOM;
+  std::memset(ws, 0, sizeof(*ws));
+  cudaGetDevice(&ws->device);
+  ws->max_rows = max_rows;
+  ws->max_cols = max_cols;
+  const int64_t m = max_rows, n = max_cols, P = m * n, N = (m - 1) * (n - 1);
+  ws->blocksum_len = (2 * P + 1023) / 1024;
+  bool ok = cudaMalloc(&ws->residues, N) == cudaSuccess && cudaMalloc(&ws->ground, 64) == cudaSuccess &&
+            cudaMalloc(&ws->costs, 4 * P * 2) == cudaSuccess && cudaMalloc(&ws->flows, 2 * P) == cudaSuccess &&
+            cudaMalloc(&ws->potentials, (N + 1) * 8) == cudaSuccess &&
+            cudaMalloc(&ws->total_cost, 64) == cudaSuccess && cudaMalloc(&ws->dev_status, 64) == cudaSuccess &&
+            cudaMalloc(&ws->hist, 65536 * 4) == cudaSuccess && cudaMalloc(&ws->steep_ctr, 64) == cudaSuccess &&
+            cudaMalloc(&ws->blocksum, ws->blocksum_len * 4) == cudaSuccess;
+  if (ok) ok = cudaMemset(ws->hist, 0, 65536 * 4) == cudaSuccess;
+  ww_status st = ok ? ww::solver_alloc(ws, m, n) : WW_ERR_OOM;
+  if (st != WW_OK) {
+    cudaGetLastError();
+    ww_workspace_free(ws);
+    return st;
+  }
+  *out = ws;
+  return WW_OK;
+}
+
+void ww_workspace_free(ww_workspace* ws) {
+  if (!ws) return;
+  cudaFree(ws->residues);
+  cudaFree(ws->ground);
+  cudaFree(ws->costs);
+  cudaFree(ws->flows);
+  cudaFree(ws->potentials);
+  cudaFree(ws->total_cost);
+  cudaFree(ws->dev_status);
+  cudaFree(ws->hist);
+  cudaFree(ws->steep_ctr);
+  cudaFree(ws->blocksum);
+  ww::solver_free(ws);
+  delete ws;
+}
+
+static bool fits(const ww_workspace* ws, int64_t m, int64_t n) {
+  return ws && m <= ws->max_rows && n <= ws->max_cols;
+}
+
+ww_status ww_residues(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask, int64_t m,
+                      int64_t n, int8_t* residues, int32_t* ground, ww_stream stream) {
+  if (!ifg || !residues || !ground || !grid_ok(m, n)) return WW_ERR_INVALID_ARG;
+  return ww::launch_residues(ifg, is_complex ? 1 : 0, coh, mask, m, n, residues, ground, (cudaStream_t)stream);
+}
+
+ww_status ww_costs(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask, int64_t m, int64_t n,
+                   const ww_lut* lut, const ww_params* params, ww_workspace* ws, int16_t* costs, ww_stream stream) {
+  ww_params def;
+  ww_params_default(&def);
+  const ww_params* p = params ? params : &def;
+  if (!ifg || !coh || !lut || !costs || !grid_ok(m, n) || !params_ok(p) || !fits(ws, m, n))
+    return WW_ERR_INVALID_ARG;
+  ww_status st;
+  const int16_t* dt = ww::lut_device_table(lut, (cudaStream_t)stream, &st);
+  if (!dt) return st;
+  return ww::launch_costs(ifg, is_complex ? 1 : 0, coh, mask, m, n, dt, p, ws, costs, (cudaStream_t)stream);
+}
+
+ww_status ww_solve_mcf(const int8_t* residues, const int32_t* ground, const int16_t* costs, int64_t m, int64_t n,
+                       const ww_params* params, ww_workspace* ws, int8_t* flows, int64_t* potentials,
+                       int64_t* total_cost, int32_t* dev_status, ww_stream stream) {
+  ww_params def;
+  ww_params_default(&def);
+  const ww_params* p = params ? params : &def;
+  if (!residues || !ground || !costs || !flows || !potentials || !total_cost || !dev_status || !grid_ok(m, n) ||
+      !params_ok(p) || !fits(ws, m, n))
+    return WW_ERR_INVALID_ARG;
+  return ww::solve_mcf(residues, ground, costs, m, n, p, ws, flows, potentials, total_cost, dev_status,
+                       (cudaStream_t)stream);
+}
+
+ww_status ww_get_solve_stats(const ww_workspace* ws, ww_solve_stats* out) {
+  if (!ws || !out) return WW_ERR_INVALID_ARG;
+  *out = ws->stats;
+  return WW_OK;
+}
+
+ww_status ww_integrate(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask,
+                       const int8_t* flows, int64_t m, int64_t n, float* unwrapped, int32_t* cycles,
+                       ww_stream stream) {
+  if (!ifg || !flows || !unwrapped || !cycles || !grid_ok(m, n)) return WW_ERR_INVALID_ARG;
+  return ww::launch_integrate(ifg, is_complex ? 1 : 0, coh, mask, flows, m, n, unwrapped, cycles,
+                              (cudaStream_t)stream);
+}
+
+ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, double nlooks, const uint8_t* mask,
+                    int64_t m, int64_t n, const ww_params* params, ww_workspace* ws, float* unwrapped,
+                    int32_t* cycles, int64_t* total_cost, ww_stream stream) {
+  ww_params def;
+  ww_params_default(&def);
+  const ww_params* p = params ? params : &def;
+  if (!ifg || !coh || !unwrapped || !cycles || !grid_ok(m, n) || !params_ok(p) || !fits(ws, m, n))
+    return WW_ERR_INVALID_ARG;
+  ww_lut* lut = nullptr;
+  ww_status st = ww_build_lut(nlooks, &lut);
+  if (st != WW_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int16_t* dt = ww::lut_device_table(lut, s, &st);
+  if (!dt) {
+    ww_lut_free(lut);
+    return st;
+  }
+  const int c = is_complex ? 1 : 0;
+  st = ww::launch_residues(ifg, c, coh, mask, m, n, ws->residues, ws->ground, s);
+  if (st == WW_OK) st = ww::launch_costs(ifg, c, coh, mask, m, n, dt, p, ws, ws->costs, s);
+  if (st == WW_OK)
+    st = ww::solve_mcf(ws->residues, ws->ground, ws->costs, m, n, p, ws, ws->flows, ws->potentials,
+                       ws->total_cost, ws->dev_status, s);
+  ww_status st2 = ww::launch_integrate(ifg, c, coh, mask, ws->flows, m, n, unwrapped, cycles, s);
+  if (st == WW_OK) st = st2;
+  if (total_cost && cudaMemcpyAsync(total_cost, ws->total_cost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = WW_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) st = WW_ERR_CUDA;
+  ww_lut_free(lut);
+  return st;
+}
+
+ww_status ww_certificate(const int8_t* residues, const int32_t* ground, const int16_t* costs, const int8_t* flows,
+                         const int64_t* potentials, int64_t m, int64_t n, int64_t* counts, ww_stream stream) {
+  if (!residues || !ground || !costs || !flows || !potentials || !counts || !grid_ok(m, n))
+    return WW_ERR_INVALID_ARG;
+  return ww::launch_certificate(residues, ground, costs, flows, potentials, m, n, counts, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,520 @@
+// Stencil and scan kernels of the hot path:
+//   k_residues       Eq. 1 residues + ground charge (Sec. II-A)
+//   k_costs          slope estimate, LUT gather, mask rule (Sec. II-B)
+//   k_steep_*        steep-edge bound with its 3% cap (Sec. II-B)
+//   k_integrate_*    integration in integer cycles (Sec. II-A, II-C)
+// All are HBM-bound streaming stencils; inputs are staged through shared memory
+// tiles so each pixel is read from HBM once per kernel.
+#include <cuda_runtime.h>
+
+#include "ww_internal.cuh"
+
+namespace ww {
+namespace {
+
+// ---------------- residues ----------------
+constexpr int RTX = 32, RTY = 8;
+
+__global__ void __launch_bounds__(RTX* RTY) k_residues(const void* __restrict__ ifg, int is_complex,
+                                                        const float* __restrict__ coh,
+                                                        const uint8_t* __restrict__ mask, int64_t m,
+                                                        int64_t n, int8_t* __restrict__ res,
+                                                        int32_t* __restrict__ ground) {
+  __shared__ float sp[RTY + 1][RTX + 1];
+  const int64_t i0 = (int64_t)blockIdx.y * RTY, j0 = (int64_t)blockIdx.x * RTX;
+  const int tid = threadIdx.y * RTX + threadIdx.x;
+  for (int q = tid; q < (RTY + 1) * (RTX + 1); q += RTX * RTY) {
+    int r = q / (RTX + 1), c = q % (RTX + 1);
+    int64_t i = i0 + r, j = j0 + c;
+    float v = 0.0f;
+    if (i < m && j < n) v = load_pixel(ifg, is_complex, coh, mask, i * n + j).psi;
+    sp[r][c] = v;
+  }
+  __syncthreads();
+  const int ty = threadIdx.y, tx = threadIdx.x;
+  const int64_t i = i0 + ty, j = j0 + tx;
+  int r = 0;
+  if (i < m - 1 && j < n - 1) {
+    int n_top = wrap_count(__fsub_rn(sp[ty][tx + 1], sp[ty][tx]));
+    int n_right = wrap_count(__fsub_rn(sp[ty + 1][tx + 1], sp[ty][tx + 1]));
+    int n_bottom = wrap_count(__fsub_rn(sp[ty + 1][tx + 1], sp[ty + 1][tx]));
+    int n_left = wrap_count(__fsub_rn(sp[ty + 1][tx], sp[ty][tx]));
+    r = -(n_top + n_right - n_bottom - n_left);
+    res[i * (n - 1) + j] = (int8_t)r;
+  }
+  // block sum of charges -> ground gets minus the total
+  int s = r;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ int ws[RTY];
+  if (tx == 0) ws[ty] = s;
+  __syncthreads();
+  if (tid == 0) {
+    int t = 0;
+    for (int k = 0; k < RTY; ++k) t += ws[k];
+    if (t) atomicAdd(ground, -t);
+  }
+}
+
+// ---------------- costs ----------------
+constexpr int CTX = 32, CTY = 16, CW = 3;  // tile, max box half-width
+constexpr int CPX = CTX + 2 * CW + 1, CPY = CTY + 2 * CW + 1;  // pixel tile
+constexpr int CEX = CTX + 2 * CW, CEY = CTY + 2 * CW;          // edge tile
+
+struct SteepCtr {
+  unsigned long long valid_edges;   // [0]
+  unsigned long long candidates;    // [1]
+  unsigned long long above;         // [2] candidates strictly above the high-bits bin
+  unsigned long long hi_bin;        // [3]
+  unsigned long long threshold;     // [4] exact |d| bits of the cut
+  unsigned long long take_at_thr;   // [5] candidates equal to threshold to zero
+  unsigned long long mode;          // [6] 0 none/all, 1 select
+  unsigned long long pad;
+};
+
+__device__ __forceinline__ float edge_d(float a, float b) {
+  float dp = __fsub_rn(b, a);
+  return __fsub_rn(dp, __fmul_rn(kTwoPiF, (float)wrap_count(dp)));
+}
+
+__global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int is_complex,
+                                               const float* __restrict__ coh,
+                                               const uint8_t* __restrict__ mask, int64_t m, int64_t n,
+                                               const int16_t* __restrict__ table, int w, float steep_rad,
+                                               int16_t* __restrict__ costs, SteepCtr* ctr) {
+  __shared__ float sp[CPY][CPX];
+  __shared__ float sc[CPY][CPX];
+  __shared__ uint8_t sv[CPY][CPX];
+  __shared__ int32_t qh[CEY][CEX + 1], qv[CEY][CEX + 1];
+  __shared__ uint8_t eh[CEY][CEX + 1], ev[CEY][CEX + 1];
+  __shared__ int32_t rh[CEY][CTX], rv[CEY][CTX];      // row (horizontal) partial sums
+  __shared__ uint8_t nh[CEY][CTX], nv[CEY][CTX];      // row partial counts
+  const int64_t i0 = (int64_t)blockIdx.y * CTY, j0 = (int64_t)blockIdx.x * CTX;
+  const int tid = threadIdx.x;
+  // 1. prepared pixels, tile origin (i0 - CW, j0 - CW)
+  for (int q = tid; q < CPY * CPX; q += 256) {
+    int r = q / CPX, c = q % CPX;
+    int64_t i = i0 - CW + r, j = j0 - CW + c;
+    Pix p{0.0f, 0.0f, false};
+    if (i >= 0 && i < m && j >= 0 && j < n) p = load_pixel(ifg, is_complex, coh, mask, i * n + j);
+    sp[r][c] = p.psi;
+    sc[r][c] = p.coh;
+    sv[r][c] = p.valid ? 1 : 0;
+  }
+  __syncthreads();
+  // 2. fixed-point wrapped gradients of every edge in the extended tile
+  for (int q = tid; q < CEY * CEX; q += 256) {
+    int r = q / CEX, c = q % CEX;
+    int64_t i = i0 - CW + r, j = j0 - CW + c;
+    int32_t a = 0, b = 0;
+    uint8_t ea = 0, eb = 0;
+    if (i >= 0 && i < m && j >= 0) {
+      if (j + 1 < n && sv[r][c] && sv[r][c + 1]) {
+        a = __float2int_rn(__fmul_rn(edge_d(sp[r][c], sp[r][c + 1]), kQScale));
+        ea = 1;
+      }
+      if (i + 1 < m && j < n && sv[r][c] && sv[r + 1][c]) {
+        b = __float2int_rn(__fmul_rn(edge_d(sp[r][c], sp[r + 1][c]), kQScale));
+        eb = 1;
+      }
+    }
+    qh[r][c] = a;
+    eh[r][c] = ea;
+    qv[r][c] = b;
+    ev[r][c] = eb;
+  }
+  __syncthreads();
+  // 3. horizontal window sums for the output columns, every extended row
+  for (int q = tid; q < CEY * CTX; q += 256) {
+    int r = q / CTX, c = q % CTX;
+    int32_t sa = 0, sb = 0;
+    int ca = 0, cb = 0;
+    for (int d = -w; d <= w; ++d) {
+      int cc = c + CW + d;
+      sa += qh[r][cc];
+      ca += eh[r][cc];
+      sb += qv[r][cc];
+      cb += ev[r][cc];
+    }
+    rh[r][c] = sa;
+    nh[r][c] = (uint8_t)ca;
+    rv[r][c] = sb;
+    nv[r][c] = (uint8_t)cb;
+  }
+  __syncthreads();
+  // 4. vertical sums, slope estimate, LUT gather, mask rule; steep candidates
+  const int64_t P = m * n;
+  unsigned cnt_valid = 0, cnt_cand = 0;
+  for (int q = tid; q < CTY * CTX; q += 256) {
+    int r = q / CTX, c = q % CTX;
+    int64_t i = i0 + r, j = j0 + c;
+    if (i >= m || j >= n) continue;
+    int R = r + CW, C = c + CW;
+    int64_t k = i * n + j;
+    // h edge (i,j)
+    int16_t hp = 0, hm = 0;
+    if (eh[R][C]) {
+      int32_t S = 0;
+      int cnt = 0;
+      for (int d = -w; d <= w; ++d) {
+        S += rh[R + d][c];
+        cnt += nh[R + d][c];
+      }
+      float ah = __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
+      int ig = gamma_index(fminf(sc[R][C], sc[R][C + 1]));
+      hp = __ldg(table + ig * kNAlpha + alpha_index(ah));
+      hm = __ldg(table + ig * kNAlpha + alpha_index(-ah));
+      ++cnt_valid;
+      if (fabsf(edge_d(sp[R][C], sp[R][C + 1])) > steep_rad) ++cnt_cand;
+    }
+    costs[k] = hp;
+    costs[P + k] = hm;
+    int16_t vp = 0, vm = 0;
+    if (ev[R][C]) {
+      int32_t S = 0;
+      int cnt = 0;
+      for (int d = -w; d <= w; ++d) {
+        S += rv[R + d][c];
+        cnt += nv[R + d][c];
+      }
+      float av = __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
+      int ig = gamma_index(fminf(sc[R][C], sc[R + 1][C]));
+      vp = __ldg(table + ig * kNAlpha + alpha_index(av));
+      vm = __ldg(table + ig * kNAlpha + alpha_index(-av));
+      ++cnt_valid;
+      if (fabsf(edge_d(sp[R][C], sp[R + 1][C])) > steep_rad) ++cnt_cand;
+    }
+    costs[2 * P + k] = vp;
+    costs[3 * P + k] = vm;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt_valid += __shfl_xor_sync(0xffffffffu, cnt_valid, o);
+    cnt_cand += __shfl_xor_sync(0xffffffffu, cnt_cand, o);
+  }
+  if ((tid & 31) == 0) {
+    if (cnt_valid) atomicAdd(&ctr->valid_edges, (unsigned long long)cnt_valid);
+    if (cnt_cand) atomicAdd(&ctr->candidates, (unsigned long long)cnt_cand);
+  }
+}
+
+// ---- steep-edge bound (Sec. II-B): global selection over candidate edges ----
+// Edge key order: h plane (i*n+j) then v plane (m*n + i*n+j).  |d| as fp32 bits
+// (monotone for non-negative floats).
+
+__device__ __forceinline__ bool steep_edge(const void* ifg, int is_complex, const float* coh,
+                                           const uint8_t* mask, int64_t m, int64_t n, int64_t key,
+                                           float steep_rad, uint32_t* bits) {
+  const int64_t P = m * n;
+  int plane = key >= P;
+  int64_t k = plane ? key - P : key;
+  int64_t i = k / n, j = k % n;
+  if (plane == 0 && j + 1 >= n) return false;
+  if (plane == 1 && i + 1 >= m) return false;
+  Pix a = load_pixel(ifg, is_complex, coh, mask, k);
+  if (!a.valid) return false;
+  Pix b = load_pixel(ifg, is_complex, coh, mask, plane ? k + n : k + 1);
+  if (!b.valid) return false;
+  float d = fabsf(edge_d(a.psi, b.psi));
+  if (!(d > steep_rad)) return false;
+  *bits = __float_as_uint(d);
+  return true;
+}
+
+__global__ void k_steep_plan(SteepCtr* ctr, int32_t cap_ppm) {
+  // mode 0: zero every candidate (count within the cap); mode 1: select
+  unsigned long long cap = (ctr->valid_edges * (unsigned long long)cap_ppm) / 1000000ull;
+  ctr->mode = ctr->candidates > cap ? 1ull : 0ull;
+  ctr->pad = cap;
+}
+
+__global__ void k_steep_hist(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                             int64_t m, int64_t n, float steep_rad, const SteepCtr* ctr,
+                             uint32_t* hist, int level) {
+  if (ctr->mode != 1) return;
+  const int64_t E = 2 * m * n;
+  for (int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; key < E;
+       key += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t b;
+    if (!steep_edge(ifg, is_complex, coh, mask, m, n, key, steep_rad, &b)) continue;
+    if (level == 0)
+      atomicAdd(&hist[b >> 16], 1u);
+    else if ((b >> 16) == (uint32_t)ctr->hi_bin)
+      atomicAdd(&hist[b & 0xFFFFu], 1u);
+  }
+}
+
+// single block: walk the histogram from the top until the cap is reached
+__global__ void k_steep_find(SteepCtr* ctr, uint32_t* hist, int level) {
+  if (ctr->mode != 1) return;
+  if (threadIdx.x != 0) return;
+  unsigned long long cap = ctr->pad;
+  unsigned long long acc = level == 0 ? 0ull : ctr->above;
+  for (int b = 65535; b >= 0; --b) {
+    unsigned long long h = hist[b];
+    if (acc + h >= cap) {
+      if (level == 0) {
+        ctr->hi_bin = (unsigned long long)b;
+        ctr->above = acc;
+      } else {
+        ctr->threshold = ((unsigned long long)ctr->hi_bin << 16) | (unsigned long long)b;
+        ctr->take_at_thr = cap - acc;
+      }
+      break;
+    }
+    acc += h;
+  }
+  for (int b = 0; b < 65536; ++b) hist[b] = 0;  // ready for the next level / call
+}
+
+// mode 0: zero all candidates; mode 1: zero |d| > threshold, and the first
+// take_at_thr ties in key order (ranked with per-block tie counts).
+constexpr int kSteepChunk = 1024;  // keys per block in the tie-ranking passes
+
+__global__ void k_steep_ties(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                             int64_t m, int64_t n, float steep_rad, const SteepCtr* ctr,
+                             uint32_t* blocksum) {
+  if (ctr->mode != 1) return;
+  const int64_t E = 2 * m * n;
+  int64_t base = (int64_t)blockIdx.x * kSteepChunk;
+  unsigned c = 0;
+  for (int64_t key = base + threadIdx.x; key < min(E, base + kSteepChunk); key += blockDim.x) {
+    uint32_t b;
+    if (steep_edge(ifg, is_complex, coh, mask, m, n, key, steep_rad, &b) && b == (uint32_t)ctr->threshold)
+      ++c;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ unsigned s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s[k];
+    blocksum[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_steep_scan(const SteepCtr* ctr, uint32_t* blocksum, int64_t nblocks) {
+  if (ctr->mode != 1) return;
+  if (threadIdx.x != 0) return;
+  uint32_t acc = 0;
+  for (int64_t b = 0; b < nblocks; ++b) {
+    uint32_t v = blocksum[b];
+    blocksum[b] = acc;
+    acc += v;
+  }
+}
+
+__global__ void k_steep_zero(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                             int64_t m, int64_t n, float steep_rad, const SteepCtr* ctr,
+                             const uint32_t* blocksum, int16_t* costs) {
+  const int64_t E = 2 * m * n, P = m * n;
+  const int mode = (int)ctr->mode;
+  const uint32_t thr = (uint32_t)ctr->threshold;
+  const unsigned long long take = ctr->take_at_thr;
+  int64_t base = (int64_t)blockIdx.x * kSteepChunk;
+  __shared__ unsigned warp_ties[32];
+  unsigned running = mode == 1 ? blocksum[blockIdx.x] : 0;
+  for (int64_t off = 0; off < kSteepChunk; off += blockDim.x) {
+    int64_t key = base + off + threadIdx.x;
+    uint32_t b = 0;
+    bool cand = key < E && steep_edge(ifg, is_complex, coh, mask, m, n, key, steep_rad, &b);
+    bool zero = false, tie = false;
+    if (cand) {
+      if (mode == 0) zero = true;
+      else if (b > thr) zero = true;
+      else if (b == thr) tie = true;
+    }
+    // rank ties in key order inside this block slice
+    unsigned bal = __ballot_sync(0xffffffffu, tie);
+    unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_ties[wid] = __popc(bal);
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (unsigned k = 0; k < (blockDim.x >> 5); ++k) {
+      if (k < wid) before += warp_ties[k];
+      total += warp_ties[k];
+    }
+    unsigned rank = running + before + __popc(bal & ((1u << lane) - 1u));
+    if (tie && rank < take) zero = true;
+    running += total;
+    __syncthreads();
+    if (zero) {
+      int plane = key >= P;
+      int64_t k = plane ? key - P : key;
+      costs[(2 * plane) * P + k] = 0;
+      costs[(2 * plane + 1) * P + k] = 0;
+    }
+  }
+}
+
+// ---------------- integration ----------------
+// Column 0 (single block): K(i+1,0) = K(i,0) + dk_v(i,0) - n_v(i,0).
+__global__ void k_integrate_col0(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                                 const int8_t* flows, int64_t m, int64_t n, int32_t* cycles) {
+  __shared__ int32_t carry_s;
+  __shared__ int32_t ws[32];
+  const int64_t P = m * n;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < m; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int32_t inc = 0;  // increment from row i-1 to row i
+    if (i >= 1 && i < m) {
+      int64_t k = (i - 1) * n;
+      float a = load_pixel(ifg, is_complex, coh, mask, k).psi;
+      float b = load_pixel(ifg, is_complex, coh, mask, k + n).psi;
+      inc = (int32_t)flows[P + k] - wrap_count(__fsub_rn(b, a));
+    }
+    // inclusive block scan
+    int32_t v = inc;
+    unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= (unsigned)o) v += t;
+    }
+    if (lane == 31) ws[wid] = v;
+    __syncthreads();
+    int32_t add = 0;
+    for (unsigned k = 0; k < wid; ++k) add += ws[k];
+    int32_t total = 0;
+    for (unsigned k = 0; k < (blockDim.x >> 5); ++k) total += ws[k];
+    v += add + carry_s;
+    if (i < m) cycles[i * n] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += total;
+    __syncthreads();
+  }
+}
+
+// Rows: one block per row; K(i,j+1) = K(i,j) + dk_h(i,j) - n_h(i,j); then
+// phi = (float)((double)psi + (double)K * 2pi), NaN where invalid.
+constexpr int kRowThreads = 256, kRowItems = 8;
+
+__global__ void __launch_bounds__(kRowThreads) k_integrate_rows(const void* ifg, int is_complex,
+                                                                const float* coh, const uint8_t* mask,
+                                                                const int8_t* flows, int64_t m, int64_t n,
+                                                                float* unw, int32_t* cycles) {
+  const int64_t i = blockIdx.x;
+  if (i >= m) return;
+  __shared__ int32_t ws[kRowThreads / 32];
+  __shared__ float first_psi[kRowThreads];
+  __shared__ int32_t carry_s;
+  const int64_t row = i * n;
+  if (threadIdx.x == 0) carry_s = cycles[row];  // K(i,0) from the column pass
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t seg = 0; seg < n; seg += kRowThreads * kRowItems) {
+    int64_t j0 = seg + (int64_t)threadIdx.x * kRowItems;
+    float psi[kRowItems];
+    bool val[kRowItems];
+#pragma unroll
+    for (int t = 0; t < kRowItems; ++t) {
+      int64_t j = j0 + t;
+      Pix p{0.0f, 0.0f, false};
+      if (j < n) p = load_pixel(ifg, is_complex, coh, mask, row + j);
+      psi[t] = p.psi;
+      val[t] = p.valid;
+    }
+    first_psi[threadIdx.x] = psi[0];
+    __syncthreads();
+    float next_psi;  // pixel j0 + kRowItems
+    if (threadIdx.x + 1 < kRowThreads)
+      next_psi = first_psi[threadIdx.x + 1];
+    else {
+      int64_t j = j0 + kRowItems;
+      next_psi = j < n ? load_pixel(ifg, is_complex, coh, mask, row + j).psi : 0.0f;
+    }
+    // increments inc[t] = K(j0+t+1) - K(j0+t)
+    int32_t local[kRowItems];
+    int32_t s = 0;
+#pragma unroll
+    for (int t = 0; t < kRowItems; ++t) {
+      int64_t j = j0 + t;
+      int32_t inc = 0;
+      if (j + 1 < n) {
+        float b = t + 1 < kRowItems ? psi[t + 1] : next_psi;
+        inc = (int32_t)flows[row + j] - wrap_count(__fsub_rn(b, psi[t]));
+      }
+      local[t] = s;  // exclusive prefix within this thread
+      s += inc;
+    }
+    // block exclusive scan of per-thread sums
+    int32_t v = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= (unsigned)o) v += t;
+    }
+    if (lane == 31) ws[wid] = v;
+    __syncthreads();
+    int32_t add = 0, total = 0;
+    for (unsigned k = 0; k < kRowThreads / 32; ++k) {
+      if (k < wid) add += ws[k];
+      total += ws[k];
+    }
+    int32_t base = carry_s + add + (v - s);
+#pragma unroll
+    for (int t = 0; t < kRowItems; ++t) {
+      int64_t j = j0 + t;
+      if (j >= n) break;
+      int32_t K = base + local[t];
+      cycles[row + j] = K;
+      float out;
+      if (val[t]) {
+        double tt = __dmul_rn((double)K, kTwoPiD);
+        out = __double2float_rn(__dadd_rn((double)psi[t], tt));
+      } else {
+        out = __int_as_float(0x7fc00000);
+      }
+      unw[row + j] = out;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += total;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+ww_status launch_residues(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                          int64_t m, int64_t n, int8_t* res, int32_t* ground, cudaStream_t s) {
+  WW_CUDA_TRY(cudaMemsetAsync(ground, 0, sizeof(int32_t), s));
+  dim3 grid((unsigned)((n - 1 + RTX - 1) / RTX), (unsigned)((m - 1 + RTY - 1) / RTY));
+  k_residues<<<grid, dim3(RTX, RTY), 0, s>>>(ifg, is_complex, coh, mask, m, n, res, ground);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}
+
+ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                       int64_t m, int64_t n, const int16_t* dtable, const ww_params* p,
+                       ww_workspace* ws, int16_t* costs, cudaStream_t s) {
+  SteepCtr* ctr = reinterpret_cast<SteepCtr*>(ws->steep_ctr);
+  WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
+  dim3 grid((unsigned)((n + CTX - 1) / CTX), (unsigned)((m + CTY - 1) / CTY));
+  k_costs<<<grid, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad,
+                               costs, ctr);
+  WW_CUDA_TRY(cudaGetLastError());
+  k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
+  const int64_t E = 2 * m * n;
+  int hist_blocks = 148 * 8;
+  k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->hist, 0);
+  k_steep_find<<<1, 32, 0, s>>>(ctr, ws->hist, 0);
+  k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->hist, 1);
+  k_steep_find<<<1, 32, 0, s>>>(ctr, ws->hist, 1);
+  int64_t nb = (E + kSteepChunk - 1) / kSteepChunk;
+  k_steep_ties<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum);
+  k_steep_scan<<<1, 32, 0, s>>>(ctr, ws->blocksum, nb);
+  k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum,
+                                            costs);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}
+
+ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                           const int8_t* flows, int64_t m, int64_t n, float* unw, int32_t* cyc,
+                           cudaStream_t s) {
+  k_integrate_col0<<<1, 1024, 0, s>>>(ifg, is_complex, coh, mask, flows, m, n, cyc);
+  k_integrate_rows<<<(unsigned)m, kRowThreads, 0, s>>>(ifg, is_complex, coh, mask, flows, m, n, unw, cyc);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}
+
+}  // namespace ww

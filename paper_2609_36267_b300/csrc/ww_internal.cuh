@@ -1,0 +1,219 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ww.h"
+
+namespace ww {
+
+// ---- fp32 constants of the specified formulas (bit patterns in comments) ----
+constexpr float kPiF = 3.14159274101257324f;        // 0x40490FDB
+constexpr float kTwoPiF = 6.28318548202514648f;     // 0x40C90FDB
+constexpr float kAlphaScale = 40.7436637878417969f; // fp32(256/(2pi)), 0x4222F983
+constexpr double kTwoPiD = 6.283185307179586;       // 0x1.921fb54442d18p+2
+constexpr int kNGamma = 128;
+constexpr int kNAlpha = 256;
+constexpr float kQScale = 4194304.0f;               // 2^22 fixed point for the slope sum
+
+// ---- search label packing: d (32 bits) | hops (29 bits) | dir (3 bits) ----
+constexpr uint64_t kInf = ~0ull;
+constexpr int kDirRoot = 0, kDirUp = 1, kDirDown = 2, kDirLeft = 3, kDirRight = 4;
+constexpr uint32_t kNoArc = 0xFFFFFFFFu;  // reduced cost of a missing residual arc
+
+#if defined(__CUDACC__)
+__host__ __device__ inline uint32_t label_dist(uint64_t k) { return (uint32_t)(k >> 32); }
+__host__ __device__ inline int label_dir(uint64_t k) { return (int)(k & 7); }
+
+// Fixed-point CORDIC atan2 (R16 of the design): 30 vectoring iterations, angle
+// unit 2^-29 rad; table entries are round(atan(2^-i) 2^29).
+static __constant__ int32_t kAtanQ[30] = {
+    421657428, 248918915, 131521918, 66762579, 33510843, 16771758, 8387925, 4194219,
+    2097141,   1048575,   524288,    262144,   131072,   65536,    32768,    16384,
+    8192,      4096,      2048,      1024,     512,      256,      128,      64,
+    32,        16,        8,         4,        2,        1};
+constexpr int64_t kHalfPiQ = 843314857;  // round(pi/2 * 2^29)
+
+__device__ __forceinline__ void f32_split(float v, int64_t* M, int* E, int* neg) {
+  uint32_t b = __float_as_uint(v);
+  *neg = (int)(b >> 31);
+  int be = (int)((b >> 23) & 0xFF);
+  uint32_t fr = b & 0x7FFFFFu;
+  if (be == 0) {
+    *M = fr;
+    *E = -149;
+  } else {
+    *M = (int64_t)(fr | 0x800000u);
+    *E = be - 150;
+  }
+}
+
+__device__ __forceinline__ int64_t fixed_scale(int64_t M, int E, int top, int neg) {
+  if (M == 0) return 0;
+  int sh = E + 30 - top;
+  int64_t r = sh >= 0 ? (M << sh) : (-sh >= 63 ? 0 : (M >> (-sh)));
+  return neg ? -r : r;
+}
+
+__device__ __forceinline__ float cordic_phase(float re, float im) {
+  int64_t Mx, My;
+  int Ex, Ey, nx, ny;
+  f32_split(re, &Mx, &Ex, &nx);
+  f32_split(im, &My, &Ey, &ny);
+  if (Mx == 0 && My == 0) return 0.0f;
+  int tx = Mx ? Ex + (64 - __clzll(Mx)) : -100000;
+  int ty = My ? Ey + (64 - __clzll(My)) : -100000;
+  int top = max(tx, ty);
+  int64_t X = fixed_scale(Mx, Ex, top, nx);
+  int64_t Y = fixed_scale(My, Ey, top, ny);
+  int64_t Z = 0;
+  if (X < 0) {
+    int64_t t = X;
+    if (Y >= 0) {
+      X = Y;
+      Y = -t;
+      Z = kHalfPiQ;
+    } else {
+      X = -Y;
+      Y = t;
+      Z = -kHalfPiQ;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 30; ++i) {
+    int64_t xs = X >> i, ys = Y >> i;
+    if (Y >= 0) {
+      X += ys;
+      Y -= xs;
+      Z += kAtanQ[i];
+    } else {
+      X -= ys;
+      Y += xs;
+      Z -= kAtanQ[i];
+    }
+  }
+  float psi = __fmul_rn(__ll2float_rn(Z), 1.0f / 536870912.0f);
+  return fminf(fmaxf(psi, -kPiF), kPiF);
+}
+
+// Wrap count of a phase difference (fp32): +1 above pi, -1 at or below -pi.
+__device__ __forceinline__ int wrap_count(float dpsi) {
+  return (dpsi > kPiF ? 1 : 0) - (dpsi <= -kPiF ? 1 : 0);
+}
+
+// Load one pixel's prepared phase and validity (invalid -> psi 0).
+struct Pix {
+  float psi;
+  float coh;
+  bool valid;
+};
+
+__device__ __forceinline__ Pix load_pixel(const void* ifg, int is_complex, const float* coh,
+                                          const uint8_t* mask, int64_t k) {
+  Pix p;
+  bool ok = mask ? (__ldg(mask + k) != 0) : true;
+  float c = coh ? __ldg(coh + k) : 1.0f;
+  ok = ok && isfinite(c);
+  float psi;
+  if (is_complex) {
+    float2 z = __ldg(reinterpret_cast<const float2*>(ifg) + k);
+    ok = ok && isfinite(z.x) && isfinite(z.y);
+    psi = ok ? cordic_phase(z.x, z.y) : 0.0f;
+  } else {
+    float v = __ldg(reinterpret_cast<const float*>(ifg) + k);
+    ok = ok && isfinite(v);
+    psi = ok ? v : 0.0f;
+  }
+  p.psi = ok ? psi : 0.0f;
+  p.coh = ok ? c : 0.0f;
+  p.valid = ok;
+  return p;
+}
+
+// LUT indices (R8): fp32, every operation rounded separately.
+__device__ __forceinline__ int alpha_index(float a) {
+  float t = __fmul_rn(__fadd_rn(a, kPiF), kAlphaScale);
+  int k = (int)floorf(t);
+  return min(255, max(0, k));
+}
+__device__ __forceinline__ int gamma_index(float g) {
+  int k = (int)floorf(__fmul_rn(g, 128.0f));
+  return min(127, max(0, k));
+}
+#endif  // __CUDACC__
+
+}  // namespace ww
+
+// ---- host-side objects ----
+struct ww_lut {
+  double nlooks;
+  void* shared;  // LutData* (see ww_api.cu)
+};
+
+struct WsCounters;  // device counters for the solver (ww_mcf.cu)
+
+struct ww_workspace {
+  int device;
+  int64_t max_rows, max_cols;
+  // solver state
+  int32_t* excess;     // [N]
+  uint64_t* labels;    // [N]
+  uint64_t* best;      // [N]
+  int32_t* cand;       // [N] compact list of imbalanced nodes
+  int32_t* cand2;      // [N]
+  int32_t* cand_root;  // [N]
+  int32_t* tile_stamp; // [T]
+  int32_t* tile_list[2];
+  void* counters;      // device counters block
+  void* host_counters; // pinned host mirror
+  void* events[2];     // cudaEvent_t pair timing the search kernels
+  // path scratch for ww_unwrap
+  int8_t* residues;
+  int32_t* ground;
+  int16_t* costs;
+  int8_t* flows;
+  int64_t* potentials;
+  int64_t* total_cost;
+  int32_t* dev_status;
+  // steep selection scratch
+  uint32_t* hist;       // [65536]
+  uint64_t* steep_ctr;  // [8]
+  uint32_t* blocksum;   // per-block tie counts
+  int64_t blocksum_len;
+  // statistics of the last solve
+  ww_solve_stats stats;
+  int32_t epoch;
+};
+
+#define WW_CUDA_TRY(expr)                          \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return WW_ERR_CUDA;     \
+  } while (0)
+
+namespace ww {
+// ww_lut.cpp
+int lut_build_host(double nlooks, int16_t* table, double* cost100);
+// ww_api.cu
+const int16_t* lut_device_table(const ww_lut* lut, cudaStream_t stream, ww_status* st);
+// ww_grid.cu
+ww_status launch_residues(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                          int64_t m, int64_t n, int8_t* res, int32_t* ground, cudaStream_t s);
+ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                       int64_t m, int64_t n, const int16_t* dtable, const ww_params* p,
+                       ww_workspace* ws, int16_t* costs, cudaStream_t s);
+ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                           const int8_t* flows, int64_t m, int64_t n, float* unw, int32_t* cyc,
+                           cudaStream_t s);
+// ww_mcf.cu
+ww_status solve_mcf(const int8_t* res, const int32_t* ground, const int16_t* costs, int64_t m,
+                    int64_t n, const ww_params* p, ww_workspace* ws, int8_t* flows, int64_t* pot,
+                    int64_t* total_cost, int32_t* dev_status, cudaStream_t s);
+ww_status launch_certificate(const int8_t* res, const int32_t* ground, const int16_t* costs,
+                             const int8_t* flows, const int64_t* pot, int64_t m, int64_t n,
+                             int64_t* counts, cudaStream_t s);
+int64_t solver_bytes(int64_t m, int64_t n);
+ww_status solver_alloc(ww_workspace* ws, int64_t m, int64_t n);
+void solver_free(ww_workspace* ws);
+}  // namespace ww

@@ -3,7 +3,8 @@
 Calls only the CPU oracle (oracle/).  For each number of looks L it stores
 100*c (Eq. 4, before flooring) and the floored int16 table on the 128 (coherence)
 x 256 (slope) bin-centre grid, built with a 4096-interval half grid in phase and
-two Gauss-Legendre panels per unit of -log(1-gamma).  Run:
+two Gauss-Legendre panels per unit of -log(1-gamma) (an 8192-interval half
+grid for L > 16, where the high-coherence rows are sharper).  Run:
 
     python tests/golden/make_golden.py            # all L
     python tests/golden/make_golden.py 9 50       # selected L
@@ -21,6 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 LOOKS = [4.0, 6.0, 9.0, 16.0, 50.0]
 NH = 4096
+NH_SHARP = 8192  # L > 16
 LAMBDA_PANELS = 2
 
 
@@ -33,8 +35,9 @@ def _one(L: float):
     import oracle
 
     t = time.time()
-    cost100, table = oracle.lut_build(L, nh=NH, lambda_panels=LAMBDA_PANELS)
-    np.savez_compressed(path_for(L), cost100=cost100, table=table, nlooks=L, nh=NH,
+    nh = NH_SHARP if L > 16 else NH
+    cost100, table = oracle.lut_build(L, nh=nh, lambda_panels=LAMBDA_PANELS)
+    np.savez_compressed(path_for(L), cost100=cost100, table=table, nlooks=L, nh=nh,
                         lambda_panels=LAMBDA_PANELS)
     return L, time.time() - t
 

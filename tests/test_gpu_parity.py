@@ -1,0 +1,241 @@
+"""GPU path vs the CPU oracle, through the C-ABI (ctypes binding over libww.so).
+
+Bar: residues, ground charge, LUT indices, cost planes, steep selection and
+integer cycle maps bit-exact; the MCF total cost equal to the oracle's optimum
+with a valid potential certificate; unwrapped phase equal to the oracle's
+bit for bit (same FP64 rounding sequence)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2609_36267_b300 as ww
+from paper_2609_36267_b300 import synth
+
+from gpu_helpers import (device_inputs, golden_table, numpy_certificate, oracle_pipeline, probe_table, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+def cases():
+    out = {
+        "cfg1_256": lambda: synth.config1(),
+        "ragged_257x301_mask": lambda: synth.small_random(21, 257, 301, mask_frac=0.08, lo=0.05, hi=0.8),
+        "complex_300x333_mask": lambda: synth.small_random(22, 300, 333, mask_frac=0.1, want_complex=True,
+                                                           lo=0.05, hi=0.9),
+        "cfg2_512": lambda: synth.config2(m=512, n=512),
+        "tall_130x33": lambda: synth.small_random(23, 130, 33, lo=0.02, hi=0.5),
+        "wide_33x130": lambda: synth.small_random(24, 33, 130, lo=0.02, hi=0.5),
+    }
+    return out
+
+
+def with_nan(x):
+    x.phase[3, 5] = np.nan
+    x.coh[7, 1] = np.inf
+    if x.ifg is not None:
+        x.ifg[9, 9] = np.complex64(complex(np.nan, 1.0))
+    return x
+
+
+@pytest.fixture(scope="module")
+def ws():
+    return ww.Workspace(2048, 2048)
+
+
+@pytest.mark.parametrize("name", list(cases()))
+def test_residues_bit_exact(name):
+    x = with_nan(cases()[name]())
+    ifg, coh, mask = device_inputs(x)
+    r, g = ww.residues(ifg, coh, mask)
+    ref = oracle_pipeline(x, probe_table())
+    assert np.array_equal(r.cpu().numpy(), ref["res"])
+    assert int(g.cpu()[0]) == ref["g"]
+
+
+@pytest.mark.parametrize("name", list(cases()))
+def test_cost_indices_bit_exact(name, ws):
+    """Probe table (entry = 256*i_gamma + i_alpha) makes the cost planes the LUT indices."""
+    x = with_nan(cases()[name]())
+    ifg, coh, mask = device_inputs(x)
+    lut = ww.Lut.from_table(x.nlooks, probe_table())
+    c = ww.costs(ifg, coh, lut, ws, mask).cpu().numpy()
+    ref = oracle_pipeline(x, probe_table())
+    assert np.array_equal(c, ref["costs"])
+
+
+@pytest.mark.parametrize("name", ["cfg1_256", "complex_300x333_mask", "cfg2_512"])
+def test_costs_with_oracle_table_bit_exact(name, ws):
+    x = cases()[name]()
+    tab = golden_table(x.nlooks)
+    ifg, coh, mask = device_inputs(x)
+    c = ww.costs(ifg, coh, ww.Lut.from_table(x.nlooks, tab), ws, mask).cpu().numpy()
+    assert np.array_equal(c, oracle_pipeline(x, tab)["costs"])
+
+
+def noise_case(seed, m, n, levels=None):
+    """Pure phase noise: about 2/3 of edges are steep, far over the 3% cap; with
+    `levels` the phases take few distinct values, so |d| ties at the cut."""
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(-np.pi, np.pi, (m, n))
+    if levels:
+        ph = np.round(ph / (2 * np.pi) * levels) / levels * 2 * np.pi
+        ph = np.clip(ph, -np.pi, np.pi)
+    ph = ph.astype(np.float32)
+    coh = rng.uniform(0, 1, (m, n)).astype(np.float32)
+    mask = (rng.uniform(size=(m, n)) > 0.05).astype(np.uint8)
+    return synth.Interferogram(phase=ph, coh=coh, mask=mask, nlooks=4.0, truth=np.zeros((m, n)))
+
+
+@pytest.mark.parametrize("levels,ppm", [(None, 30000), (7, 30000), (12, 5000), (None, 0), (5, 999999)])
+def test_steep_selection_over_cap_bit_exact(levels, ppm, ws):
+    x = noise_case(5 + (levels or 0), 211, 173, levels)
+    ifg, coh, mask = device_inputs(x)
+    prm = ww.default_params(steep_cap_ppm=ppm)
+    lut = ww.Lut.from_table(4.0, probe_table())
+    c = ww.costs(ifg, coh, lut, ws, mask, params=prm).cpu().numpy()
+    ref = oracle_pipeline(x, probe_table(), steep_cap_ppm=ppm)
+    assert np.array_equal(c, ref["costs"])
+    assert ref["nsteep"] > 0 or ppm == 0
+
+
+@pytest.mark.parametrize("name", list(cases()))
+def test_integrate_bit_exact_with_oracle_flows(name):
+    x = with_nan(cases()[name]())
+    ref = oracle_pipeline(x, golden_table(x.nlooks))
+    st, flows, pot, tc = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+    assert st == 0
+    unw_o, K_o = oracle.integrate(ref["psi"], ref["valid"], flows)
+    ifg, coh, mask = device_inputs(x)
+    unw, K = ww.integrate(ifg, to_dev(flows), coh, mask)
+    assert np.array_equal(K.cpu().numpy(), K_o)
+    u = unw.cpu().numpy()
+    assert np.array_equal(np.isnan(u), np.isnan(unw_o))
+    assert np.array_equal(u[~np.isnan(u)].view(np.uint32), unw_o[~np.isnan(unw_o)].view(np.uint32))
+
+
+def solve_and_check(ref, ws, params=None):
+    res, g, costs = ref["res"], ref["g"], ref["costs"]
+    flows, pot, tc, status = ww.solve_mcf(to_dev(res), to_dev(np.array([g], np.int32)), to_dev(costs), ws,
+                                          params=params, check=False)
+    return status, flows.cpu().numpy(), pot.cpu().numpy(), int(tc.cpu()[0])
+
+
+@pytest.mark.parametrize("name", list(cases()))
+def test_solve_equals_oracle_optimum_with_certificate(name, ws):
+    x = cases()[name]()
+    ref = oracle_pipeline(x, golden_table(x.nlooks))
+    st_o, flows_o, pot_o, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+    assert st_o == 0
+    status, flows, pot, tc = solve_and_check(ref, ws)
+    assert status == ww.WW_OK, ww.status_string(status)
+    assert tc == tc_o
+    code, tc2, bad = oracle.check_certificate(ref["res"], ref["g"], ref["costs"], flows, pot)
+    assert code == 0 and tc2 == tc
+    ok, tc3, why = numpy_certificate(ref["res"], ref["g"], ref["costs"], flows, pot)
+    assert ok, why
+    import torch
+    counts = ww.certificate(to_dev(ref["res"]), to_dev(np.array([ref["g"]], np.int32)), to_dev(ref["costs"]),
+                            to_dev(flows), to_dev(pot))
+    assert counts[:3] == (0, 0, 0) and counts[3] == tc
+    # report how much of the cycle map matches the oracle's (ties allow several optima)
+    _, K_g = oracle.integrate(ref["psi"], ref["valid"], flows)
+    _, K_o = oracle.integrate(ref["psi"], ref["valid"], flows_o)
+    agree = float(np.mean(K_g == K_o))
+    print(f"{name}: cost {tc}, residues {np.count_nonzero(ref['res'])}, K agreement {agree:.4f}, "
+          f"stats {ws.stats()}")
+
+
+def test_solve_is_deterministic(ws):
+    x = synth.config2(m=512, n=512)
+    ref = oracle_pipeline(x, golden_table(x.nlooks))
+    a = solve_and_check(ref, ws)
+    b = solve_and_check(ref, ws)
+    assert a[0] == b[0] == 0
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_solve_charge_two_random_supplies(seed, ws):
+    rng = np.random.default_rng(seed)
+    m, n = int(rng.integers(20, 90)), int(rng.integers(20, 90))
+    res = rng.choice([-2, -1, 0, 0, 0, 0, 0, 0, 1, 2], size=(m - 1, n - 1)).astype(np.int8)
+    g = -int(res.sum())
+    costs = rng.integers(0, 500, (4, m, n)).astype(np.int16)
+    costs[rng.random((4, m, n)) < 0.15] = 0
+    ref = dict(res=res, g=g, costs=costs)
+    st_o, _, _, tc_o = oracle.solve_mcf(res, g, costs)
+    status, flows, pot, tc = solve_and_check(ref, ws)
+    if st_o == 0:
+        assert status == 0 and tc == tc_o
+        assert numpy_certificate(res, g, costs, flows, pot)[0]
+    else:
+        assert status == ww.WW_ERR_INFEASIBLE
+
+
+def test_solve_infeasible_block(ws):
+    m = n = 14
+    res = np.zeros((m - 1, n - 1), np.int8)
+    res[3:9, 3:9] = 1
+    res[0, 0] = -1
+    g = -int(res.sum())
+    costs = np.ones((4, m, n), np.int16)
+    assert not oracle.feasible(res, g)
+    status, *_ = solve_and_check(dict(res=res, g=g, costs=costs), ws)
+    assert status == ww.WW_ERR_INFEASIBLE
+
+
+def test_solve_pass_limit_times_out(ws):
+    x = synth.config2(m=256, n=256)
+    ref = oracle_pipeline(x, golden_table(x.nlooks))
+    status, *_ = solve_and_check(ref, ws, params=ww.default_params(max_passes=1))
+    assert status == ww.WW_ERR_TIMEOUT
+
+
+@pytest.mark.parametrize("m,n", [(2, 2), (2, 9), (9, 2), (3, 3), (33, 33), (65, 2)])
+def test_tiny_grids(m, n, ws):
+    x = synth.small_random(m * 100 + n, m, n, lo=0.0, hi=0.3)
+    ref = oracle_pipeline(x, golden_table(9.0))
+    ifg, coh, mask = device_inputs(x)
+    r, g = ww.residues(ifg, coh, mask)
+    assert np.array_equal(r.cpu().numpy(), ref["res"]) and int(g.cpu()[0]) == ref["g"]
+    c = ww.costs(ifg, coh, ww.Lut.from_table(9.0, golden_table(9.0)), ws, mask).cpu().numpy()
+    assert np.array_equal(c, ref["costs"])
+    st_o, _, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+    status, flows, pot, tc = solve_and_check(ref, ws)
+    assert status == 0 and tc == tc_o
+    assert numpy_certificate(ref["res"], ref["g"], ref["costs"], flows, pot)[0]
+
+
+def test_all_masked_and_single_valid_pixel(ws):
+    for keep in (0, 1):
+        x = synth.small_random(77, 40, 50)
+        x.mask[:] = 0
+        if keep:
+            x.mask[20, 25] = 1
+        ref = oracle_pipeline(x, golden_table(9.0))
+        assert not ref["res"].any()
+        unw, K, tc = ww.unwrap(to_dev(x.phase), to_dev(x.coh), 9.0, to_dev(x.mask), ws=ws)
+        u = unw.cpu().numpy()
+        assert tc == 0 and not K.cpu().numpy().any()
+        assert np.isnan(u).sum() == x.mask.size - keep
+
+
+@pytest.mark.parametrize("name", ["cfg1_256", "complex_300x333_mask", "cfg2_512"])
+def test_unwrap_end_to_end(name, ws):
+    """Whole path with the library's own table; optimal cost equal to the
+    oracle run on the library's table values (index/gather parity is tested
+    above with the oracle's table), rewrap within 1e-5 rad."""
+    x = cases()[name]()
+    ifg, coh, mask = device_inputs(x)
+    unw, K, tc = ww.unwrap(ifg, coh, x.nlooks, mask, ws=ws)
+    u, Kn = unw.cpu().numpy(), K.cpu().numpy()
+    ref = oracle_pipeline(x, golden_table(x.nlooks))
+    lib_tab = ww.Lut.build(x.nlooks).table()
+    if np.array_equal(lib_tab, golden_table(x.nlooks)):
+        st_o, flows_o, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+        assert tc == tc_o
+    v = ~np.isnan(u)
+    assert np.array_equal(v, ref["valid"].astype(bool))
+    exact = ref["psi"].astype(np.float64) + 2 * np.pi * Kn
+    assert np.max(np.abs(u[v] - exact[v]), initial=0.0) <= 1e-5
+    assert Kn[0, 0] == 0
