@@ -287,19 +287,19 @@ def run_ours(args, rank, world, local):
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": None, "roofline": roof, "cpu_baseline": base, "clocks": clk.summary(),
                 "solver": {k: st[k] for k in ("passes", "augmentations", "search_iterations", "tile_visits",
-                                                 "residues", "ms_search_gpu", "ms_search", "ms_other")},
+                                                 "residues", "ms_search_gpu", "ms_other", "local_rounds",
+                                                 "visit_cycles")},
                 "total_costs_seen": sorted(costs_seen)}
         line["gpu_launches"] = launch_count(st, args.steps)
         print(json.dumps(line), flush=True)
 
 
 def launch_count(st, steps):
-    """Kernels of this library launched per timed step times steps."""
-    per_pass = 8  # init_labels, seed, select, augment, reset, potentials, compact, finish
-    grid = 1 + 1 + 1 + 7 + 2  # residues, costs, steep plan, steep passes, integrate
-    solver_fixed = 1 + 2  # init_state, total_cost, write_result
-    per_step = grid + solver_fixed + st["passes"] * per_pass + st["search_iterations"]
-    return int(per_step * steps)
+    """Kernels of this library launched per timed step, times steps."""
+    grid = 12  # residues, costs, steep plan/hist x2/find x2/ties/scan/zero, integrate col0/rows
+    solver_fixed = 3  # init_state, total_cost, write_result
+    per_pass = 9  # init_labels, seed_tiles, search, select, augment, reset_best, potentials, compact, finish
+    return int((grid + solver_fixed + st["passes"] * per_pass) * steps)
 
 
 def main():

@@ -152,6 +152,8 @@ typedef struct ww_solve_stats {
   double ms_search;      /* host wall time in the search loops */
   double ms_other;       /* host wall time in select/augment/update */
   double ms_search_gpu;  /* device time of the search kernel launches (CUDA events) */
+  int64_t local_rounds;  /* directional-scan rounds summed over tile visits */
+  int64_t visit_cycles;  /* SM clock cycles summed over tile visits */
 } ww_solve_stats;
 ww_status ww_get_solve_stats(const ww_workspace* ws, ww_solve_stats* out);
 

@@ -50,7 +50,8 @@ class SolveStats(ctypes.Structure):
                 ("search_iterations", ctypes.c_int64), ("tile_visits", ctypes.c_int64),
                 ("residues", ctypes.c_int64), ("ground_net", ctypes.c_int64),
                 ("ms_search", ctypes.c_double), ("ms_other", ctypes.c_double),
-                ("ms_search_gpu", ctypes.c_double)]
+                ("ms_search_gpu", ctypes.c_double), ("local_rounds", ctypes.c_int64),
+                ("visit_cycles", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

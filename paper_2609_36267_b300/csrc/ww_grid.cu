@@ -242,27 +242,53 @@ __global__ void k_steep_hist(const void* ifg, int is_complex, const float* coh, 
   }
 }
 
-// single block: walk the histogram from the top until the cap is reached
-__global__ void k_steep_find(SteepCtr* ctr, uint32_t* hist, int level) {
+// One block of 1024 threads: thread t owns the 64 bins [65535-64t-63, 65535-64t];
+// a block scan from the top finds the bin where the running count reaches the cap.
+constexpr int kFindThreads = 1024;
+
+__global__ void __launch_bounds__(kFindThreads) k_steep_find(SteepCtr* ctr, uint32_t* hist, int level) {
   if (ctr->mode != 1) return;
-  if (threadIdx.x != 0) return;
-  unsigned long long cap = ctr->pad;
-  unsigned long long acc = level == 0 ? 0ull : ctr->above;
-  for (int b = 65535; b >= 0; --b) {
-    unsigned long long h = hist[b];
-    if (acc + h >= cap) {
-      if (level == 0) {
-        ctr->hi_bin = (unsigned long long)b;
-        ctr->above = acc;
-      } else {
-        ctr->threshold = ((unsigned long long)ctr->hi_bin << 16) | (unsigned long long)b;
-        ctr->take_at_thr = cap - acc;
-      }
-      break;
-    }
-    acc += h;
+  __shared__ unsigned long long part[kFindThreads];
+  const int t = threadIdx.x;
+  const int hi = 65535 - 64 * t;
+  unsigned long long s = 0;
+  for (int k = 0; k < 64; ++k) s += hist[hi - k];
+  part[t] = s;
+  __syncthreads();
+  // inclusive scan of part[] (from the top bins down) by doubling
+  for (int off = 1; off < kFindThreads; off <<= 1) {
+    unsigned long long v = t >= off ? part[t - off] : 0ull;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
   }
-  for (int b = 0; b < 65536; ++b) hist[b] = 0;  // ready for the next level / call
+  const unsigned long long cap = ctr->pad;
+  const unsigned long long base = level == 0 ? 0ull : ctr->above;
+  unsigned long long before = (t ? part[t - 1] : 0ull) + base;
+  unsigned long long after = part[t] + base;
+  // the first thread whose range reaches the cap walks its bins
+  bool mine = after >= cap && before < cap;
+  if (t == 0 && cap == 0) mine = true;  // nothing to take: cut above every bin
+  if (mine) {
+    unsigned long long acc = before;
+    for (int k = 0; k < 64; ++k) {
+      int b = hi - k;
+      unsigned long long h = hist[b];
+      if (acc + h >= cap) {
+        if (level == 0) {
+          ctr->hi_bin = (unsigned long long)b;
+          ctr->above = acc;
+        } else {
+          ctr->threshold = ((unsigned long long)ctr->hi_bin << 16) | (unsigned long long)b;
+          ctr->take_at_thr = cap - acc;
+        }
+        break;
+      }
+      acc += h;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < 64; ++k) hist[hi - k] = 0;  // ready for the next level / call
 }
 
 // mode 0: zero all candidates; mode 1: zero |d| > threshold, and the first
@@ -292,11 +318,27 @@ __global__ void k_steep_ties(const void* ifg, int is_complex, const float* coh, 
   }
 }
 
-__global__ void k_steep_scan(const SteepCtr* ctr, uint32_t* blocksum, int64_t nblocks) {
+// Exclusive scan of the per-chunk tie counts, one block: each thread scans a
+// contiguous slice, then the slice totals are scanned in shared memory.
+__global__ void __launch_bounds__(kFindThreads) k_steep_scan(const SteepCtr* ctr, uint32_t* blocksum,
+                                                             int64_t nblocks) {
   if (ctr->mode != 1) return;
-  if (threadIdx.x != 0) return;
-  uint32_t acc = 0;
-  for (int64_t b = 0; b < nblocks; ++b) {
+  __shared__ uint32_t part[kFindThreads];
+  const int t = threadIdx.x;
+  const int64_t per = (nblocks + kFindThreads - 1) / kFindThreads;
+  const int64_t b0 = t * per, b1 = min(nblocks, b0 + per);
+  uint32_t s = 0;
+  for (int64_t b = b0; b < b1; ++b) s += blocksum[b];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < kFindThreads; off <<= 1) {
+    uint32_t v = t >= off ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t acc = t ? part[t - 1] : 0u;
+  for (int64_t b = b0; b < b1; ++b) {
     uint32_t v = blocksum[b];
     blocksum[b] = acc;
     acc += v;
@@ -496,12 +538,12 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
   const int64_t E = 2 * m * n;
   int hist_blocks = 148 * 8;
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->hist, 0);
-  k_steep_find<<<1, 32, 0, s>>>(ctr, ws->hist, 0);
+  k_steep_find<<<1, kFindThreads, 0, s>>>(ctr, ws->hist, 0);
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->hist, 1);
-  k_steep_find<<<1, 32, 0, s>>>(ctr, ws->hist, 1);
+  k_steep_find<<<1, kFindThreads, 0, s>>>(ctr, ws->hist, 1);
   int64_t nb = (E + kSteepChunk - 1) / kSteepChunk;
   k_steep_ties<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum);
-  k_steep_scan<<<1, 32, 0, s>>>(ctr, ws->blocksum, nb);
+  k_steep_scan<<<1, kFindThreads, 0, s>>>(ctr, ws->blocksum, nb);
   k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum,
                                             costs);
   WW_CUDA_TRY(cudaGetLastError());

@@ -163,8 +163,9 @@ struct ww_workspace {
   int32_t* cand;       // [N] compact list of imbalanced nodes
   int32_t* cand2;      // [N]
   int32_t* cand_root;  // [N]
-  int32_t* tile_stamp; // [T]
-  int32_t* tile_list[2];
+  int32_t* tile_stamp; // [T] search worklist: 1 while a tile is queued
+  int32_t* tile_list[2]; // [0]: worklist ring slots (tile+1, 0 = empty); [1] spare
+  void* search_q;      // worklist head/tail/pending counters
   void* counters;      // device counters block
   void* host_counters; // pinned host mirror
   void* events[2];     // cudaEvent_t pair timing the search kernels

@@ -42,8 +42,9 @@ constexpr int TS = 32;         // tile side in nodes
 constexpr int TSH = TS + 2;    // with halo
 constexpr int SEARCH_THREADS = 256;
 constexpr int kMaxLocalSweeps = 8192;
+constexpr int kMaxSearchGrid = 148 * 64;  // ring slack: at most one outstanding ticket per CTA
 
-enum : int32_t { kErrOverflow = 1, kErrInternal = 2, kErrWalk = 4 };
+enum : int32_t { kErrOverflow = 1, kErrInternal = 2, kErrWalk = 4, kErrSpin = 8 };
 
 struct McfCtr {
   int32_t list_count[2];
@@ -56,6 +57,8 @@ struct McfCtr {
   long long g_net;
   unsigned long long tile_visits;
   long long total_cost;
+  unsigned long long local_rounds;
+  unsigned long long visit_cycles;
 };
 
 namespace {
@@ -64,13 +67,6 @@ struct Grid {
   int64_t m, n, R, C, N, P;  // pixel rows/cols, node rows/cols, nodes, pixels
   int tiles_x, tiles_y;
 };
-
-__device__ __forceinline__ void activate(int tile, int epoch, int32_t* stamp, int32_t* list, int32_t* count) {
-  if (atomicExch(&stamp[tile], epoch) != epoch) {
-    int pos = atomicAdd(count, 1);
-    list[pos] = tile;
-  }
-}
 
 // Raw residual cost of the arc entering node (i,j) from direction dir (forward
 // search: arc u->v) or leaving it toward dir (reverse search: arc v->u).
@@ -109,49 +105,158 @@ __device__ __forceinline__ int64_t nb_node(const Grid& g, int64_t i, int64_t j, 
   }
 }
 
+// ---- tile worklist shared by all CTAs of one persistent search launch ----
+// Producers reserve ring positions with atomicAdd(tail) and then publish the
+// tile in that slot; consumers take tickets with atomicAdd(head) and wait for
+// their slot to be published.  A tile is queued at most once at a time (flag
+// `inq`), and at most one ticket per CTA is outstanding, so a ring of
+// tiles + CTAs slots never wraps onto an unconsumed entry.  `pending` counts
+// tiles queued or in process; it is decremented only after a tile's
+// neighbours have been queued, so it reaches zero exactly at convergence, and
+// a consumer whose slot is still empty then leaves.
+struct SearchQ {
+  int32_t head, tail, pending, pad;
+};
+
+constexpr int kSpinLimit = 1 << 25;  // idle polls (~100 ns each) before giving up
+
+__device__ __forceinline__ int ld_volatile(const int32_t* p) { return *((volatile const int32_t*)p); }
+
+// Returns false if the slot stayed occupied past the wait limit (reported as an error).
+__device__ __forceinline__ bool q_push(int tile, int ring, SearchQ* q, int32_t* slots, int32_t* inq) {
+  if (atomicExch(&inq[tile], 1) != 0) return true;
+  atomicAdd(&q->pending, 1);
+  int pos = atomicAdd(&q->tail, 1);
+  __threadfence();
+  int* slot = &slots[pos % ring];
+  for (int spin = 0; spin < kSpinLimit; ++spin) {
+    if (atomicCAS(slot, 0, tile + 1) == 0) return true;
+    __nanosleep(100);
+  }
+  return false;
+}
+
+// Returns a tile, -1 when the search has converged, -2 on a bounded-wait timeout.
+__device__ int q_pop(int ring, SearchQ* q, int32_t* slots, int32_t* inq) {
+  const int h = atomicAdd(&q->head, 1);
+  int* slot = &slots[h % ring];
+  for (int spin = 0; spin < kSpinLimit; ++spin) {
+    int v = ld_volatile(slot);
+    if (v != 0) {
+      atomicExch(slot, 0);
+      atomicExch(&inq[v - 1], 0);
+      __threadfence();
+      return v - 1;
+    }
+    if (ld_volatile(&q->pending) == 0) return -1;
+    __nanosleep(spin < 64 ? 20 : 200);
+  }
+  return -2;
+}
+
+constexpr uint64_t KINF = kInf >> 3;                  // (distance, hops) part of an unreached label
+constexpr uint64_t KDIST_INF = 0xFFFFFFFFull << 29;   // distance field all ones
+
+__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
+  uint64_t s = a + b;  // a, b <= KINF < 2^61: no wrap
+  return s < KINF ? s : KINF;
+}
+
+__device__ __forceinline__ uint64_t arc_weight(uint32_t w) {
+  return w == kNoArc ? KINF : (((uint64_t)w << 29) + 1ull);  // +w distance, +1 hop
+}
+
+// One directional min-plus scan over 32 cells held one per lane:
+//   c_k = min(K_k, c_{k-1} + b_k), c_{-1} = halo, k in scan order,
+// then every cell takes the candidate from its predecessor in scan order
+// (direction code dir) if that beats its label.  Returns true if any changed.
+template <bool DOWNWARD>
+__device__ __forceinline__ bool scan_line(uint64_t* cell, uint64_t halo_key, uint32_t wraw, int dir, int lane,
+                                          int* err) {
+  const uint64_t lab = *cell;
+  const uint64_t K = lab >> 3;
+  const uint64_t b = arc_weight(wraw);
+  const uint64_t h = halo_key >> 3;
+  uint64_t A = K, B = b;
+  const bool first = DOWNWARD ? lane == 0 : lane == 31;
+  if (first) A = min(A, sat_add(h, b));
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    uint64_t Ap = DOWNWARD ? __shfl_up_sync(0xffffffffu, A, off) : __shfl_down_sync(0xffffffffu, A, off);
+    uint64_t Bp = DOWNWARD ? __shfl_up_sync(0xffffffffu, B, off) : __shfl_down_sync(0xffffffffu, B, off);
+    bool has = DOWNWARD ? lane >= off : lane + off < 32;
+    if (has) {
+      A = min(A, sat_add(Ap, B));
+      B = sat_add(Bp, B);
+    }
+  }
+  uint64_t prev = DOWNWARD ? __shfl_up_sync(0xffffffffu, A, 1) : __shfl_down_sync(0xffffffffu, A, 1);
+  if (first) prev = h;
+  uint64_t cand = sat_add(prev, b);
+  bool ch = false;
+  if (cand < KINF) {
+    if (cand >= KDIST_INF) {
+      *err |= kErrOverflow;
+    } else {
+      uint64_t key = (cand << 3) | (uint64_t)dir;
+      if (key < lab) {
+        *cell = key;
+        ch = true;
+      }
+    }
+  }
+  return ch;
+}
+
+constexpr int LROW = TS + 3;  // padded row stride of the label tile (halo 1 each side + 1 pad)
+constexpr int RCOL = TS + 1;  // padded row stride of the arc-weight planes
+
 template <bool FWD>
 __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t* __restrict__ costs,
                                                            const int8_t* __restrict__ flows,
-                                                           const int64_t* __restrict__ pot,
-                                                           uint64_t* labels, const int32_t* list_in,
-                                                           const int32_t* count_in, int32_t* list_out,
-                                                           int32_t* count_out, int32_t* stamp, int epoch,
-                                                           McfCtr* ctr) {
-  __shared__ uint64_t lab[TSH][TSH];
-  __shared__ uint32_t rc[4][TS][TS];
+                                                           const int64_t* __restrict__ pot, uint64_t* labels,
+                                                           SearchQ* q, int32_t* slots, int32_t* inq, McfCtr* ctr) {
+  __shared__ uint64_t lab[TSH][LROW];
+  __shared__ uint32_t rc[4][TS][RCOL];
   __shared__ int side[4];
+  __shared__ int s_tile;
   const int tid = threadIdx.x;
-  const int lx = tid & 31, ly0 = tid >> 5;  // column lx, rows ly0 + 8k
-  const int count = *count_in;
+  const int lane = tid & 31, warp = tid >> 5;  // 8 warps; a warp owns rows/cols warp + 8k
+  const int ring = g.tiles_x * g.tiles_y + (int)gridDim.x + 64;
   const int64_t pG = pot[g.N];
-  for (int t = blockIdx.x; t < count; t += gridDim.x) {
-    const int tile = list_in[t];
+  int err = 0;
+  for (;;) {
+    if (tid == 0) s_tile = q_pop(ring, q, slots, inq);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile < 0) {
+      if (tid == 0 && tile == -2) atomicOr(&ctr->err, kErrSpin);
+      break;
+    }
     const int64_t ti = tile / g.tiles_x, tj = tile % g.tiles_x;
     const int64_t i0 = ti * TS, j0 = tj * TS;
     if (tid < 4) side[tid] = 0;
-    // labels with halo; outside the grid stands G, a root (label 0)
-    for (int q = tid; q < TSH * TSH; q += SEARCH_THREADS) {
-      int r = q / TSH, c = q % TSH;
+    const long long t_start = clock64();
+    // labels with halo; directly outside the grid stands G, a root (label 0)
+    for (int qd = tid; qd < TSH * TSH; qd += SEARCH_THREADS) {
+      int r = qd / TSH, c = qd % TSH;
       int64_t i = i0 + r - 1, j = j0 + c - 1;
       uint64_t v;
       if (i < 0 || j < 0 || i >= g.R || j >= g.C) {
-        bool ring = (i >= -1 && i <= g.R && j >= -1 && j <= g.C);  // direct neighbour of the grid
+        bool ring = (i >= -1 && i <= g.R && j >= -1 && j <= g.C);
         v = ring ? 0ull : kInf;
       } else {
         v = *((volatile const uint64_t*)&labels[i * g.C + j]);
       }
       lab[r][c] = v;
     }
-    // reduced costs of the four arcs of every node in the tile
-    uint64_t orig[4];
-    int err = 0;
+    // reduced costs of the four arcs of every node (row = warp + 8k, col = lane)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      int ly = ly0 + 8 * k;
-      int64_t i = i0 + ly, j = j0 + lx;
+      int ly = warp + 8 * k;
+      int64_t i = i0 + ly, j = j0 + lane;
       bool ex = i < g.R && j < g.C;
-      int64_t v = i * g.C + j;
-      int64_t pv = ex ? pot[v] : 0;
+      int64_t pv = ex ? pot[i * g.C + j] : 0;
 #pragma unroll
       for (int d = 1; d <= 4; ++d) {
         uint32_t r = kNoArc;
@@ -164,75 +269,78 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
             err |= kErrInternal;
             red = 0;
           }
-          if (red >= (int64_t)kNoArc) {
+          if (red >= (int64_t)kNoArc)
             err |= kErrOverflow;
-          } else {
+          else
             r = (uint32_t)red;
-          }
         }
-        rc[d - 1][ly][lx] = r;
+        rc[d - 1][ly][lane] = r;
       }
     }
     __syncthreads();
+    uint64_t orig[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) orig[k] = lab[ly0 + 8 * k + 1][lx + 1];
-    // local relaxation to the tile's fixed point
-    for (int sweep = 0; sweep < kMaxLocalSweeps; ++sweep) {
+    for (int k = 0; k < 4; ++k) orig[k] = lab[warp + 8 * k + 1][lane + 1];
+    // local fixed point by directional scans: rows left->right and right->left,
+    // then columns top->bottom and bottom->top, until nothing changes
+    int round = 0;
+    for (; round < kMaxLocalSweeps; ++round) {
       bool ch = false;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        int ly = ly0 + 8 * k;
-        int r = ly + 1, c = lx + 1;
-        uint64_t cur = lab[r][c];
-        uint64_t best = cur;
+        int r = warp + 8 * k;  // node row
+        uint64_t* cell = &lab[r + 1][lane + 1];
+        ch |= scan_line<true>(cell, lab[r + 1][0], rc[kDirLeft - 1][r][lane], kDirLeft, lane, &err);
+        __syncwarp();
+        ch |= scan_line<false>(cell, lab[r + 1][TS + 1], rc[kDirRight - 1][r][lane], kDirRight, lane, &err);
+        __syncwarp();
+      }
+      __syncthreads();
 #pragma unroll
-        for (int d = 1; d <= 4; ++d) {
-          uint32_t w = rc[d - 1][ly][lx];
-          if (w == kNoArc) continue;
-          int rr = d == kDirUp ? r - 1 : d == kDirDown ? r + 1 : r;
-          int cc = d == kDirLeft ? c - 1 : d == kDirRight ? c + 1 : c;
-          uint64_t lu = *((volatile uint64_t*)&lab[rr][cc]);
-          if (lu == kInf) continue;
-          uint64_t du = lu >> 32;
-          if (du + w >= 0xFFFFFFFFull) {
-            err |= kErrOverflow;
-            continue;
-          }
-          uint64_t cand = (((lu & ~7ull) + ((uint64_t)w << 32) + 8ull) & ~7ull) | (uint64_t)d;
-          if (cand < best) best = cand;
-        }
-        if (best < cur) {
-          lab[r][c] = best;
-          ch = true;
-        }
+      for (int k = 0; k < 4; ++k) {
+        int c = warp + 8 * k;  // node column; lane = node row
+        uint64_t* cell = &lab[lane + 1][c + 1];
+        ch |= scan_line<true>(cell, lab[0][c + 1], rc[kDirUp - 1][lane][c], kDirUp, lane, &err);
+        __syncwarp();
+        ch |= scan_line<false>(cell, lab[TS + 1][c + 1], rc[kDirDown - 1][lane][c], kDirDown, lane, &err);
+        __syncwarp();
       }
       if (!__syncthreads_or(ch)) break;
     }
     // write back and note which tile sides changed
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      int ly = ly0 + 8 * k;
-      int64_t i = i0 + ly, j = j0 + lx;
-      uint64_t v = lab[ly + 1][lx + 1];
+      int ly = warp + 8 * k;
+      int64_t i = i0 + ly, j = j0 + lane;
+      uint64_t v = lab[ly + 1][lane + 1];
       if (i < g.R && j < g.C && v != orig[k]) {
-        labels[i * g.C + j] = v;
+        // the same tile may be in process in two CTAs (it can be re-queued
+        // while in flight); atomicMin keeps every label monotone
+        atomicMin((unsigned long long*)&labels[i * g.C + j], (unsigned long long)v);
         if (ly == 0) side[0] = 1;
         if (ly == TS - 1) side[1] = 1;
-        if (lx == 0) side[2] = 1;
-        if (lx == TS - 1) side[3] = 1;
+        if (lane == 0) side[2] = 1;
+        if (lane == TS - 1) side[3] = 1;
       }
     }
-    if (err) atomicOr(&ctr->err, err);
+    __threadfence();
     __syncthreads();
     if (tid == 0) {
-      if (side[0] && ti > 0) activate(tile - g.tiles_x, epoch, stamp, list_out, count_out);
-      if (side[1] && ti + 1 < g.tiles_y) activate(tile + g.tiles_x, epoch, stamp, list_out, count_out);
-      if (side[2] && tj > 0) activate(tile - 1, epoch, stamp, list_out, count_out);
-      if (side[3] && tj + 1 < g.tiles_x) activate(tile + 1, epoch, stamp, list_out, count_out);
+      bool ok = true;
+      if (side[0] && ti > 0) ok &= q_push(tile - g.tiles_x, ring, q, slots, inq);
+      if (side[1] && ti + 1 < g.tiles_y) ok &= q_push(tile + g.tiles_x, ring, q, slots, inq);
+      if (side[2] && tj > 0) ok &= q_push(tile - 1, ring, q, slots, inq);
+      if (side[3] && tj + 1 < g.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq);
+      if (!ok) err |= kErrSpin;
       atomicAdd(&ctr->tile_visits, 1ull);
+      atomicAdd(&ctr->local_rounds, (unsigned long long)(round + 1));
+      atomicAdd(&ctr->visit_cycles, (unsigned long long)(clock64() - t_start));
+      __threadfence();
+      atomicSub(&q->pending, 1);
     }
     __syncthreads();
   }
+  if (err) atomicOr(&ctr->err, err);
 }
 
 __global__ void k_init_state(Grid g, const int8_t* res, int32_t* excess, int32_t* cand, McfCtr* ctr) {
@@ -252,28 +360,32 @@ __global__ void k_init_labels(Grid g, const int32_t* excess, uint64_t* labels) {
   }
 }
 
+__device__ __forceinline__ int32_t& ctr_err(const McfCtr* c) { return const_cast<McfCtr*>(c)->err; }
+
+// Seed the worklist: tiles holding a root, and every border tile (G is a root).
 template <bool FWD>
-__global__ void k_seed_tiles(Grid g, const int32_t* excess, const int32_t* cand, const McfCtr* ctr,
-                             int32_t* stamp, int32_t* list, int32_t* count, int epoch) {
+__global__ void k_seed_tiles(Grid g, const int32_t* excess, const int32_t* cand, const McfCtr* ctr, SearchQ* q,
+                             int32_t* slots, int32_t* inq, int search_grid) {
   const int nc = ctr->ncand;
   const int nborder = 2 * g.tiles_x + 2 * g.tiles_y;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nc + nborder;
-       q += (int64_t)gridDim.x * blockDim.x) {
+  const int ring = g.tiles_x * g.tiles_y + search_grid + 64;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc + nborder;
+       k += (int64_t)gridDim.x * blockDim.x) {
     int tile;
-    if (q < nc) {
-      int32_t v = cand[q];
+    if (k < nc) {
+      int32_t v = cand[k];
       int32_t e = excess[v];
       if (!(FWD ? e > 0 : e < 0)) continue;
       int64_t i = v / g.C, j = v % g.C;
       tile = (int)((i / TS) * g.tiles_x + j / TS);
     } else {
-      int b = (int)(q - nc);
-      if (b < g.tiles_x) tile = b;                                             // top row
-      else if (b < 2 * g.tiles_x) tile = (g.tiles_y - 1) * g.tiles_x + (b - g.tiles_x);  // bottom row
-      else if (b < 2 * g.tiles_x + g.tiles_y) tile = (b - 2 * g.tiles_x) * g.tiles_x;     // left col
-      else tile = (b - 2 * g.tiles_x - g.tiles_y) * g.tiles_x + g.tiles_x - 1;           // right col
+      int b = (int)(k - nc);
+      if (b < g.tiles_x) tile = b;
+      else if (b < 2 * g.tiles_x) tile = (g.tiles_y - 1) * g.tiles_x + (b - g.tiles_x);
+      else if (b < 2 * g.tiles_x + g.tiles_y) tile = (b - 2 * g.tiles_x) * g.tiles_x;
+      else tile = (b - 2 * g.tiles_x - g.tiles_y) * g.tiles_x + g.tiles_x - 1;
     }
-    activate(tile, epoch, stamp, list, count);
+    if (!q_push(tile, ring, q, slots, inq)) atomicOr(&ctr_err(ctr), kErrSpin);
   }
 }
 
@@ -441,14 +553,17 @@ ww_status solver_alloc(ww_workspace* ws, int64_t m, int64_t n) {
   if (cudaMalloc(&ws->cand2, N * 4) != cudaSuccess) return WW_ERR_OOM;
   if (cudaMalloc(&ws->cand_root, N * 4) != cudaSuccess) return WW_ERR_OOM;
   if (cudaMalloc(&ws->tile_stamp, tiles * 4) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->tile_list[0], tiles * 4) != cudaSuccess) return WW_ERR_OOM;
+  if (cudaMalloc(&ws->tile_list[0], (tiles + kMaxSearchGrid + 64) * 4) != cudaSuccess) return WW_ERR_OOM;
   if (cudaMalloc(&ws->tile_list[1], tiles * 4) != cudaSuccess) return WW_ERR_OOM;
   if (cudaMalloc(&ws->counters, sizeof(McfCtr)) != cudaSuccess) return WW_ERR_OOM;
+  if (cudaMalloc(&ws->search_q, sizeof(SearchQ)) != cudaSuccess) return WW_ERR_OOM;
   if (cudaMallocHost(&ws->host_counters, sizeof(McfCtr)) != cudaSuccess) return WW_ERR_OOM;
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
   if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) return WW_ERR_CUDA;
   if (cudaMemset(ws->best, 0xFF, N * 8) != cudaSuccess) return WW_ERR_CUDA;
+  // queue flags and ring slots start (and end every search) all zero
   if (cudaMemset(ws->tile_stamp, 0, tiles * 4) != cudaSuccess) return WW_ERR_CUDA;
+  if (cudaMemset(ws->tile_list[0], 0, (tiles + kMaxSearchGrid + 64) * 4) != cudaSuccess) return WW_ERR_CUDA;
   ws->epoch = 0;
   return WW_OK;
 }
@@ -464,58 +579,43 @@ void solver_free(ww_workspace* ws) {
   cudaFree(ws->tile_list[0]);
   cudaFree(ws->tile_list[1]);
   cudaFree(ws->counters);
+  cudaFree(ws->search_q);
   cudaFreeHost(ws->host_counters);
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
   if (ev[0]) cudaEventDestroy(ev[0]);
   if (ev[1]) cudaEventDestroy(ev[1]);
 }
 
+// One multi-root search: labels reset, worklist seeded with root and border
+// tiles, then one persistent launch drains the worklist to the fixed point.
 template <bool FWD>
 static ww_status run_search(const Grid& g, const int16_t* costs, const int8_t* flows, const int64_t* pot,
-                            ww_workspace* ws, McfCtr* dctr, McfCtr* hctr, int max_sweeps, int sm_count,
-                            int64_t* iters, cudaStream_t s) {
+                            ww_workspace* ws, McfCtr* dctr, int sm_count, cudaStream_t s) {
   const int nb_nodes = grid_blocks(g.N, 256, sm_count * 16);
   k_init_labels<FWD><<<nb_nodes, 256, 0, s>>>(g, ws->excess, ws->labels);
-  int cur = 0;
-  WW_CUDA_TRY(cudaMemsetAsync(&dctr->list_count[0], 0, 2 * sizeof(int32_t), s));
-  int epoch = ++ws->epoch;
+  SearchQ* q = reinterpret_cast<SearchQ*>(ws->search_q);
+  WW_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(SearchQ), s));
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search<FWD>, SEARCH_THREADS, 0);
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const int search_grid = std::min(sm_count * per_sm, kMaxSearchGrid);
   k_seed_tiles<FWD><<<grid_blocks(g.N / 64 + 1024, 256, sm_count * 4), 256, 0, s>>>(
-      g, ws->excess, ws->cand, dctr, ws->tile_stamp, ws->tile_list[cur], &dctr->list_count[cur], epoch);
-  int32_t count = 1;  // unknown on the host: launch the first sweep unconditionally
+      g, ws->excess, ws->cand, dctr, q, ws->tile_list[0], ws->tile_stamp, search_grid);
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
-  const int max_blocks = sm_count * 6;
-  for (int it = 0; it < max_sweeps; ++it) {
-    int nxt = cur ^ 1;
-    epoch = ++ws->epoch;
-    WW_CUDA_TRY(cudaMemsetAsync(&dctr->list_count[nxt], 0, sizeof(int32_t), s));
-    int blocks = it == 0 ? max_blocks : std::min(max_blocks, std::max(1, count));
-    WW_CUDA_TRY(cudaEventRecord(ev[0], s));
-    k_search<FWD><<<blocks, SEARCH_THREADS, 0, s>>>(g, costs, flows, pot, ws->labels, ws->tile_list[cur],
-                                                   &dctr->list_count[cur], ws->tile_list[nxt],
-                                                   &dctr->list_count[nxt], ws->tile_stamp, epoch, dctr);
-    WW_CUDA_TRY(cudaGetLastError());
-    WW_CUDA_TRY(cudaEventRecord(ev[1], s));
-    WW_CUDA_TRY(cudaMemcpyAsync(&hctr->list_count[nxt], &dctr->list_count[nxt], sizeof(int32_t),
-                                cudaMemcpyDeviceToHost, s));
-    WW_CUDA_TRY(cudaStreamSynchronize(s));
-    float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) ws->stats.ms_search_gpu += ms;
-    ++*iters;
-    count = hctr->list_count[nxt];
-    cur = nxt;
-    if (count == 0) return WW_OK;
-  }
-  return WW_ERR_TIMEOUT;
+  WW_CUDA_TRY(cudaEventRecord(ev[0], s));
+  k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(g, costs, flows, pot, ws->labels, q, ws->tile_list[0],
+                                                            ws->tile_stamp, dctr);
+  WW_CUDA_TRY(cudaEventRecord(ev[1], s));
+  WW_CUDA_TRY(cudaGetLastError());
+  ++ws->stats.search_iterations;
+  return WW_OK;
 }
 
 template <bool FWD>
 static ww_status run_pass(const Grid& g, const int16_t* costs, int8_t* flows, int64_t* pot, ww_workspace* ws,
                           McfCtr* dctr, McfCtr* hctr, const ww_params* p, int sm_count, cudaStream_t s) {
   auto t0 = std::chrono::steady_clock::now();
-  ww_status st = run_search<FWD>(g, costs, flows, pot, ws, dctr, hctr, p->max_sweeps, sm_count,
-                                 &ws->stats.search_iterations, s);
-  auto t1 = std::chrono::steady_clock::now();
-  ws->stats.ms_search += std::chrono::duration<double, std::milli>(t1 - t0).count();
+  ww_status st = run_search<FWD>(g, costs, flows, pot, ws, dctr, sm_count, s);
   if (st != WW_OK) return st;
   const int nb = grid_blocks(hctr->ncand > 0 ? hctr->ncand : g.N, 256, sm_count * 16);
   WW_CUDA_TRY(cudaMemsetAsync(&dctr->D, 0, 2 * sizeof(int32_t), s));  // D, naug
@@ -529,7 +629,10 @@ static ww_status run_pass(const Grid& g, const int16_t* costs, int8_t* flows, in
   std::swap(ws->cand, ws->cand2);
   WW_CUDA_TRY(cudaMemcpyAsync(hctr, dctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, s));
   WW_CUDA_TRY(cudaStreamSynchronize(s));
-  ws->stats.ms_other += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) ws->stats.ms_search_gpu += ms;
+  ws->stats.ms_other += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return WW_OK;
 }
 
@@ -590,6 +693,8 @@ ww_status solve_mcf(const int8_t* res, const int32_t* ground, const int16_t* cos
   WW_CUDA_TRY(cudaMemcpyAsync(&hst, dev_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   WW_CUDA_TRY(cudaStreamSynchronize(s));
   ws->stats.tile_visits = (int64_t)hctr->tile_visits;
+  ws->stats.local_rounds = (int64_t)hctr->local_rounds;
+  ws->stats.visit_cycles = (int64_t)hctr->visit_cycles;
   return hst;
 }
 

@@ -61,7 +61,7 @@ def test_lut_from_table_roundtrip():
 
 # tolerance in 100*c units between the two independent FP64 builds; the
 # tabulation error of each shrinks ~h^4-h^5 (see the oracle convergence test)
-TOL = {4.0: 2e-3, 6.0: 2e-3, 9.0: 2e-3, 16.0: 4e-3, 50.0: 2e-2}
+TOL = {4.0: 2e-3, 6.0: 2e-3, 9.0: 2e-3, 16.0: 4e-3, 50.0: 8e-3}
 
 
 @pytest.mark.parametrize("L", [4.0, 6.0, 9.0, 16.0, 50.0])
