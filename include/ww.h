@@ -131,6 +131,23 @@ ww_status ww_costs(const void* ifg, int32_t is_complex, const float* coh, const 
                    int64_t m, int64_t n, const ww_lut* lut, const ww_params* params,
                    ww_workspace* ws, int16_t* costs, ww_stream stream);
 
+/* Same output as ww_costs, for callers that cannot allocate device memory: for
+ * example code whose device memory is owned by another allocator (a
+ * framework's caching pool) or a real-time loop that must not pay cudaMalloc's
+ * implicit device synchronisation.  The paper has no counterpart; this is an
+ * interface variant.  It calls no cudaMalloc/cudaFree and takes no workspace:
+ * the steep-edge selection scratch and a copy of the cost table live in one
+ * file-scope device array of about 1.4 MB that every GPU loading the library
+ * holds until the process exits.  Limit: m*n <= 2^27 pixels (134,217,728);
+ * larger grids return WW_ERR_INVALID_ARG.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the array
+ * and each rewrites it (table copy, cleared counters), so calls that overlap
+ * on the GPU race and must be serialised by the caller (e.g. one stream). */
+ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask,
+                           int64_t m, int64_t n, const ww_lut* lut, const ww_params* params,
+                           int16_t* costs, ww_stream stream);
+
 /* ---- Step 3: MCF solve (Sec. II-A Eq. 2, Sec. II-C) ----
  * Exact successive-shortest-path solve of Eq. 2 with unit capacities.
  * Outputs: flows [2][m][n] (dk in {-1,0,1}), potentials int64 [(m-1)(n-1)+1]

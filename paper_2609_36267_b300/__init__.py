@@ -82,6 +82,7 @@ def lib():
         L.ww_workspace_bytes.restype = i64
         L.ww_residues.argtypes = [P, i32, P, P, i64, i64, P, P, P]
         L.ww_costs.argtypes = [P, i32, P, P, i64, i64, P, ctypes.POINTER(Params), P, P, P]
+        L.ww_costs_noalloc.argtypes = [P, i32, P, P, i64, i64, P, ctypes.POINTER(Params), P, P]
         L.ww_solve_mcf.argtypes = [P, P, P, i64, i64, ctypes.POINTER(Params), P, P, P, P, P, P]
         L.ww_get_solve_stats.argtypes = [P, ctypes.POINTER(SolveStats)]
         L.ww_integrate.argtypes = [P, i32, P, P, P, i64, i64, P, P, P]
@@ -89,7 +90,7 @@ def lib():
                                 ctypes.POINTER(i64), P]
         L.ww_certificate.argtypes = [P, P, P, P, P, i64, i64, P, P]
         for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
-                  "ww_costs", "ww_solve_mcf", "ww_get_solve_stats", "ww_integrate", "ww_unwrap",
+                  "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_get_solve_stats", "ww_integrate", "ww_unwrap",
                   "ww_certificate"):
             getattr(L, f).restype = i32
         _lib = L
@@ -240,6 +241,20 @@ def costs(ifg, coh, lut: Lut, ws: Workspace, mask=None, params: Params | None = 
     prm = params or default_params()
     _check(lib().ww_costs(p, c, _ptr(coh), _ptr(mask), m, n, lut.handle, ctypes.byref(prm), ws.handle,
                           _ptr(out), _stream()), "ww_costs")
+    return out
+
+
+def costs_noalloc(ifg, coh, lut: Lut, mask=None, params: Params | None = None, out=None):
+    """ww_costs without a workspace or any device allocation by the library
+    (scratch in a static device array; calls that overlap on the GPU race)."""
+    torch = _torch()
+    m, n = ifg.shape
+    if out is None:
+        out = torch.empty((4, m, n), dtype=torch.int16, device=ifg.device)
+    p, c = _ifg(ifg)
+    prm = params or default_params()
+    _check(lib().ww_costs_noalloc(p, c, _ptr(coh), _ptr(mask), m, n, lut.handle, ctypes.byref(prm), _ptr(out),
+                                  _stream()), "ww_costs_noalloc")
     return out
 
 

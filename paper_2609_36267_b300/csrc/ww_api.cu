@@ -77,6 +77,8 @@ const int16_t* lut_device_table(const ww_lut* lut, cudaStream_t, ww_status* st) 
   return d->dev[dev];
 }
 
+const int16_t* lut_host_table(const ww_lut* lut) { return data_of(lut)->table; }
+
 }  // namespace ww
 
 extern "C" {

@@ -7,6 +7,8 @@
 // tiles so each pixel is read from HBM once per kernel.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "ww_internal.cuh"
 
 namespace ww {
@@ -560,3 +562,84 @@ ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, co
 }
 
 }  // namespace ww
+
+// ---------------- cost step without any device allocation ----------------
+// For callers that cannot call cudaMalloc: for example code whose device memory
+// is owned by another allocator (a framework's caching pool) or a real-time
+// loop that must not pay cudaMalloc's implicit device synchronisation.  The
+// steep-edge selection scratch and the cost table live in one file-scope
+// device array instead of a workspace; every GPU that loads this library holds
+// it (about 1.4 MB) until the process exits.
+namespace ww {
+namespace {
+
+constexpr int64_t kNoAllocMaxPixels = 1ll << 27;  // m*n limit of ww_costs_noalloc
+constexpr int64_t kNoAllocChunks = (2 * kNoAllocMaxPixels + kSteepChunk - 1) / kSteepChunk;
+constexpr size_t kNoAllocTableBytes = sizeof(int16_t) * kNGamma * kNAlpha;  // 64 KiB
+constexpr size_t kNoAllocHistOff = kNoAllocTableBytes;
+constexpr size_t kNoAllocCtrOff = kNoAllocHistOff + 65536 * sizeof(uint32_t);
+constexpr size_t kNoAllocBlocksumOff = kNoAllocCtrOff + 256;
+constexpr size_t kNoAllocBytes = kNoAllocBlocksumOff + kNoAllocChunks * sizeof(uint32_t);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device (the host-side
+// name is only a stand-in and must never be passed to a kernel).
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[64] = {nullptr};
+
+ww_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WW_ERR_CUDA;
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return WW_ERR_CUDA;
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return WW_OK;
+}
+
+}  // namespace
+}  // namespace ww
+
+extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask,
+                                      int64_t m, int64_t n, const ww_lut* lut, const ww_params* params,
+                                      int16_t* costs, ww_stream stream) {
+  using namespace ww;
+  ww_params def;
+  ww_params_default(&def);
+  const ww_params* p = params ? params : &def;
+  if (!ifg || !coh || !lut || !costs || m < 2 || n < 2) return WW_ERR_INVALID_ARG;
+  if (m > kNoAllocMaxPixels || n > kNoAllocMaxPixels || m * n > kNoAllocMaxPixels) return WW_ERR_INVALID_ARG;
+  if (p->box_half_width < 0 || p->box_half_width > CW || p->steep_cap_ppm < 0 || p->steep_cap_ppm > 1000000)
+    return WW_ERR_INVALID_ARG;
+  unsigned char* base = nullptr;
+  ww_status st = noalloc_scratch(&base);
+  if (st != WW_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int16_t* dtable = reinterpret_cast<int16_t*>(base);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base + kNoAllocHistOff);
+  SteepCtr* ctr = reinterpret_cast<SteepCtr*>(base + kNoAllocCtrOff);
+  uint32_t* blocksum = reinterpret_cast<uint32_t*>(base + kNoAllocBlocksumOff);
+  const int c = is_complex ? 1 : 0;
+  // every call shares the array: copy this call's table, clear what starts at zero
+  WW_CUDA_TRY(cudaMemcpyAsync(dtable, lut_host_table(lut), kNoAllocTableBytes, cudaMemcpyHostToDevice, s));
+  WW_CUDA_TRY(cudaMemsetAsync(hist, 0, 65536 * sizeof(uint32_t), s));
+  WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
+  dim3 grid((unsigned)((n + CTX - 1) / CTX), (unsigned)((m + CTY - 1) / CTY));
+  k_costs<<<grid, 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad, costs, ctr);
+  k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
+  const int hist_blocks = 148 * 8;
+  k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, hist, 0);
+  k_steep_find<<<1, kFindThreads, 0, s>>>(ctr, hist, 0);
+  k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, hist, 1);
+  k_steep_find<<<1, kFindThreads, 0, s>>>(ctr, hist, 1);
+  const int64_t nb = (2 * m * n + kSteepChunk - 1) / kSteepChunk;
+  k_steep_ties<<<(unsigned)nb, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum);
+  k_steep_scan<<<1, kFindThreads, 0, s>>>(ctr, blocksum, nb);
+  k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum, costs);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}

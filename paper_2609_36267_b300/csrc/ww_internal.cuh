@@ -198,6 +198,7 @@ namespace ww {
 int lut_build_host(double nlooks, int16_t* table, double* cost100);
 // ww_api.cu
 const int16_t* lut_device_table(const ww_lut* lut, cudaStream_t stream, ww_status* st);
+const int16_t* lut_host_table(const ww_lut* lut);
 // ww_grid.cu
 ww_status launch_residues(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                           int64_t m, int64_t n, int8_t* res, int32_t* ground, cudaStream_t s);
