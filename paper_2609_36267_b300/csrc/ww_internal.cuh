@@ -164,7 +164,7 @@ struct ww_workspace {
   int32_t* cand2;      // [N]
   int32_t* cand_root;  // [N]
   int32_t* tile_stamp; // [T] search worklist: 1 while a tile is queued
-  int32_t* tile_list[2]; // [0]: worklist ring slots (tile+1, 0 = empty); [1] spare
+  int32_t* tile_list[2]; // [0]: worklist ring slots (tile+1, 0 = empty); [1]: per-tile "dropped at cap" flags
   void* search_q;      // worklist head/tail/pending counters
   void* counters;      // device counters block
   void* host_counters; // pinned host mirror
@@ -185,6 +185,7 @@ struct ww_workspace {
   // statistics of the last solve
   ww_solve_stats stats;
   int32_t epoch;
+  uint32_t last_D;     // largest augmented distance of the previous pass
 };
 
 #define WW_CUDA_TRY(expr)                          \

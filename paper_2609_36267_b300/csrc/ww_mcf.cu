@@ -32,6 +32,8 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "ww_internal.cuh"
@@ -59,6 +61,8 @@ struct McfCtr {
   long long total_cost;
   unsigned long long local_rounds;
   unsigned long long visit_cycles;
+  int32_t found;       // candidates reached by the current search
+  int32_t capped_any;  // a tile discarded a candidate at or beyond the cap
 };
 
 namespace {
@@ -166,46 +170,72 @@ __device__ __forceinline__ uint64_t arc_weight(uint32_t w) {
   return w == kNoArc ? KINF : (((uint64_t)w << 29) + 1ull);  // +w distance, +1 hop
 }
 
-// One directional min-plus scan over 32 cells held one per lane:
-//   c_k = min(K_k, c_{k-1} + b_k), c_{-1} = halo, k in scan order,
-// then every cell takes the candidate from its predecessor in scan order
-// (direction code dir) if that beats its label.  Returns true if any changed.
-template <bool DOWNWARD>
-__device__ __forceinline__ bool scan_line(uint64_t* cell, uint64_t halo_key, uint32_t wraw, int dir, int lane,
-                                          int* err) {
-  const uint64_t lab = *cell;
-  const uint64_t K = lab >> 3;
-  const uint64_t b = arc_weight(wraw);
-  const uint64_t h = halo_key >> 3;
-  uint64_t A = K, B = b;
-  const bool first = DOWNWARD ? lane == 0 : lane == 31;
-  if (first) A = min(A, sat_add(h, b));
+// Segmented directional min-plus scan over four 32-cell lines per warp.
+// Lane = 8*line + seg; seg owns cells 4*seg .. 4*seg+3 of its line (in scan
+// order when forward, mirrored when backward).  For one line with cells k in
+// scan order, labels K_k (distance,hops) and entering-arc weights b_k:
+//   c_k = min(K_k, c_{k-1} + b_k),  c_{-1} = halo,
+// computed as a sequential pass inside each segment, an exclusive scan of the
+// segment aggregates (A, B) across the 8 segments (operator
+// (A1,B1).(A2,B2) = (min(A2, A1+B2), B1+B2)), and a sequential fix-up that
+// offers every cell the candidate from its predecessor (direction code dir).
+// `cell(k)` / `wt(k)` address the lane's k-th cell in scan order.
+template <bool FORWARD, class CellF, class WtF>
+__device__ __forceinline__ unsigned scan_segments(CellF cell, WtF wt, uint64_t halo_key, int dir, int seg,
+                                                  uint64_t capK, bool* capped, int* err) {
+  uint64_t K[4], b[4];
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    uint64_t Ap = DOWNWARD ? __shfl_up_sync(0xffffffffu, A, off) : __shfl_down_sync(0xffffffffu, A, off);
-    uint64_t Bp = DOWNWARD ? __shfl_up_sync(0xffffffffu, B, off) : __shfl_down_sync(0xffffffffu, B, off);
-    bool has = DOWNWARD ? lane >= off : lane + off < 32;
+  for (int k = 0; k < 4; ++k) {
+    K[k] = *cell(k) >> 3;
+    b[k] = arc_weight(wt(k));
+  }
+  uint64_t A = K[0], B = b[0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    A = min(K[k], sat_add(A, b[k]));
+    B = sat_add(B, b[k]);
+  }
+  const uint64_t h = halo_key >> 3;
+  const bool first = FORWARD ? seg == 0 : seg == 7;
+  if (first) A = min(A, sat_add(h, B));
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) {
+    uint64_t Ap = FORWARD ? __shfl_up_sync(0xffffffffu, A, off, 8) : __shfl_down_sync(0xffffffffu, A, off, 8);
+    uint64_t Bp = FORWARD ? __shfl_up_sync(0xffffffffu, B, off, 8) : __shfl_down_sync(0xffffffffu, B, off, 8);
+    bool has = FORWARD ? seg >= off : seg + off < 8;
     if (has) {
       A = min(A, sat_add(Ap, B));
       B = sat_add(Bp, B);
     }
   }
-  uint64_t prev = DOWNWARD ? __shfl_up_sync(0xffffffffu, A, 1) : __shfl_down_sync(0xffffffffu, A, 1);
-  if (first) prev = h;
-  uint64_t cand = sat_add(prev, b);
-  bool ch = false;
-  if (cand < KINF) {
-    if (cand >= KDIST_INF) {
-      *err |= kErrOverflow;
-    } else {
-      uint64_t key = (cand << 3) | (uint64_t)dir;
-      if (key < lab) {
-        *cell = key;
-        ch = true;
+  uint64_t cin = FORWARD ? __shfl_up_sync(0xffffffffu, A, 1, 8) : __shfl_down_sync(0xffffffffu, A, 1, 8);
+  if (first) cin = h;
+  unsigned changed = 0;
+  uint64_t prev = cin;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint64_t cand = sat_add(prev, b[k]);
+    uint64_t cur = K[k];
+    if (cand < KINF) {
+      if (cand >= KDIST_INF) {
+        *err |= kErrOverflow;
+      } else if (cand >= capK) {
+        // beyond this search's distance band: dropped, the tile is re-seeded
+        // if the band is widened
+        if (cand < cur) *capped = true;
+      } else {
+        uint64_t* c = cell(k);
+        uint64_t key = (cand << 3) | (uint64_t)dir;
+        if (key < *c) {
+          *c = key;
+          changed |= 1u << k;
+        }
+        cur = min(cur, cand);
       }
     }
+    prev = cur;
   }
-  return ch;
+  return changed;  // bit k: the lane's k-th cell (scan order) improved
 }
 
 constexpr int LROW = TS + 3;  // padded row stride of the label tile (halo 1 each side + 1 pad)
@@ -215,16 +245,22 @@ template <bool FWD>
 __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t* __restrict__ costs,
                                                            const int8_t* __restrict__ flows,
                                                            const int64_t* __restrict__ pot, uint64_t* labels,
-                                                           SearchQ* q, int32_t* slots, int32_t* inq, McfCtr* ctr) {
+                                                           SearchQ* q, int32_t* slots, int32_t* inq, McfCtr* ctr,
+                                                           uint64_t capK, int32_t* capped_flag) {
   __shared__ uint64_t lab[TSH][LROW];
   __shared__ uint32_t rc[4][TS][RCOL];
   __shared__ int side[4];
   __shared__ int s_tile;
+  __shared__ unsigned rowdirty, coldirty, rowdirty_next, coldirty_next;
   const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;  // 8 warps; a warp owns rows/cols warp + 8k
+  const int lane = tid & 31, warp = tid >> 5;  // 8 warps
   const int ring = g.tiles_x * g.tiles_y + (int)gridDim.x + 64;
   const int64_t pG = pot[g.N];
   int err = 0;
+  if (tid == 0) {
+    rowdirty_next = 0;
+    coldirty_next = 0;
+  }
   for (;;) {
     if (tid == 0) s_tile = q_pop(ring, q, slots, inq);
     __syncthreads();
@@ -282,30 +318,82 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
 #pragma unroll
     for (int k = 0; k < 4; ++k) orig[k] = lab[warp + 8 * k + 1][lane + 1];
     // local fixed point by directional scans: rows left->right and right->left,
-    // then columns top->bottom and bottom->top, until nothing changes
+    // then columns top->bottom and bottom->top; a line is rescanned only if a
+    // scan in the other orientation changed one of its cells (all start dirty)
+    if (tid == 0) {
+      rowdirty = 0xFFFFFFFFu;
+      coldirty = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    const int grp = lane >> 3, seg = lane & 7;
+    bool capped = false;
     int round = 0;
     for (; round < kMaxLocalSweeps; ++round) {
-      bool ch = false;
+      // rows 4*warp + grp; this lane holds columns 4*seg..4*seg+3
+      const unsigned rd = rowdirty;
+      const int r = 4 * warp + grp;
+      unsigned chr = 0;
+      if ((rd >> (4 * warp)) & 0xFu) {
+        uint64_t* rowp = &lab[r + 1][0];
+        const uint32_t* wl = &rc[kDirLeft - 1][r][0];
+        const uint32_t* wr = &rc[kDirRight - 1][r][0];
+        unsigned f = scan_segments<true>([&](int k) { return rowp + 1 + 4 * seg + k; },
+                                         [&](int k) { return wl[4 * seg + k]; }, rowp[0], kDirLeft, seg, capK,
+                                         &capped, &err);
+        unsigned bk = scan_segments<false>([&](int k) { return rowp + 1 + 4 * seg + 3 - k; },
+                                           [&](int k) { return wr[4 * seg + 3 - k]; }, rowp[TS + 1], kDirRight, seg,
+                                           capK, &capped, &err);
+        // columns touched: bit k of f is column 4seg+k, bit k of bk is column 4seg+3-k
+        unsigned cols = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        int r = warp + 8 * k;  // node row
-        uint64_t* cell = &lab[r + 1][lane + 1];
-        ch |= scan_line<true>(cell, lab[r + 1][0], rc[kDirLeft - 1][r][lane], kDirLeft, lane, &err);
-        __syncwarp();
-        ch |= scan_line<false>(cell, lab[r + 1][TS + 1], rc[kDirRight - 1][r][lane], kDirRight, lane, &err);
-        __syncwarp();
+        for (int k = 0; k < 4; ++k) {
+          if ((f >> k) & 1u) cols |= 1u << (4 * seg + k);
+          if ((bk >> k) & 1u) cols |= 1u << (4 * seg + 3 - k);
+        }
+        chr = cols;
       }
       __syncthreads();
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        int c = warp + 8 * k;  // node column; lane = node row
-        uint64_t* cell = &lab[lane + 1][c + 1];
-        ch |= scan_line<true>(cell, lab[0][c + 1], rc[kDirUp - 1][lane][c], kDirUp, lane, &err);
-        __syncwarp();
-        ch |= scan_line<false>(cell, lab[TS + 1][c + 1], rc[kDirDown - 1][lane][c], kDirDown, lane, &err);
-        __syncwarp();
+      if (tid == 0) rowdirty = 0;
+      // reduce the changed-column masks of the block
+      unsigned cm = __reduce_or_sync(0xffffffffu, chr);
+      if (lane == 0 && cm) atomicOr(&coldirty_next, cm);
+      __syncthreads();
+      if (tid == 0) {
+        coldirty |= coldirty_next;
+        coldirty_next = 0;
       }
-      if (!__syncthreads_or(ch)) break;
+      __syncthreads();
+      const unsigned cd = coldirty;
+      const int c = 4 * warp + grp;
+      unsigned chc = 0;
+      if ((cd >> (4 * warp)) & 0xFu) {
+        const uint32_t* wu = &rc[kDirUp - 1][0][c];
+        const uint32_t* wd = &rc[kDirDown - 1][0][c];
+        unsigned f = scan_segments<true>([&](int k) { return &lab[4 * seg + k + 1][c + 1]; },
+                                         [&](int k) { return wu[(4 * seg + k) * RCOL]; }, lab[0][c + 1], kDirUp,
+                                         seg, capK, &capped, &err);
+        unsigned bk = scan_segments<false>([&](int k) { return &lab[4 * seg + 3 - k + 1][c + 1]; },
+                                           [&](int k) { return wd[(4 * seg + 3 - k) * RCOL]; }, lab[TS + 1][c + 1],
+                                           kDirDown, seg, capK, &capped, &err);
+        unsigned rows = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if ((f >> k) & 1u) rows |= 1u << (4 * seg + k);
+          if ((bk >> k) & 1u) rows |= 1u << (4 * seg + 3 - k);
+        }
+        chc = rows;
+      }
+      __syncthreads();
+      if (tid == 0) coldirty = 0;
+      unsigned rm = __reduce_or_sync(0xffffffffu, chc);
+      if (lane == 0 && rm) atomicOr(&rowdirty_next, rm);
+      __syncthreads();
+      if (tid == 0) {
+        rowdirty = rowdirty_next;
+        rowdirty_next = 0;
+      }
+      __syncthreads();
+      if (rowdirty == 0) break;
     }
     // write back and note which tile sides changed
 #pragma unroll
@@ -322,6 +410,10 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
         if (lane == 0) side[2] = 1;
         if (lane == TS - 1) side[3] = 1;
       }
+    }
+    if (__syncthreads_or(capped) && tid == 0) {
+      capped_flag[tile] = 1;
+      ctr->capped_any = 1;
     }
     __threadfence();
     __syncthreads();
@@ -387,6 +479,33 @@ __global__ void k_seed_tiles(Grid g, const int32_t* excess, const int32_t* cand,
     }
     if (!q_push(tile, ring, q, slots, inq)) atomicOr(&ctr_err(ctr), kErrSpin);
   }
+}
+
+// Widen the distance band: queue every tile that dropped a candidate.
+__global__ void k_reseed(Grid g, int32_t* capped_flag, SearchQ* q, int32_t* slots, int32_t* inq, int search_grid,
+                         McfCtr* ctr) {
+  const int T = g.tiles_x * g.tiles_y;
+  const int ring = T + search_grid + 64;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    if (capped_flag[t]) {
+      capped_flag[t] = 0;
+      if (!q_push(t, ring, q, slots, inq)) atomicOr(&ctr->err, kErrSpin);
+    }
+  }
+}
+
+// Candidates (deficits forward, excess nodes reverse) the search has reached.
+template <bool FWD>
+__global__ void k_count_found(const int32_t* excess, const uint64_t* labels, const int32_t* cand, McfCtr* ctr) {
+  const int nc = ctr->ncand;
+  int c = 0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+    int32_t t = cand[q];
+    int32_t e = excess[t];
+    if ((FWD ? e < 0 : e > 0) && labels[t] != kInf) ++c;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->found, c);
 }
 
 // Walk from v along the forest to its root.  Returns the root, or -1 on a walk
@@ -528,6 +647,15 @@ __global__ void k_write_result(const McfCtr* ctr, const int32_t* ground, int32_t
   *total_cost = ctr->total_cost;
 }
 
+bool trace_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("WW_TRACE");
+    on = (e && e[0] == '1') ? 1 : 0;
+  }
+  return on == 1;
+}
+
 int grid_blocks(int64_t work, int threads, int cap) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -564,6 +692,7 @@ ww_status solver_alloc(ww_workspace* ws, int64_t m, int64_t n) {
   // queue flags and ring slots start (and end every search) all zero
   if (cudaMemset(ws->tile_stamp, 0, tiles * 4) != cudaSuccess) return WW_ERR_CUDA;
   if (cudaMemset(ws->tile_list[0], 0, (tiles + kMaxSearchGrid + 64) * 4) != cudaSuccess) return WW_ERR_CUDA;
+  if (cudaMemset(ws->tile_list[1], 0, tiles * 4) != cudaSuccess) return WW_ERR_CUDA;
   ws->epoch = 0;
   return WW_OK;
 }
@@ -587,10 +716,14 @@ void solver_free(ww_workspace* ws) {
 }
 
 // One multi-root search: labels reset, worklist seeded with root and border
-// tiles, then one persistent launch drains the worklist to the fixed point.
+// tiles, then persistent launches drain the worklist to the fixed point below a
+// distance cap.  Nodes whose true distance is below the cap end with exact
+// labels.  If no candidate was reached and some tile dropped candidates at the
+// cap, the cap grows (x8) and the search resumes from those tiles.
 template <bool FWD>
 static ww_status run_search(const Grid& g, const int16_t* costs, const int8_t* flows, const int64_t* pot,
-                            ww_workspace* ws, McfCtr* dctr, int sm_count, cudaStream_t s) {
+                            ww_workspace* ws, McfCtr* dctr, McfCtr* hctr, uint64_t cap, int sm_count,
+                            cudaStream_t s) {
   const int nb_nodes = grid_blocks(g.N, 256, sm_count * 16);
   k_init_labels<FWD><<<nb_nodes, 256, 0, s>>>(g, ws->excess, ws->labels);
   SearchQ* q = reinterpret_cast<SearchQ*>(ws->search_q);
@@ -602,12 +735,31 @@ static ww_status run_search(const Grid& g, const int16_t* costs, const int8_t* f
   k_seed_tiles<FWD><<<grid_blocks(g.N / 64 + 1024, 256, sm_count * 4), 256, 0, s>>>(
       g, ws->excess, ws->cand, dctr, q, ws->tile_list[0], ws->tile_stamp, search_grid);
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
-  WW_CUDA_TRY(cudaEventRecord(ev[0], s));
-  k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(g, costs, flows, pot, ws->labels, q, ws->tile_list[0],
-                                                            ws->tile_stamp, dctr);
-  WW_CUDA_TRY(cudaEventRecord(ev[1], s));
-  WW_CUDA_TRY(cudaGetLastError());
-  ++ws->stats.search_iterations;
+  const int T = g.tiles_x * g.tiles_y;
+  float ms_total = 0.0f;
+  for (int band = 0; band < 64; ++band) {
+    const uint64_t capK = cap >= 0xFFFFFFFFull ? KINF : (cap << 29);
+    WW_CUDA_TRY(cudaMemsetAsync(&dctr->found, 0, 2 * sizeof(int32_t), s));  // found, capped_any
+    WW_CUDA_TRY(cudaEventRecord(ev[0], s));
+    k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(g, costs, flows, pot, ws->labels, q, ws->tile_list[0],
+                                                         ws->tile_stamp, dctr, capK, ws->tile_list[1]);
+    WW_CUDA_TRY(cudaEventRecord(ev[1], s));
+    WW_CUDA_TRY(cudaGetLastError());
+    ++ws->stats.search_iterations;
+    if (capK == KINF) break;
+    k_count_found<FWD><<<grid_blocks(hctr->ncand > 0 ? hctr->ncand : 1, 256, sm_count * 8), 256, 0, s>>>(
+        ws->excess, ws->labels, ws->cand, dctr);
+    WW_CUDA_TRY(cudaMemcpyAsync(&hctr->found, &dctr->found, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    WW_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hctr->found > 0 || !hctr->capped_any) break;  // the pass adds this last launch's time
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) ms_total += ms;
+    cap = cap >= (0xFFFFFFFFull >> 3) ? 0xFFFFFFFFull : cap * 8;
+    WW_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(SearchQ), s));
+    k_reseed<<<grid_blocks(T, 256, sm_count * 8), 256, 0, s>>>(g, ws->tile_list[1], q, ws->tile_list[0],
+                                                                 ws->tile_stamp, search_grid, dctr);
+  }
+  ws->stats.ms_search_gpu += ms_total;  // earlier bands; the pass adds the last launch
   return WW_OK;
 }
 
@@ -615,7 +767,10 @@ template <bool FWD>
 static ww_status run_pass(const Grid& g, const int16_t* costs, int8_t* flows, int64_t* pot, ww_workspace* ws,
                           McfCtr* dctr, McfCtr* hctr, const ww_params* p, int sm_count, cudaStream_t s) {
   auto t0 = std::chrono::steady_clock::now();
-  ww_status st = run_search<FWD>(g, costs, flows, pot, ws, dctr, sm_count, s);
+  // full search while many roots remain; distance bands once only a few are left
+  uint64_t cap = 0xFFFFFFFFull;
+  if (ws->stats.passes >= 2 && hctr->ncand * 1000ll < g.N) cap = std::max<uint64_t>(4096, 4ull * ws->last_D);
+  ww_status st = run_search<FWD>(g, costs, flows, pot, ws, dctr, hctr, cap, sm_count, s);
   if (st != WW_OK) return st;
   const int nb = grid_blocks(hctr->ncand > 0 ? hctr->ncand : g.N, 256, sm_count * 16);
   WW_CUDA_TRY(cudaMemsetAsync(&dctr->D, 0, 2 * sizeof(int32_t), s));  // D, naug
@@ -632,6 +787,13 @@ static ww_status run_pass(const Grid& g, const int16_t* costs, int8_t* flows, in
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) ws->stats.ms_search_gpu += ms;
+  if (hctr->naug > 0) ws->last_D = hctr->D;
+  if (trace_enabled())
+    std::fprintf(stderr, "[ww] pass %lld %s: cap %llu, last search %.3f ms, augment %d (D %u), left %d, "
+                 "tile visits %llu, rounds %llu\n",
+                 (long long)ws->stats.passes, FWD ? "fwd" : "rev", (unsigned long long)cap, ms, hctr->naug, hctr->D,
+                 hctr->ncand,
+                 (unsigned long long)hctr->tile_visits, (unsigned long long)hctr->local_rounds);
   ws->stats.ms_other += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return WW_OK;
 }
@@ -654,6 +816,7 @@ ww_status solve_mcf(const int8_t* res, const int32_t* ground, const int16_t* cos
   McfCtr* dctr = reinterpret_cast<McfCtr*>(ws->counters);
   McfCtr* hctr = reinterpret_cast<McfCtr*>(ws->host_counters);
   ws->stats = ww_solve_stats{};
+  ws->last_D = 0;
   WW_CUDA_TRY(cudaMemsetAsync(dctr, 0, sizeof(McfCtr), s));
   WW_CUDA_TRY(cudaMemsetAsync(flows, 0, 2 * g.P, s));
   WW_CUDA_TRY(cudaMemsetAsync(pot, 0, (g.N + 1) * sizeof(int64_t), s));
@@ -674,6 +837,7 @@ ww_status solve_mcf(const int8_t* res, const int32_t* ground, const int16_t* cos
     st = fwd ? run_pass<true>(g, costs, flows, pot, ws, dctr, hctr, p, sm_count, s)
              : run_pass<false>(g, costs, flows, pot, ws, dctr, hctr, p, sm_count, s);
     ++pass;
+    ws->stats.passes = pass;
     if (st != WW_OK) break;
     ws->stats.augmentations += hctr->naug;
     if (hctr->err) break;
