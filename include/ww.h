@@ -189,6 +189,38 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
                     ww_workspace* ws, float* unwrapped, int32_t* cycles, int64_t* total_cost,
                     ww_stream stream);
 
+/* ---- Batched form: many uneven interferograms in one solve ----
+ * Each item is one unwrap request (device pointers; outputs unwrapped/cycles are
+ * m x n).  All items are solved together: their node grids are independent
+ * (no arcs between items) and they share one free ground node, which leaves
+ * each item's optimum unchanged because every item's supplies sum to zero.
+ * One persistent search launch per pass covers the tiles of all unfinished
+ * items.  Residues, costs and integration run per item on the same stream.
+ * On return total_cost and status are filled in for every item. */
+typedef struct ww_batch_item {
+  const void* ifg;        /* float32 phase or interleaved complex64 [m][n] */
+  int32_t is_complex;
+  const float* coh;       /* [m][n] */
+  const uint8_t* mask;    /* [m][n] or NULL */
+  int64_t m, n;
+  double nlooks;
+  float* unwrapped;       /* out [m][n] */
+  int32_t* cycles;        /* out [m][n] */
+  int64_t total_cost;     /* out (host field) */
+  int32_t status;         /* out (host field) */
+} ww_batch_item;
+
+typedef struct ww_batch ww_batch;  /* library-owned device scratch for batches */
+/* Capacity: up to max_items items with at most max_pixels pixels in total and
+ * max_item_pixels pixels in the largest item. */
+ww_status ww_batch_create(int64_t max_items, int64_t max_pixels, int64_t max_item_pixels, ww_batch** out);
+void ww_batch_free(ww_batch* b);
+int64_t ww_batch_bytes(int64_t max_items, int64_t max_pixels, int64_t max_item_pixels);
+/* Synchronises the stream; returns the first non-OK item status, else WW_OK. */
+ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* params, ww_batch* b,
+                          ww_stream stream);
+ww_status ww_batch_stats(const ww_batch* b, ww_solve_stats* out);
+
 /* ---- Harness: optimality certificate on the GPU ----
  * Counts violations into counts (device int64[4]): [0] |dk|>1 or flow on a
  * non-existent edge, [1] nodes (G included) whose out-in flow differs from the

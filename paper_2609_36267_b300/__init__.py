@@ -57,6 +57,13 @@ class SolveStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("ifg", ctypes.c_void_p), ("is_complex", ctypes.c_int32), ("coh", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nlooks", ctypes.c_double),
+                ("unwrapped", ctypes.c_void_p), ("cycles", ctypes.c_void_p), ("total_cost", ctypes.c_int64),
+                ("status", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -89,9 +96,15 @@ def lib():
         L.ww_unwrap.argtypes = [P, i32, P, d, P, i64, i64, ctypes.POINTER(Params), P, P, P,
                                 ctypes.POINTER(i64), P]
         L.ww_certificate.argtypes = [P, P, P, P, P, i64, i64, P, P]
+        L.ww_batch_create.argtypes = [i64, i64, i64, ctypes.POINTER(P)]
+        L.ww_batch_free.argtypes = [P]
+        L.ww_batch_bytes.argtypes = [i64, i64, i64]
+        L.ww_batch_bytes.restype = i64
+        L.ww_unwrap_batch.argtypes = [ctypes.POINTER(BatchItem), i64, ctypes.POINTER(Params), P, P]
+        L.ww_batch_stats.argtypes = [P, ctypes.POINTER(SolveStats)]
         for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
                   "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_get_solve_stats", "ww_integrate", "ww_unwrap",
-                  "ww_certificate"):
+                  "ww_certificate", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -316,3 +329,60 @@ def certificate(res, ground, cost_planes, flows, potentials):
     _check(lib().ww_certificate(_ptr(res), _ptr(ground), _ptr(cost_planes), _ptr(flows), _ptr(potentials), m, n,
                                 _ptr(counts), _stream()), "ww_certificate")
     return tuple(int(x) for x in counts.cpu())
+
+
+class Batch:
+    """Device scratch for batched unwraps (up to max_items items, max_pixels in total)."""
+
+    def __init__(self, max_items: int, max_pixels: int, max_item_pixels: int | None = None):
+        h = ctypes.c_void_p()
+        mip = max_item_pixels or max_pixels
+        _check(lib().ww_batch_create(int(max_items), int(max_pixels), int(mip), ctypes.byref(h)), "ww_batch_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        st = SolveStats()
+        _check(lib().ww_batch_stats(self._h, ctypes.byref(st)), "ww_batch_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().ww_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unwrap_batch(requests, batch: Batch | None = None, params: Params | None = None, check=True):
+    """requests: list of (ifg, coh, nlooks, mask) device tensors.  Returns a list
+    of (unwrapped, cycles, total_cost, status) in the same order."""
+    torch = _torch()
+    outs = []
+    arr = (BatchItem * len(requests))()
+    total = 0
+    biggest = 0
+    for k, (ifg, coh, nlooks, mask) in enumerate(requests):
+        m, n = ifg.shape
+        unw = torch.empty((m, n), dtype=torch.float32, device=ifg.device)
+        cyc = torch.empty((m, n), dtype=torch.int32, device=ifg.device)
+        p, c = _ifg(ifg)
+        arr[k] = BatchItem(p.value, c, _ptr(coh).value, _ptr(mask).value if mask is not None else None, m, n,
+                           float(nlooks), unw.data_ptr(), cyc.data_ptr(), 0, 0)
+        outs.append((unw, cyc))
+        total += m * n
+        biggest = max(biggest, m * n)
+    if batch is None:
+        batch = Batch(len(requests), total, biggest)
+    prm = params or default_params()
+    st = lib().ww_unwrap_batch(arr, len(requests), ctypes.byref(prm), batch.handle, _stream())
+    if check:
+        _check(st, "ww_unwrap_batch")
+    return [(u, k, arr[i].total_cost, arr[i].status) for i, (u, k) in enumerate(outs)]

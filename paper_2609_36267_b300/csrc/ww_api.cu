@@ -7,6 +7,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <vector>
 
 #include "ww_internal.cuh"
 
@@ -174,7 +175,7 @@ int64_t ww_workspace_bytes(int64_t m, int64_t n) {
   int64_t P = m * n, N = (m - 1) * (n - 1);
   int64_t grid = N /*residues*/ + 4 * P * 2 /*costs*/ + 2 * P /*flows*/ + (N + 1) * 8 /*potentials*/ + 64;
   int64_t steep = 65536 * 4 + 64 + ((2 * P + 1023) / 1024) * 4;
-  return grid + steep + ww::solver_bytes(m, n);
+  return grid + steep + ww::solver_bytes(N, ww::tiles_for(m, n), 1);
 }
 
 ww_status ww_workspace_create(int64_t max_rows, int64_t max_cols, ww_workspace** out) {
@@ -194,7 +195,7 @@ ww_status ww_workspace_create(int64_t max_rows, int64_t max_cols, ww_workspace**
             cudaMalloc(&ws->hist, 65536 * 4) == cudaSuccess && cudaMalloc(&ws->steep_ctr, 64) == cudaSuccess &&
             cudaMalloc(&ws->blocksum, ws->blocksum_len * 4) == cudaSuccess;
   if (ok) ok = cudaMemset(ws->hist, 0, 65536 * 4) == cudaSuccess;
-  ww_status st = ok ? ww::solver_alloc(ws, m, n) : WW_ERR_OOM;
+  ww_status st = ok ? ww::solver_alloc(&ws->sv, N, ww::tiles_for(m, n), 1) : WW_ERR_OOM;
   if (st != WW_OK) {
     cudaGetLastError();
     ww_workspace_free(ws);
@@ -216,7 +217,7 @@ void ww_workspace_free(ww_workspace* ws) {
   cudaFree(ws->hist);
   cudaFree(ws->steep_ctr);
   cudaFree(ws->blocksum);
-  ww::solver_free(ws);
+  ww::solver_free(&ws->sv);
   delete ws;
 }
 
@@ -252,8 +253,8 @@ ww_status ww_solve_mcf(const int8_t* residues, const int32_t* ground, const int1
   if (!residues || !ground || !costs || !flows || !potentials || !total_cost || !dev_status || !grid_ok(m, n) ||
       !params_ok(p) || !fits(ws, m, n))
     return WW_ERR_INVALID_ARG;
-  return ww::solve_mcf(residues, ground, costs, m, n, p, ws, flows, potentials, total_cost, dev_status,
-                       (cudaStream_t)stream);
+  ww::ProbHost ph{m, n, residues, ground, costs, flows, nullptr, total_cost, dev_status};
+  return ww::solve_problems(&ph, 1, &ws->sv, p, potentials, &ws->stats, (cudaStream_t)stream);
 }
 
 ww_status ww_get_solve_stats(const ww_workspace* ws, ww_solve_stats* out) {
@@ -290,9 +291,10 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
   const int c = is_complex ? 1 : 0;
   st = ww::launch_residues(ifg, c, coh, mask, m, n, ws->residues, ws->ground, s);
   if (st == WW_OK) st = ww::launch_costs(ifg, c, coh, mask, m, n, dt, p, ws, ws->costs, s);
-  if (st == WW_OK)
-    st = ww::solve_mcf(ws->residues, ws->ground, ws->costs, m, n, p, ws, ws->flows, ws->potentials,
-                       ws->total_cost, ws->dev_status, s);
+  if (st == WW_OK) {
+    ww::ProbHost ph{m, n, ws->residues, ws->ground, ws->costs, ws->flows, nullptr, ws->total_cost, ws->dev_status};
+    st = ww::solve_problems(&ph, 1, &ws->sv, p, ws->potentials, &ws->stats, s);
+  }
   ww_status st2 = ww::launch_integrate(ifg, c, coh, mask, ws->flows, m, n, unwrapped, cycles, s);
   if (st == WW_OK) st = st2;
   if (total_cost && cudaMemcpyAsync(total_cost, ws->total_cost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -307,6 +309,164 @@ ww_status ww_certificate(const int8_t* residues, const int32_t* ground, const in
   if (!residues || !ground || !costs || !flows || !potentials || !counts || !grid_ok(m, n))
     return WW_ERR_INVALID_ARG;
   return ww::launch_certificate(residues, ground, costs, flows, potentials, m, n, counts, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---------------- batched form ----------------
+struct ww_batch {
+  int device;
+  int64_t max_items, max_pixels, max_item_pixels;
+  ww::SolverWs sv;
+  int8_t* residues;     // concatenated per item
+  int32_t* ground;      // [max_items]
+  int16_t* costs;       // [4 * max_pixels]
+  int8_t* flows;        // [2 * max_pixels]
+  int64_t* total_cost;  // [max_items]
+  int32_t* status;      // [max_items]
+  // steep selection scratch, reused item after item (stream-ordered)
+  ww_workspace steep;
+  ww_solve_stats stats;
+};
+
+// Tiles of an m x n item: ceil((m-1)/32) ceil((n-1)/32) <= P/1024 + (m+n)/32 + 1, and
+// m + n <= P/2 + 2 for m, n >= 2, so a batch needs at most P/1024 + P/64 + 2 per item.
+static int64_t batch_tiles(int64_t items, int64_t pixels) { return pixels / 1024 + pixels / 64 + 4 * items + 64; }
+
+extern "C" {
+
+int64_t ww_batch_bytes(int64_t max_items, int64_t max_pixels, int64_t max_item_pixels) {
+  if (max_items < 1 || max_pixels < 4 || max_item_pixels < 4) return -1;
+  int64_t tiles = batch_tiles(max_items, max_pixels);
+  return max_pixels * (1 + 8 + 2) + max_items * 16 + 65536 * 4 + 64 + ((2 * max_item_pixels + 1023) / 1024) * 4 +
+         ww::solver_bytes(max_pixels, tiles, max_items);
+}
+
+ww_status ww_batch_create(int64_t max_items, int64_t max_pixels, int64_t max_item_pixels, ww_batch** out) {
+  if (!out || max_items < 1 || max_pixels < 4 || max_item_pixels < 4 || max_item_pixels > max_pixels)
+    return WW_ERR_INVALID_ARG;
+  ww_batch* b = new (std::nothrow) ww_batch;
+  if (!b) return WW_ERR_OOM;
+  std::memset(b, 0, sizeof(*b));
+  cudaGetDevice(&b->device);
+  b->max_items = max_items;
+  b->max_pixels = max_pixels;
+  b->max_item_pixels = max_item_pixels;
+  const int64_t tiles = batch_tiles(max_items, max_pixels);
+  b->steep.blocksum_len = (2 * max_item_pixels + 1023) / 1024;
+  bool ok = cudaMalloc(&b->residues, max_pixels) == cudaSuccess &&
+            cudaMalloc(&b->ground, max_items * 4) == cudaSuccess &&
+            cudaMalloc(&b->costs, 4 * max_pixels * 2) == cudaSuccess &&
+            cudaMalloc(&b->flows, 2 * max_pixels) == cudaSuccess &&
+            cudaMalloc(&b->total_cost, max_items * 8) == cudaSuccess &&
+            cudaMalloc(&b->status, max_items * 4) == cudaSuccess &&
+            cudaMalloc(&b->steep.hist, 65536 * 4) == cudaSuccess && cudaMalloc(&b->steep.steep_ctr, 64) == cudaSuccess &&
+            cudaMalloc(&b->steep.blocksum, b->steep.blocksum_len * 4) == cudaSuccess;
+  if (ok) ok = cudaMemset(b->steep.hist, 0, 65536 * 4) == cudaSuccess;
+  ww_status st = ok ? ww::solver_alloc(&b->sv, max_pixels, tiles, max_items) : WW_ERR_OOM;
+  if (st != WW_OK) {
+    cudaGetLastError();
+    ww_batch_free(b);
+    return st;
+  }
+  *out = b;
+  return WW_OK;
+}
+
+void ww_batch_free(ww_batch* b) {
+  if (!b) return;
+  cudaFree(b->residues);
+  cudaFree(b->ground);
+  cudaFree(b->costs);
+  cudaFree(b->flows);
+  cudaFree(b->total_cost);
+  cudaFree(b->status);
+  cudaFree(b->steep.hist);
+  cudaFree(b->steep.steep_ctr);
+  cudaFree(b->steep.blocksum);
+  ww::solver_free(&b->sv);
+  delete b;
+}
+
+ww_status ww_batch_stats(const ww_batch* b, ww_solve_stats* out) {
+  if (!b || !out) return WW_ERR_INVALID_ARG;
+  *out = b->stats;
+  return WW_OK;
+}
+
+ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* params, ww_batch* b,
+                          ww_stream stream) {
+  ww_params def;
+  ww_params_default(&def);
+  const ww_params* p = params ? params : &def;
+  if (!items || !b || count < 1 || count > b->max_items || !params_ok(p)) return WW_ERR_INVALID_ARG;
+  int64_t tot = 0;
+  for (int64_t k = 0; k < count; ++k) {
+    const ww_batch_item& it = items[k];
+    if (!it.ifg || !it.coh || !it.unwrapped || !it.cycles || !grid_ok(it.m, it.n) ||
+        it.m * it.n > b->max_item_pixels)
+      return WW_ERR_INVALID_ARG;
+    tot += it.m * it.n;
+  }
+  if (tot > b->max_pixels) return WW_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // tables per number of looks (cached by the library)
+  std::vector<ww_lut*> luts(count, nullptr);
+  std::map<uint64_t, ww_lut*> by_l;
+  ww_status st = WW_OK;
+  for (int64_t k = 0; k < count && st == WW_OK; ++k) {
+    uint64_t key = key_of(items[k].nlooks);
+    auto it = by_l.find(key);
+    if (it != by_l.end()) {
+      luts[k] = it->second;
+      continue;
+    }
+    ww_lut* l = nullptr;
+    st = ww_build_lut(items[k].nlooks, &l);
+    if (st == WW_OK) luts[k] = by_l[key] = l;
+  }
+  std::vector<ww::ProbHost> probs(count);
+  int64_t off = 0;
+  for (int64_t k = 0; k < count && st == WW_OK; ++k) {
+    const ww_batch_item& it = items[k];
+    const int c = it.is_complex ? 1 : 0;
+    const int16_t* dt = ww::lut_device_table(luts[k], s, &st);
+    if (!dt) break;
+    ww::ProbHost& ph = probs[k];
+    ph.m = it.m;
+    ph.n = it.n;
+    ph.res = b->residues + off;
+    ph.ground = b->ground + k;
+    ph.costs = b->costs + 4 * off;
+    ph.flows = b->flows + 2 * off;
+    ph.pot_out = nullptr;
+    ph.total_cost = b->total_cost + k;
+    ph.status = b->status + k;
+    st = ww::launch_residues(it.ifg, c, it.coh, it.mask, it.m, it.n, const_cast<int8_t*>(ph.res),
+                             const_cast<int32_t*>(ph.ground), s);
+    if (st == WW_OK)
+      st = ww::launch_costs(it.ifg, c, it.coh, it.mask, it.m, it.n, dt, p, &b->steep, const_cast<int16_t*>(ph.costs), s);
+    off += it.m * it.n;
+  }
+  if (st == WW_OK) st = ww::solve_problems(probs.data(), (int)count, &b->sv, p, nullptr, &b->stats, s);
+  for (int64_t k = 0; k < count; ++k) {
+    const ww_batch_item& it = items[k];
+    ww_status s2 = ww::launch_integrate(it.ifg, it.is_complex ? 1 : 0, it.coh, it.mask, probs[k].flows, it.m, it.n,
+                                        it.unwrapped, it.cycles, s);
+    if (st == WW_OK) st = s2;
+  }
+  std::vector<int64_t> tc(count);
+  std::vector<int32_t> sts(count);
+  if (cudaMemcpyAsync(tc.data(), b->total_cost, count * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(sts.data(), b->status, count * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    st = st == WW_OK ? WW_ERR_CUDA : st;
+  for (int64_t k = 0; k < count; ++k) {
+    items[k].total_cost = tc[k];
+    items[k].status = st == WW_OK ? sts[k] : st;
+  }
+  for (auto& kv : by_l) ww_lut_free(kv.second);
+  return st;
 }
 
 }  // extern "C"

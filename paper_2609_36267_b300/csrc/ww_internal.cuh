@@ -151,24 +151,53 @@ struct ww_lut {
   void* shared;  // LutData* (see ww_api.cu)
 };
 
-struct WsCounters;  // device counters for the solver (ww_mcf.cu)
+namespace ww {
+// Device state of the MCF solver for up to n_cap nodes, t_cap 32x32 tiles and
+// p_cap problems (ww_mcf.cu).
+struct SolverWs {
+  int64_t n_cap, t_cap, p_cap;
+  int32_t* excess;     // [n_cap] imbalance per node
+  uint64_t* labels;    // [n_cap] search labels (distance | hops | direction)
+  uint64_t* best;      // [n_cap] per tree root: nearest candidate (distance, id)
+  int32_t* cand;       // [2 n_cap] current / next list of imbalanced nodes
+  int32_t* cand_root;  // [n_cap]
+  int64_t* pot;        // [n_cap + 1] potentials when the caller's array is not used; last = ground
+  int32_t* inq;        // [t_cap] 1 while a tile is queued
+  int32_t* slots;      // [t_cap + ring slack] worklist ring (tile + 1, 0 = empty)
+  int32_t* capped;     // [t_cap] tile dropped a candidate at the distance cap
+  int32_t* tile_prob;  // [t_cap] tile -> problem
+  int32_t* border;     // border tiles of every problem
+  void* probs;         // ProbDev [p_cap]
+  void* host_probs;    // pinned ProbDev [p_cap]
+  int32_t* prob_left;  // [p_cap] imbalanced nodes per problem
+  long long* g_net;    // [p_cap] net units emitted by the ground node per problem
+  long long* tc;       // [p_cap] total cost per problem
+  int32_t* order;      // [p_cap] active slots by node offset
+  int32_t* slot_list;  // [p_cap] scratch list of slots for per-problem launches
+  int32_t* status_all; // [p_cap] statuses of a finalize call
+  void* ctr;           // McfCtr
+  void* q;             // SearchQ
+  void* host_ctr;      // pinned McfCtr mirror
+  void* events[2];     // search timing
+};
+
+// One problem handed to the solver (all pointers on the device).
+struct ProbHost {
+  int64_t m, n;
+  const int8_t* res;
+  const int32_t* ground;
+  const int16_t* costs;
+  int8_t* flows;
+  int64_t* pot_out;
+  int64_t* total_cost;
+  int32_t* status;
+};
+}  // namespace ww
 
 struct ww_workspace {
   int device;
   int64_t max_rows, max_cols;
-  // solver state
-  int32_t* excess;     // [N]
-  uint64_t* labels;    // [N]
-  uint64_t* best;      // [N]
-  int32_t* cand;       // [N] compact list of imbalanced nodes
-  int32_t* cand2;      // [N]
-  int32_t* cand_root;  // [N]
-  int32_t* tile_stamp; // [T] search worklist: 1 while a tile is queued
-  int32_t* tile_list[2]; // [0]: worklist ring slots (tile+1, 0 = empty); [1]: per-tile "dropped at cap" flags
-  void* search_q;      // worklist head/tail/pending counters
-  void* counters;      // device counters block
-  void* host_counters; // pinned host mirror
-  void* events[2];     // cudaEvent_t pair timing the search kernels
+  ww::SolverWs sv;
   // path scratch for ww_unwrap
   int8_t* residues;
   int32_t* ground;
@@ -184,8 +213,6 @@ struct ww_workspace {
   int64_t blocksum_len;
   // statistics of the last solve
   ww_solve_stats stats;
-  int32_t epoch;
-  uint32_t last_D;     // largest augmented distance of the previous pass
 };
 
 #define WW_CUDA_TRY(expr)                          \
@@ -210,13 +237,13 @@ ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, co
                            const int8_t* flows, int64_t m, int64_t n, float* unw, int32_t* cyc,
                            cudaStream_t s);
 // ww_mcf.cu
-ww_status solve_mcf(const int8_t* res, const int32_t* ground, const int16_t* costs, int64_t m,
-                    int64_t n, const ww_params* p, ww_workspace* ws, int8_t* flows, int64_t* pot,
-                    int64_t* total_cost, int32_t* dev_status, cudaStream_t s);
+ww_status solve_problems(const ProbHost* probs, int nprob, SolverWs* sv, const ww_params* prm, int64_t* pot_global,
+                         ww_solve_stats* stats, cudaStream_t s);
 ww_status launch_certificate(const int8_t* res, const int32_t* ground, const int16_t* costs,
                              const int8_t* flows, const int64_t* pot, int64_t m, int64_t n,
                              int64_t* counts, cudaStream_t s);
-int64_t solver_bytes(int64_t m, int64_t n);
-ww_status solver_alloc(ww_workspace* ws, int64_t m, int64_t n);
-void solver_free(ww_workspace* ws);
+int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs);
+ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n_probs);
+void solver_free(SolverWs* sv);
+inline int64_t tiles_for(int64_t m, int64_t n) { return ((m - 1 + 31) / 32) * ((n - 1 + 31) / 32); }
 }  // namespace ww

@@ -31,9 +31,11 @@
 // treating it as a free source/sink keeps the optimum of Eq. 2.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "ww_internal.cuh"
@@ -48,6 +50,24 @@ constexpr int kMaxSearchGrid = 148 * 64;  // ring slack: at most one outstanding
 
 enum : int32_t { kErrOverflow = 1, kErrInternal = 2, kErrWalk = 4, kErrSpin = 8 };
 
+// One problem of a (possibly one-element) batch.  Node arrays of all problems
+// are concatenated (node_off); tiles are numbered consecutively (tile_off).
+// All problems share one free ground node, whose potential sits after the
+// last node: the supplies of every problem sum to zero, so no flow can cross
+// between problems through it and the joint optimum is the sum of the optima.
+struct ProbDev {
+  int64_t m, n, R, C, N;
+  int64_t node_off, tile_off;
+  int32_t tiles_x, tiles_y;
+  const int8_t* res;
+  const int32_t* ground;
+  const int16_t* costs;
+  int8_t* flows;
+  int64_t* pot_out;      // caller's potentials (N + 1) or nullptr when pot is the caller's array
+  int64_t* total_cost;   // device int64
+  int32_t* status;       // device int32
+};
+
 struct McfCtr {
   int32_t list_count[2];
   uint32_t D;
@@ -55,41 +75,67 @@ struct McfCtr {
   int32_t ncand;
   int32_t ncand_next;
   int32_t err;
-  int32_t pad;
+  int32_t cand_sel;    // which half of the candidate buffer is current
   long long g_net;
   unsigned long long tile_visits;
   long long total_cost;
   unsigned long long local_rounds;
   unsigned long long visit_cycles;
   int32_t found;       // candidates reached by the current search
-  int32_t capped_any;  // a tile discarded a candidate at or beyond the cap
+  int32_t capped_any;  // a tile dropped a candidate at or beyond the cap
+  uint32_t cap;        // distance cap of the current search (0xFFFFFFFF = none)
+  uint32_t last_D;     // largest augmented distance of the last pass that augmented
+  int32_t passes;
+  int32_t idle;        // consecutive passes without augmentation
+  int32_t band_again;  // the band loop continues
+  int32_t go_on;       // the pass loop continues
+  int32_t status;      // solver status (WW_OK while running)
+  int32_t max_passes;
+  int64_t n_total;     // nodes of the active problems
+  int64_t n_cap_nodes; // node capacity (the candidate list halves are this far apart)
 };
 
 namespace {
 
-struct Grid {
-  int64_t m, n, R, C, N, P;  // pixel rows/cols, node rows/cols, nodes, pixels
-  int tiles_x, tiles_y;
+// Problems live in slots (stable ids); `order` lists the active slots sorted by
+// node offset.  The shared ground potential sits at pot[g_index].
+struct Batch {
+  const ProbDev* probs;      // by slot
+  const int32_t* order;      // active slots by ascending node_off
+  int nact;                  // active slots
+  const int32_t* tile_prob;  // global tile -> slot
+  int64_t g_index;           // index of the ground potential
+  int64_t n_total;           // nodes of the active problems (pass policy)
+  int64_t t_total;           // upper bound of the tile ids in use
 };
+
+__device__ __forceinline__ int prob_of_node(const Batch& b, int64_t v) {
+  int lo = 0, hi = b.nact - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.probs[b.order[mid]].node_off <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return b.order[lo];
+}
 
 // Raw residual cost of the arc entering node (i,j) from direction dir (forward
 // search: arc u->v) or leaving it toward dir (reverse search: arc v->u).
 // Returns false if the arc does not exist.
 template <bool FWD>
-__device__ __forceinline__ bool arc_cost(const int16_t* __restrict__ costs, const int8_t* __restrict__ flows,
-                                         const Grid& g, int64_t i, int64_t j, int dir, int32_t* cost) {
-  const int64_t P = g.P;
+__device__ __forceinline__ bool arc_cost(const ProbDev& p, int64_t i, int64_t j, int dir, int32_t* cost) {
+  const int64_t P = p.m * p.n;
   int64_t e;
-  int plane;        // 0: h edge, 1: v edge
-  bool plus;        // move raises dk
+  int plane;  // 0: h edge, 1: v edge
+  bool plus;  // move raises dk
   switch (dir) {
-    case kDirUp: e = i * g.n + j; plane = 0; plus = FWD; break;
-    case kDirDown: e = (i + 1) * g.n + j; plane = 0; plus = !FWD; break;
-    case kDirLeft: e = i * g.n + j; plane = 1; plus = !FWD; break;
-    default: e = i * g.n + j + 1; plane = 1; plus = FWD; break;
+    case kDirUp: e = i * p.n + j; plane = 0; plus = FWD; break;
+    case kDirDown: e = (i + 1) * p.n + j; plane = 0; plus = !FWD; break;
+    case kDirLeft: e = i * p.n + j; plane = 1; plus = !FWD; break;
+    default: e = i * p.n + j + 1; plane = 1; plus = FWD; break;
   }
-  int dk = flows[plane * P + e];
-  int32_t cp = costs[(2 * plane) * P + e], cm = costs[(2 * plane + 1) * P + e];
+  int dk = p.flows[plane * P + e];
+  int32_t cp = p.costs[(2 * plane) * P + e], cm = p.costs[(2 * plane + 1) * P + e];
   if (plus) {
     if (dk > 0) return false;
     *cost = dk == 0 ? cp : -cm;
@@ -100,12 +146,13 @@ __device__ __forceinline__ bool arc_cost(const int16_t* __restrict__ costs, cons
   return true;
 }
 
-__device__ __forceinline__ int64_t nb_node(const Grid& g, int64_t i, int64_t j, int dir) {
+// Local neighbour index inside a problem, -1 for the ground node.
+__device__ __forceinline__ int64_t nb_local(const ProbDev& p, int64_t i, int64_t j, int dir) {
   switch (dir) {
-    case kDirUp: return i > 0 ? (i - 1) * g.C + j : -1;
-    case kDirDown: return i + 1 < g.R ? (i + 1) * g.C + j : -1;
-    case kDirLeft: return j > 0 ? i * g.C + j - 1 : -1;
-    default: return j + 1 < g.C ? i * g.C + j + 1 : -1;
+    case kDirUp: return i > 0 ? (i - 1) * p.C + j : -1;
+    case kDirDown: return i + 1 < p.R ? (i + 1) * p.C + j : -1;
+    case kDirLeft: return j > 0 ? i * p.C + j - 1 : -1;
+    default: return j + 1 < p.C ? i * p.C + j + 1 : -1;
   }
 }
 
@@ -242,11 +289,9 @@ constexpr int LROW = TS + 3;  // padded row stride of the label tile (halo 1 eac
 constexpr int RCOL = TS + 1;  // padded row stride of the arc-weight planes
 
 template <bool FWD>
-__global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t* __restrict__ costs,
-                                                           const int8_t* __restrict__ flows,
-                                                           const int64_t* __restrict__ pot, uint64_t* labels,
-                                                           SearchQ* q, int32_t* slots, int32_t* inq, McfCtr* ctr,
-                                                           uint64_t capK, int32_t* capped_flag) {
+__global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch b, const int64_t* __restrict__ pot,
+                                                           uint64_t* labels, SearchQ* q, int32_t* slots,
+                                                           int32_t* inq, McfCtr* ctr, int32_t* capped_flag) {
   __shared__ uint64_t lab[TSH][LROW];
   __shared__ uint32_t rc[4][TS][RCOL];
   __shared__ int side[4];
@@ -254,8 +299,10 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
   __shared__ unsigned rowdirty, coldirty, rowdirty_next, coldirty_next;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;  // 8 warps
-  const int ring = g.tiles_x * g.tiles_y + (int)gridDim.x + 64;
-  const int64_t pG = pot[g.N];
+  const int ring = (int)b.t_total + (int)gridDim.x + 64;
+  const int64_t pG = pot[b.g_index];
+  const uint32_t cap = ctr->cap;
+  const uint64_t capK = cap == 0xFFFFFFFFu ? KINF : ((uint64_t)cap << 29);
   int err = 0;
   if (tid == 0) {
     rowdirty_next = 0;
@@ -269,8 +316,12 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
       if (tid == 0 && tile == -2) atomicOr(&ctr->err, kErrSpin);
       break;
     }
-    const int64_t ti = tile / g.tiles_x, tj = tile % g.tiles_x;
+    const ProbDev& p = b.probs[b.tile_prob[tile]];
+    const int64_t lt = tile - p.tile_off;
+    const int64_t ti = lt / p.tiles_x, tj = lt % p.tiles_x;
     const int64_t i0 = ti * TS, j0 = tj * TS;
+    uint64_t* plab = labels + p.node_off;
+    const int64_t* ppot = pot + p.node_off;
     if (tid < 4) side[tid] = 0;
     const long long t_start = clock64();
     // labels with halo; directly outside the grid stands G, a root (label 0)
@@ -278,11 +329,11 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
       int r = qd / TSH, c = qd % TSH;
       int64_t i = i0 + r - 1, j = j0 + c - 1;
       uint64_t v;
-      if (i < 0 || j < 0 || i >= g.R || j >= g.C) {
-        bool ring = (i >= -1 && i <= g.R && j >= -1 && j <= g.C);
+      if (i < 0 || j < 0 || i >= p.R || j >= p.C) {
+        bool ring = (i >= -1 && i <= p.R && j >= -1 && j <= p.C);
         v = ring ? 0ull : kInf;
       } else {
-        v = *((volatile const uint64_t*)&labels[i * g.C + j]);
+        v = *((volatile const uint64_t*)&plab[i * p.C + j]);
       }
       lab[r][c] = v;
     }
@@ -291,15 +342,15 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
     for (int k = 0; k < 4; ++k) {
       int ly = warp + 8 * k;
       int64_t i = i0 + ly, j = j0 + lane;
-      bool ex = i < g.R && j < g.C;
-      int64_t pv = ex ? pot[i * g.C + j] : 0;
+      bool ex = i < p.R && j < p.C;
+      int64_t pv = ex ? ppot[i * p.C + j] : 0;
 #pragma unroll
       for (int d = 1; d <= 4; ++d) {
         uint32_t r = kNoArc;
         int32_t c;
-        if (ex && arc_cost<FWD>(costs, flows, g, i, j, d, &c)) {
-          int64_t u = nb_node(g, i, j, d);
-          int64_t pu = u >= 0 ? pot[u] : pG;
+        if (ex && arc_cost<FWD>(p, i, j, d, &c)) {
+          int64_t u = nb_local(p, i, j, d);
+          int64_t pu = u >= 0 ? ppot[u] : pG;
           int64_t red = FWD ? (int64_t)c - pu + pv : (int64_t)c - pv + pu;
           if (red < 0) {
             err |= kErrInternal;
@@ -401,10 +452,10 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
       int ly = warp + 8 * k;
       int64_t i = i0 + ly, j = j0 + lane;
       uint64_t v = lab[ly + 1][lane + 1];
-      if (i < g.R && j < g.C && v != orig[k]) {
+      if (i < p.R && j < p.C && v != orig[k]) {
         // the same tile may be in process in two CTAs (it can be re-queued
         // while in flight); atomicMin keeps every label monotone
-        atomicMin((unsigned long long*)&labels[i * g.C + j], (unsigned long long)v);
+        atomicMin((unsigned long long*)&plab[i * p.C + j], (unsigned long long)v);
         if (ly == 0) side[0] = 1;
         if (ly == TS - 1) side[1] = 1;
         if (lane == 0) side[2] = 1;
@@ -419,10 +470,10 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
     __syncthreads();
     if (tid == 0) {
       bool ok = true;
-      if (side[0] && ti > 0) ok &= q_push(tile - g.tiles_x, ring, q, slots, inq);
-      if (side[1] && ti + 1 < g.tiles_y) ok &= q_push(tile + g.tiles_x, ring, q, slots, inq);
+      if (side[0] && ti > 0) ok &= q_push(tile - p.tiles_x, ring, q, slots, inq);
+      if (side[1] && ti + 1 < p.tiles_y) ok &= q_push(tile + p.tiles_x, ring, q, slots, inq);
       if (side[2] && tj > 0) ok &= q_push(tile - 1, ring, q, slots, inq);
-      if (side[3] && tj + 1 < g.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq);
+      if (side[3] && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq);
       if (!ok) err |= kErrSpin;
       atomicAdd(&ctr->tile_visits, 1ull);
       atomicAdd(&ctr->local_rounds, (unsigned long long)(round + 1));
@@ -435,69 +486,105 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Grid g, const int16_t
   if (err) atomicOr(&ctr->err, err);
 }
 
-__global__ void k_init_state(Grid g, const int8_t* res, int32_t* excess, int32_t* cand, McfCtr* ctr) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x) {
-    int32_t r = res[v];
-    excess[v] = r;
-    if (r != 0) cand[atomicAdd(&ctr->ncand, 1)] = (int32_t)v;
-  }
+__device__ __forceinline__ int32_t* cand_cur(int32_t* base, const McfCtr* c, int64_t) {
+  return base + (c->cand_sel ? c->n_cap_nodes : 0);
+}
+__device__ __forceinline__ int32_t* cand_nxt(int32_t* base, const McfCtr* c, int64_t) {
+  return base + (c->cand_sel ? 0 : c->n_cap_nodes);
 }
 
+// A problem joins: imbalances from its residues, its imbalanced nodes appended
+// to the current list, and every node potential set to the current ground
+// potential (all its reduced costs then equal its raw costs, >= 0).
+// Grid: x over the problem's nodes, y over the listed slots.
+__global__ void k_init_state(Batch b, const int32_t* slots, int32_t* excess, int32_t* cand_base, int64_t* pot,
+                             int32_t* prob_left, McfCtr* ctr) {
+  const int slot = slots[blockIdx.y];
+  const ProbDev& p = b.probs[slot];
+  const int64_t pg = pot[b.g_index];
+  int32_t* cand = cand_cur(cand_base, ctr, ctr->n_cap_nodes);
+  int cnt = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.N; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t r = p.res[v];
+    excess[p.node_off + v] = r;
+    pot[p.node_off + v] = pg;
+    if (r != 0) {
+      cand[atomicAdd(&ctr->ncand, 1)] = (int32_t)(p.node_off + v);
+      ++cnt;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&prob_left[slot], cnt);
+}
+
+// Per-pass setup: distance cap (full search while many imbalanced nodes
+// remain, a band of 4x the last augmented distance once few are left),
+// counters and the worklist.
+__global__ void k_pass_setup(McfCtr* ctr, SearchQ* q) {
+  if (!ctr->go_on) return;
+  ctr->D = 0;
+  ctr->naug = 0;
+  ctr->found = 0;
+  ctr->capped_any = 0;
+  ctr->band_again = 1;
+  uint32_t cap = 0xFFFFFFFFu;
+  if (ctr->passes >= 2 && (long long)ctr->ncand * 1000ll < ctr->n_total) {
+    unsigned long long c = 4ull * ctr->last_D;
+    cap = (uint32_t)(c < 4096ull ? 4096ull : (c > 0x7FFFFFFFull ? 0x7FFFFFFFull : c));
+  }
+  ctr->cap = cap;
+  q->head = q->tail = q->pending = 0;
+}
+
+// Grid: x over a problem's nodes, y over the active problems.
 template <bool FWD>
-__global__ void k_init_labels(Grid g, const int32_t* excess, uint64_t* labels) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x) {
-    int32_t e = excess[v];
+__global__ void k_init_labels(Batch b, const int32_t* excess, uint64_t* labels, const McfCtr* ctr) {
+  if (!ctr->go_on) return;
+  const ProbDev& p = b.probs[b.order[blockIdx.y]];
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.N; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t e = excess[p.node_off + v];
     bool root = FWD ? e > 0 : e < 0;
-    labels[v] = root ? 0ull : kInf;
+    labels[p.node_off + v] = root ? 0ull : kInf;
   }
 }
 
 __device__ __forceinline__ int32_t& ctr_err(const McfCtr* c) { return const_cast<McfCtr*>(c)->err; }
 
-// Seed the worklist: tiles holding a root, and every border tile (G is a root).
+// Seed the worklist: tiles holding a root, and the border tiles (the ground
+// node is a root) of every problem that is not yet balanced.
 template <bool FWD>
-__global__ void k_seed_tiles(Grid g, const int32_t* excess, const int32_t* cand, const McfCtr* ctr, SearchQ* q,
+__global__ void k_seed_tiles(Batch b, const int32_t* excess, int32_t* cand_base, const McfCtr* ctr,
+                             const int32_t* prob_left, const int32_t* border, int32_t n_border, SearchQ* q,
                              int32_t* slots, int32_t* inq, int search_grid) {
+  if (!ctr->go_on) return;
   const int nc = ctr->ncand;
-  const int nborder = 2 * g.tiles_x + 2 * g.tiles_y;
-  const int ring = g.tiles_x * g.tiles_y + search_grid + 64;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc + nborder;
+  const int32_t* cand = cand_cur(cand_base, ctr, b.n_total);
+  const int ring = (int)b.t_total + search_grid + 64;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc + n_border;
        k += (int64_t)gridDim.x * blockDim.x) {
     int tile;
     if (k < nc) {
       int32_t v = cand[k];
       int32_t e = excess[v];
       if (!(FWD ? e > 0 : e < 0)) continue;
-      int64_t i = v / g.C, j = v % g.C;
-      tile = (int)((i / TS) * g.tiles_x + j / TS);
+      const ProbDev& p = b.probs[prob_of_node(b, v)];
+      int64_t loc = v - p.node_off, i = loc / p.C, j = loc % p.C;
+      tile = (int)(p.tile_off + (i / TS) * p.tiles_x + j / TS);
     } else {
-      int b = (int)(k - nc);
-      if (b < g.tiles_x) tile = b;
-      else if (b < 2 * g.tiles_x) tile = (g.tiles_y - 1) * g.tiles_x + (b - g.tiles_x);
-      else if (b < 2 * g.tiles_x + g.tiles_y) tile = (b - 2 * g.tiles_x) * g.tiles_x;
-      else tile = (b - 2 * g.tiles_x - g.tiles_y) * g.tiles_x + g.tiles_x - 1;
+      tile = border[k - nc];
+      if (prob_left[b.tile_prob[tile]] == 0) continue;
     }
     if (!q_push(tile, ring, q, slots, inq)) atomicOr(&ctr_err(ctr), kErrSpin);
   }
 }
 
-// Widen the distance band: queue every tile that dropped a candidate.
-__global__ void k_reseed(Grid g, int32_t* capped_flag, SearchQ* q, int32_t* slots, int32_t* inq, int search_grid,
-                         McfCtr* ctr) {
-  const int T = g.tiles_x * g.tiles_y;
-  const int ring = T + search_grid + 64;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-    if (capped_flag[t]) {
-      capped_flag[t] = 0;
-      if (!q_push(t, ring, q, slots, inq)) atomicOr(&ctr->err, kErrSpin);
-    }
-  }
-}
-
-// Candidates (deficits forward, excess nodes reverse) the search has reached.
+// Candidates (deficits forward, excess nodes reverse) reached by the search.
 template <bool FWD>
-__global__ void k_count_found(const int32_t* excess, const uint64_t* labels, const int32_t* cand, McfCtr* ctr) {
+__global__ void k_count_found(const int32_t* excess, const uint64_t* labels, int32_t* cand_base, int64_t n_total,
+                              McfCtr* ctr) {
+  if (!ctr->band_again) return;
   const int nc = ctr->ncand;
+  const int32_t* cand = cand_cur(cand_base, ctr, n_total);
   int c = 0;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
     int32_t t = cand[q];
@@ -508,23 +595,61 @@ __global__ void k_count_found(const int32_t* excess, const uint64_t* labels, con
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->found, c);
 }
 
-// Walk from v along the forest to its root.  Returns the root, or -1 on a walk
-// longer than the node count (reported as an internal error).
-__device__ __forceinline__ int64_t walk_root(const Grid& g, const uint64_t* labels, int64_t v) {
-  for (int64_t steps = 0; steps <= g.N; ++steps) {
-    int d = label_dir(labels[v]);
+// After a band: widen (x8, or unbounded on the last band) if no candidate was
+// reached and some tile dropped candidates at the cap; otherwise the band loop
+// is over.  Runs on one thread.
+__global__ void k_band_decide(McfCtr* ctr, SearchQ* q, int last_band) {
+  if (!ctr->band_again) return;
+  bool again = ctr->cap != 0xFFFFFFFFu && ctr->found == 0 && ctr->capped_any;
+  if (again) {
+    ctr->cap = (last_band || ctr->cap >= 0x0FFFFFFFu) ? 0xFFFFFFFFu : ctr->cap * 8u;
+    q->head = q->tail = q->pending = 0;
+    ctr->capped_any = 0;
+  }
+  ctr->band_again = again ? 1 : 0;
+}
+
+// Widen the band: queue every tile that dropped a candidate.
+__global__ void k_reseed(Batch b, int32_t* capped_flag, SearchQ* q, int32_t* slots, int32_t* inq, int search_grid,
+                         McfCtr* ctr) {
+  if (!ctr->band_again) return;
+  const int ring = (int)b.t_total + search_grid + 64;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < b.t_total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (capped_flag[t]) {
+      capped_flag[t] = 0;
+      if (!q_push((int)t, ring, q, slots, inq)) atomicOr(&ctr->err, kErrSpin);
+    }
+  }
+}
+
+// After the last band: drop the leftover "dropped at cap" flags.
+__global__ void k_clear_capped(Batch b, int32_t* capped_flag, const McfCtr* ctr) {
+  if (!ctr->go_on) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < b.t_total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    capped_flag[t] = 0;
+}
+
+// Walk from local node v along the forest to its tree root (local index), or
+// -1 after more steps than nodes (reported as an internal error).
+__device__ __forceinline__ int64_t walk_root(const ProbDev& p, const uint64_t* plab, int64_t v) {
+  for (int64_t steps = 0; steps <= p.N; ++steps) {
+    int d = label_dir(plab[v]);
     if (d == kDirRoot) return v;
-    int64_t u = nb_node(g, v / g.C, v % g.C, d);
-    if (u < 0) return v;  // parent is G: v roots a subtree of G
+    int64_t u = nb_local(p, v / p.C, v % p.C, d);
+    if (u < 0) return v;  // parent is the ground node: v roots a subtree of it
     v = u;
   }
   return -1;
 }
 
 template <bool FWD>
-__global__ void k_select(Grid g, const int32_t* excess, const uint64_t* labels, const int32_t* cand,
+__global__ void k_select(Batch b, const int32_t* excess, const uint64_t* labels, int32_t* cand_base,
                          int32_t* cand_root, uint64_t* best, McfCtr* ctr) {
+  if (!ctr->go_on) return;
   const int nc = ctr->ncand;
+  const int32_t* cand = cand_cur(cand_base, ctr, b.n_total);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
     int32_t t = cand[q];
     int32_t e = excess[t];
@@ -532,20 +657,24 @@ __global__ void k_select(Grid g, const int32_t* excess, const uint64_t* labels, 
     if (!(FWD ? e < 0 : e > 0)) continue;
     uint64_t l = labels[t];
     if (l == kInf) continue;
-    int64_t r = walk_root(g, labels, t);
+    const ProbDev& p = b.probs[prob_of_node(b, t)];
+    int64_t r = walk_root(p, labels + p.node_off, t - p.node_off);
     if (r < 0) {
       atomicOr(&ctr->err, kErrWalk);
       continue;
     }
+    r += p.node_off;
     cand_root[q] = (int32_t)r;
     atomicMin((unsigned long long*)&best[r], ((l >> 32) << 32) | (uint64_t)(uint32_t)t);
   }
 }
 
 template <bool FWD>
-__global__ void k_augment(Grid g, int32_t* excess, const uint64_t* labels, const int32_t* cand,
-                          const int32_t* cand_root, const uint64_t* best, int8_t* flows, McfCtr* ctr) {
+__global__ void k_augment(Batch b, int32_t* excess, const uint64_t* labels, int32_t* cand_base,
+                          const int32_t* cand_root, const uint64_t* best, long long* g_net, McfCtr* ctr) {
+  if (!ctr->go_on) return;
   const int nc = ctr->ncand;
+  const int32_t* cand = cand_cur(cand_base, ctr, b.n_total);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
     int32_t r = cand_root[q];
     if (r < 0) continue;
@@ -554,23 +683,26 @@ __global__ void k_augment(Grid g, int32_t* excess, const uint64_t* labels, const
     if (best[r] != (((l >> 32) << 32) | (uint64_t)(uint32_t)t)) continue;
     atomicMax(&ctr->D, (uint32_t)(l >> 32));
     atomicAdd(&ctr->naug, 1);
-    // flip dk along the path t -> ... -> r (-> G)
-    int64_t v = t;
-    for (int64_t steps = 0; steps <= g.N; ++steps) {
-      int d = label_dir(labels[v]);
+    const int pi = prob_of_node(b, t);
+    const ProbDev& p = b.probs[pi];
+    const uint64_t* plab = labels + p.node_off;
+    const int64_t P = p.m * p.n;
+    // flip dk along the path t -> ... -> r (-> ground)
+    int64_t v = t - p.node_off;
+    for (int64_t steps = 0; steps <= p.N; ++steps) {
+      int d = label_dir(plab[v]);
       if (d == kDirRoot) break;
-      int64_t i = v / g.C, j = v % g.C;
+      int64_t i = v / p.C, j = v % p.C;
       int64_t e;
-      int plane;
-      int s;  // +1 if the forward-direction move raises dk
+      int plane, s;  // s = +1 if the move u -> v raises dk
       switch (d) {
-        case kDirUp: e = i * g.n + j; plane = 0; s = 1; break;
-        case kDirDown: e = (i + 1) * g.n + j; plane = 0; s = -1; break;
-        case kDirLeft: e = i * g.n + j; plane = 1; s = -1; break;
-        default: e = i * g.n + j + 1; plane = 1; s = 1; break;
+        case kDirUp: e = i * p.n + j; plane = 0; s = 1; break;
+        case kDirDown: e = (i + 1) * p.n + j; plane = 0; s = -1; break;
+        case kDirLeft: e = i * p.n + j; plane = 1; s = -1; break;
+        default: e = i * p.n + j + 1; plane = 1; s = 1; break;
       }
-      flows[plane * g.P + e] += (int8_t)(FWD ? s : -s);
-      int64_t u = nb_node(g, i, j, d);
+      p.flows[plane * P + e] += (int8_t)(FWD ? s : -s);
+      int64_t u = nb_local(p, i, j, d);
       if (u < 0) break;
       v = u;
     }
@@ -578,73 +710,129 @@ __global__ void k_augment(Grid g, int32_t* excess, const uint64_t* labels, const
     if (FWD) {
       excess[t] += 1;
       if (real_root) excess[r] -= 1;
-      else atomicAdd((unsigned long long*)&ctr->g_net, 1ull);  // G emitted one unit
+      else atomicAdd((unsigned long long*)&g_net[pi], 1ull);  // the ground node emitted a unit
     } else {
       excess[t] -= 1;
       if (real_root) excess[r] += 1;
-      else atomicAdd((unsigned long long*)&ctr->g_net, ~0ull);  // G absorbed one unit
+      else atomicAdd((unsigned long long*)&g_net[pi], ~0ull);  // the ground node absorbed a unit
     }
   }
 }
 
-__global__ void k_reset_best(const int32_t* cand_root, uint64_t* best, const McfCtr* ctr) {
+__global__ void k_reset_best(Batch b, const int32_t* cand_root, uint64_t* best, int32_t* prob_left, int nslots,
+                             const McfCtr* ctr) {
+  if (!ctr->go_on) return;
   const int nc = ctr->ncand;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
     int32_t r = cand_root[q];
     if (r >= 0) best[r] = kInf;
   }
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nslots; q += gridDim.x * blockDim.x) prob_left[q] = 0;
 }
 
+// Grid: x over a problem's nodes, y over the active problems.
 template <bool FWD>
-__global__ void k_potentials(Grid g, const uint64_t* labels, int64_t* pot, const McfCtr* ctr) {
+__global__ void k_potentials(Batch b, const uint64_t* labels, int64_t* pot, const McfCtr* ctr) {
+  if (!ctr->go_on || ctr->naug == 0) return;
   const uint32_t D = ctr->D;
-  if (ctr->naug == 0) return;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t l = labels[v];
+  const ProbDev& p = b.probs[b.order[blockIdx.y]];
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.N; v += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t l = labels[p.node_off + v];
     if (l == kInf) continue;
     uint32_t d = (uint32_t)(l >> 32);
-    if (d < D) pot[v] += FWD ? (int64_t)(D - d) : -(int64_t)(D - d);
+    if (d < D) pot[p.node_off + v] += FWD ? (int64_t)(D - d) : -(int64_t)(D - d);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) pot[g.N] += FWD ? (int64_t)D : -(int64_t)D;
 }
 
-__global__ void k_compact(const int32_t* excess, const int32_t* cand, int32_t* cand2, McfCtr* ctr) {
+// The ground node is a root of every search (distance 0).
+template <bool FWD>
+__global__ void k_potential_ground(Batch b, int64_t* pot, const McfCtr* ctr) {
+  if (!ctr->go_on || ctr->naug == 0) return;
+  pot[b.g_index] += FWD ? (int64_t)ctr->D : -(int64_t)ctr->D;
+}
+
+__global__ void k_compact(Batch b, const int32_t* excess, int32_t* cand_base, int32_t* prob_left, McfCtr* ctr) {
+  if (!ctr->go_on) return;
   const int nc = ctr->ncand;
+  const int32_t* cand = cand_cur(cand_base, ctr, b.n_total);
+  int32_t* next = cand_nxt(cand_base, ctr, b.n_total);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
     int32_t v = cand[q];
-    if (excess[v] != 0) cand2[atomicAdd(&ctr->ncand_next, 1)] = v;
+    if (excess[v] != 0) {
+      next[atomicAdd(&ctr->ncand_next, 1)] = v;
+      atomicAdd(&prob_left[prob_of_node(b, v)], 1);
+    }
   }
 }
 
+// End of a pass: swap the candidate lists and decide whether to go on.
 __global__ void k_finish_pass(McfCtr* ctr) {
+  if (!ctr->go_on) return;
   ctr->ncand = ctr->ncand_next;
   ctr->ncand_next = 0;
+  ctr->cand_sel ^= 1;
+  ctr->passes += 1;
+  if (ctr->naug > 0) {
+    ctr->last_D = ctr->D;
+    ctr->idle = 0;
+  } else {
+    ctr->idle += 1;
+  }
+  int st = WW_OK;
+  if (ctr->err & kErrOverflow) st = WW_ERR_OVERFLOW;
+  else if (ctr->err & kErrSpin) st = WW_ERR_TIMEOUT;
+  else if (ctr->err) st = WW_ERR_INTERNAL;
+  else if (ctr->ncand > 0 && ctr->idle >= 2) st = WW_ERR_INFEASIBLE;
+  else if (ctr->ncand > 0 && ctr->passes >= ctr->max_passes) st = WW_ERR_TIMEOUT;
+  ctr->status = st;
+  ctr->go_on = (st == WW_OK && ctr->ncand > 0) ? 1 : 0;
 }
 
-// total cost sum c_a x_a (block partial sums, int64 atomics)
-__global__ void k_total_cost(const int16_t* costs, const int8_t* flows, int64_t P, long long* out) {
+// Total cost of the listed slots; grid: x over a problem's pixels, y over the list.
+__global__ void k_total_cost(Batch b, const int32_t* slots, long long* tc) {
+  const int slot = slots[blockIdx.y];
+  const ProbDev& p = b.probs[slot];
+  const int64_t P = p.m * p.n;
   long long s = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
-    int a = flows[e], b = flows[P + e];
-    if (a == 1) s += costs[e];
-    if (a == -1) s += costs[P + e];
-    if (b == 1) s += costs[2 * P + e];
-    if (b == -1) s += costs[3 * P + e];
+    int a = p.flows[e], c = p.flows[P + e];
+    if (a == 1) s += p.costs[e];
+    if (a == -1) s += p.costs[P + e];
+    if (c == 1) s += p.costs[2 * P + e];
+    if (c == -1) s += p.costs[3 * P + e];
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd((unsigned long long*)out, (unsigned long long)s);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd((unsigned long long*)&tc[slot], (unsigned long long)s);
 }
 
-__global__ void k_write_result(const McfCtr* ctr, const int32_t* ground, int32_t status_host, int32_t* dev_status,
-                               int64_t* total_cost) {
-  int32_t st = status_host;
-  if (st == WW_OK) {
-    if (ctr->err & kErrOverflow) st = WW_ERR_OVERFLOW;
-    else if (ctr->err) st = WW_ERR_INTERNAL;
-    else if (ctr->g_net != (long long)*ground) st = WW_ERR_INTERNAL;
+// Potentials out for the listed slots (when the solve used library storage).
+__global__ void k_copy_pot(Batch b, const int32_t* slots, const int64_t* pot) {
+  const ProbDev& p = b.probs[slots[blockIdx.y]];
+  if (!p.pot_out) return;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= p.N; v += (int64_t)gridDim.x * blockDim.x)
+    p.pot_out[v] = v < p.N ? pot[p.node_off + v] : pot[b.g_index];
+}
+
+// Status and total cost of the listed slots; ground balance check (G's net
+// outflow must equal r_G once every other node is balanced).
+__global__ void k_write_results(Batch b, const int32_t* slots, int nlist, const McfCtr* ctr, const long long* g_net,
+                                const long long* tc, int32_t* status_all) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nlist; q += gridDim.x * blockDim.x) {
+    const int slot = slots[q];
+    const ProbDev& p = b.probs[slot];
+    int32_t st = ctr->status;
+    if (st == WW_OK && g_net[slot] != (long long)*p.ground) st = WW_ERR_INTERNAL;
+    *p.status = st;
+    status_all[q] = st;
+    *p.total_cost = tc[slot];
   }
-  *dev_status = st;
-  *total_cost = ctr->total_cost;
+}
+
+int grid_blocks(int64_t work, int threads, int cap) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
 }
 
 bool trace_enabled() {
@@ -656,210 +844,391 @@ bool trace_enabled() {
   return on == 1;
 }
 
-int grid_blocks(int64_t work, int threads, int cap) {
-  int64_t b = (work + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
-
 }  // namespace
+// ---------------- host side ----------------
 
-int64_t solver_bytes(int64_t m, int64_t n) {
-  int64_t N = (m - 1) * (n - 1);
-  int64_t tiles = ((m - 1 + TS - 1) / TS) * ((n - 1 + TS - 1) / TS);
-  return N * (4 + 8 + 8 + 4 + 4 + 4) + tiles * 4 * 3 + (int64_t)sizeof(McfCtr) + 4096;
+int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
+  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8) + (n_nodes + 1) * 8 + n_tiles * 4 * 6 + (kMaxSearchGrid + 64) * 4 +
+         n_probs * (sizeof(ProbDev) + 4 + 8 + 8 + 16 + 12) + (int64_t)sizeof(McfCtr) + 4096;
 }
 
-ww_status solver_alloc(ww_workspace* ws, int64_t m, int64_t n) {
-  int64_t N = (m - 1) * (n - 1);
-  int64_t tiles = ((m - 1 + TS - 1) / TS) * ((n - 1 + TS - 1) / TS);
-  if (cudaMalloc(&ws->excess, N * 4) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->labels, N * 8) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->best, N * 8) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->cand, N * 4) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->cand2, N * 4) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->cand_root, N * 4) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->tile_stamp, tiles * 4) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->tile_list[0], (tiles + kMaxSearchGrid + 64) * 4) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->tile_list[1], tiles * 4) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->counters, sizeof(McfCtr)) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMalloc(&ws->search_q, sizeof(SearchQ)) != cudaSuccess) return WW_ERR_OOM;
-  if (cudaMallocHost(&ws->host_counters, sizeof(McfCtr)) != cudaSuccess) return WW_ERR_OOM;
-  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
+ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
+  std::memset(sv, 0, sizeof(*sv));
+  sv->n_cap = n_nodes;
+  sv->t_cap = n_tiles;
+  sv->p_cap = n_probs;
+  const int64_t nb = 2 * n_tiles + 4 * n_probs;
+  bool ok = cudaMalloc(&sv->excess, n_nodes * 4) == cudaSuccess && cudaMalloc(&sv->labels, n_nodes * 8) == cudaSuccess &&
+            cudaMalloc(&sv->best, n_nodes * 8) == cudaSuccess && cudaMalloc(&sv->cand, 2 * n_nodes * 4) == cudaSuccess &&
+            cudaMalloc(&sv->cand_root, n_nodes * 4) == cudaSuccess &&
+            cudaMalloc(&sv->pot, (n_nodes + 1) * 8) == cudaSuccess && cudaMalloc(&sv->inq, n_tiles * 4) == cudaSuccess &&
+            cudaMalloc(&sv->slots, (n_tiles + kMaxSearchGrid + 64) * 4) == cudaSuccess &&
+            cudaMalloc(&sv->capped, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tile_prob, n_tiles * 4) == cudaSuccess &&
+            cudaMalloc(&sv->border, nb * 4) == cudaSuccess && cudaMalloc(&sv->probs, n_probs * sizeof(ProbDev)) == cudaSuccess &&
+            cudaMalloc(&sv->prob_left, n_probs * 4) == cudaSuccess && cudaMalloc(&sv->g_net, n_probs * 8) == cudaSuccess &&
+            cudaMalloc(&sv->tc, n_probs * 8) == cudaSuccess && cudaMalloc(&sv->ctr, sizeof(McfCtr)) == cudaSuccess &&
+            cudaMalloc(&sv->order, n_probs * 4) == cudaSuccess && cudaMalloc(&sv->slot_list, n_probs * 4) == cudaSuccess &&
+            cudaMalloc(&sv->status_all, n_probs * 4) == cudaSuccess &&
+            cudaMalloc(&sv->q, sizeof(SearchQ)) == cudaSuccess &&
+            cudaMallocHost(&sv->host_ctr, sizeof(McfCtr)) == cudaSuccess &&
+            cudaMallocHost(&sv->host_probs, n_probs * sizeof(ProbDev)) == cudaSuccess;
+  if (!ok) return WW_ERR_OOM;
+  // best labels start unreached; worklist flags, ring slots and cap flags start (and end every search) zero
+  if (cudaMemset(sv->best, 0xFF, n_nodes * 8) != cudaSuccess || cudaMemset(sv->inq, 0, n_tiles * 4) != cudaSuccess ||
+      cudaMemset(sv->slots, 0, (n_tiles + kMaxSearchGrid + 64) * 4) != cudaSuccess ||
+      cudaMemset(sv->capped, 0, n_tiles * 4) != cudaSuccess)
+    return WW_ERR_CUDA;
+  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(sv->events);
   if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) return WW_ERR_CUDA;
-  if (cudaMemset(ws->best, 0xFF, N * 8) != cudaSuccess) return WW_ERR_CUDA;
-  // queue flags and ring slots start (and end every search) all zero
-  if (cudaMemset(ws->tile_stamp, 0, tiles * 4) != cudaSuccess) return WW_ERR_CUDA;
-  if (cudaMemset(ws->tile_list[0], 0, (tiles + kMaxSearchGrid + 64) * 4) != cudaSuccess) return WW_ERR_CUDA;
-  if (cudaMemset(ws->tile_list[1], 0, tiles * 4) != cudaSuccess) return WW_ERR_CUDA;
-  ws->epoch = 0;
   return WW_OK;
 }
 
-void solver_free(ww_workspace* ws) {
-  cudaFree(ws->excess);
-  cudaFree(ws->labels);
-  cudaFree(ws->best);
-  cudaFree(ws->cand);
-  cudaFree(ws->cand2);
-  cudaFree(ws->cand_root);
-  cudaFree(ws->tile_stamp);
-  cudaFree(ws->tile_list[0]);
-  cudaFree(ws->tile_list[1]);
-  cudaFree(ws->counters);
-  cudaFree(ws->search_q);
-  cudaFreeHost(ws->host_counters);
-  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
+void solver_free(SolverWs* sv) {
+  cudaFree(sv->excess);
+  cudaFree(sv->labels);
+  cudaFree(sv->best);
+  cudaFree(sv->cand);
+  cudaFree(sv->cand_root);
+  cudaFree(sv->pot);
+  cudaFree(sv->inq);
+  cudaFree(sv->slots);
+  cudaFree(sv->capped);
+  cudaFree(sv->tile_prob);
+  cudaFree(sv->border);
+  cudaFree(sv->probs);
+  cudaFree(sv->prob_left);
+  cudaFree(sv->g_net);
+  cudaFree(sv->tc);
+  cudaFree(sv->ctr);
+  cudaFree(sv->order);
+  cudaFree(sv->slot_list);
+  cudaFree(sv->status_all);
+  cudaFree(sv->q);
+  cudaFreeHost(sv->host_ctr);
+  cudaFreeHost(sv->host_probs);
+  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(sv->events);
   if (ev[0]) cudaEventDestroy(ev[0]);
   if (ev[1]) cudaEventDestroy(ev[1]);
 }
 
-// One multi-root search: labels reset, worklist seeded with root and border
-// tiles, then persistent launches drain the worklist to the fixed point below a
-// distance cap.  Nodes whose true distance is below the cap end with exact
-// labels.  If no candidate was reached and some tile dropped candidates at the
-// cap, the cap grows (x8) and the search resumes from those tiles.
-template <bool FWD>
-static ww_status run_search(const Grid& g, const int16_t* costs, const int8_t* flows, const int64_t* pot,
-                            ww_workspace* ws, McfCtr* dctr, McfCtr* hctr, uint64_t cap, int sm_count,
-                            cudaStream_t s) {
-  const int nb_nodes = grid_blocks(g.N, 256, sm_count * 16);
-  k_init_labels<FWD><<<nb_nodes, 256, 0, s>>>(g, ws->excess, ws->labels);
-  SearchQ* q = reinterpret_cast<SearchQ*>(ws->search_q);
-  WW_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(SearchQ), s));
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search<FWD>, SEARCH_THREADS, 0);
-  per_sm = per_sm < 1 ? 1 : per_sm;
-  const int search_grid = std::min(sm_count * per_sm, kMaxSearchGrid);
-  k_seed_tiles<FWD><<<grid_blocks(g.N / 64 + 1024, 256, sm_count * 4), 256, 0, s>>>(
-      g, ws->excess, ws->cand, dctr, q, ws->tile_list[0], ws->tile_stamp, search_grid);
-  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
-  const int T = g.tiles_x * g.tiles_y;
-  float ms_total = 0.0f;
-  for (int band = 0; band < 64; ++band) {
-    const uint64_t capK = cap >= 0xFFFFFFFFull ? KINF : (cap << 29);
-    WW_CUDA_TRY(cudaMemsetAsync(&dctr->found, 0, 2 * sizeof(int32_t), s));  // found, capped_any
-    WW_CUDA_TRY(cudaEventRecord(ev[0], s));
-    k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(g, costs, flows, pot, ws->labels, q, ws->tile_list[0],
-                                                         ws->tile_stamp, dctr, capK, ws->tile_list[1]);
-    WW_CUDA_TRY(cudaEventRecord(ev[1], s));
-    WW_CUDA_TRY(cudaGetLastError());
-    ++ws->stats.search_iterations;
-    if (capK == KINF) break;
-    k_count_found<FWD><<<grid_blocks(hctr->ncand > 0 ? hctr->ncand : 1, 256, sm_count * 8), 256, 0, s>>>(
-        ws->excess, ws->labels, ws->cand, dctr);
-    WW_CUDA_TRY(cudaMemcpyAsync(&hctr->found, &dctr->found, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    WW_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hctr->found > 0 || !hctr->capped_any) break;  // the pass adds this last launch's time
-    float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) ms_total += ms;
-    cap = cap >= (0xFFFFFFFFull >> 3) ? 0xFFFFFFFFull : cap * 8;
-    WW_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(SearchQ), s));
-    k_reseed<<<grid_blocks(T, 256, sm_count * 8), 256, 0, s>>>(g, ws->tile_list[1], q, ws->tile_list[0],
-                                                                 ws->tile_stamp, search_grid, dctr);
+namespace {
+
+int search_grid_size(int sm_count) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int a = 1, b = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_search<true>, SEARCH_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<false>, SEARCH_THREADS, 0);
+    per_sm = std::max(1, std::min(a, b));
   }
-  ws->stats.ms_search_gpu += ms_total;  // earlier bands; the pass adds the last launch
-  return WW_OK;
+  return std::min(sm_count * per_sm, kMaxSearchGrid);
 }
 
-template <bool FWD>
-static ww_status run_pass(const Grid& g, const int16_t* costs, int8_t* flows, int64_t* pot, ww_workspace* ws,
-                          McfCtr* dctr, McfCtr* hctr, const ww_params* p, int sm_count, cudaStream_t s) {
-  auto t0 = std::chrono::steady_clock::now();
-  // full search while many roots remain; distance bands once only a few are left
-  uint64_t cap = 0xFFFFFFFFull;
-  if (ws->stats.passes >= 2 && hctr->ncand * 1000ll < g.N) cap = std::max<uint64_t>(4096, 4ull * ws->last_D);
-  ww_status st = run_search<FWD>(g, costs, flows, pot, ws, dctr, hctr, cap, sm_count, s);
-  if (st != WW_OK) return st;
-  const int nb = grid_blocks(hctr->ncand > 0 ? hctr->ncand : g.N, 256, sm_count * 16);
-  WW_CUDA_TRY(cudaMemsetAsync(&dctr->D, 0, 2 * sizeof(int32_t), s));  // D, naug
-  k_select<FWD><<<nb, 256, 0, s>>>(g, ws->excess, ws->labels, ws->cand, ws->cand_root, ws->best, dctr);
-  k_augment<FWD><<<nb, 256, 0, s>>>(g, ws->excess, ws->labels, ws->cand, ws->cand_root, ws->best, flows, dctr);
-  k_reset_best<<<nb, 256, 0, s>>>(ws->cand_root, ws->best, dctr);
-  k_potentials<FWD><<<grid_blocks(g.N, 256, sm_count * 16), 256, 0, s>>>(g, ws->labels, pot, dctr);
-  k_compact<<<nb, 256, 0, s>>>(ws->excess, ws->cand, ws->cand2, dctr);
-  k_finish_pass<<<1, 1, 0, s>>>(dctr);
-  WW_CUDA_TRY(cudaGetLastError());
-  std::swap(ws->cand, ws->cand2);
-  WW_CUDA_TRY(cudaMemcpyAsync(hctr, dctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, s));
-  WW_CUDA_TRY(cudaStreamSynchronize(s));
-  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(ws->events);
-  float ms = 0.0f;
-  if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) ws->stats.ms_search_gpu += ms;
-  if (hctr->naug > 0) ws->last_D = hctr->D;
-  if (trace_enabled())
-    std::fprintf(stderr, "[ww] pass %lld %s: cap %llu, last search %.3f ms, augment %d (D %u), left %d, "
-                 "tile visits %llu, rounds %llu\n",
-                 (long long)ws->stats.passes, FWD ? "fwd" : "rev", (unsigned long long)cap, ms, hctr->naug, hctr->D,
-                 hctr->ncand,
-                 (unsigned long long)hctr->tile_visits, (unsigned long long)hctr->local_rounds);
-  ws->stats.ms_other += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  return WW_OK;
+constexpr int kBands = 4;  // cap c, 8c, 64c, then unbounded
+
+__global__ void k_fill_tiles(int32_t* tile_prob, int64_t tile_off, int64_t count, int32_t slot) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    tile_prob[tile_off + t] = slot;
 }
 
-ww_status solve_mcf(const int8_t* res, const int32_t* ground, const int16_t* costs, int64_t m, int64_t n,
-                    const ww_params* p, ww_workspace* ws, int8_t* flows, int64_t* pot, int64_t* total_cost,
-                    int32_t* dev_status, cudaStream_t s) {
-  Grid g;
-  g.m = m;
-  g.n = n;
-  g.R = m - 1;
-  g.C = n - 1;
-  g.N = g.R * g.C;
-  g.P = m * n;
-  g.tiles_x = (int)((g.C + TS - 1) / TS);
-  g.tiles_y = (int)((g.R + TS - 1) / TS);
-  int dev = 0, sm_count = 148;
+// After membership changes: go on if anything is imbalanced.
+__global__ void k_resume(McfCtr* ctr, int64_t n_total) {
+  ctr->n_total = n_total;
+  ctr->idle = 0;
+  if (ctr->status == WW_OK) ctr->go_on = ctr->ncand > 0 ? 1 : 0;
+}
+
+}  // namespace
+
+// A solve over a changing set of problems: problems join (add + commit) and
+// leave (finalize + remove) between passes; passes alternate forward/reverse.
+class Session {
+ public:
+  Session(SolverWs* sv, int64_t* pot, int64_t g_index, int max_passes, cudaStream_t s);
+  int add(const ProbHost& ph, int64_t node_off, int64_t tile_off);  // -> slot, or -1 if full
+  void remove(int slot);
+  ww_status commit();                                               // upload layout, initialise joiners
+  ww_status pass(ww_solve_stats* st);                               // one pass, then a host sync
+  ww_status left(std::vector<int32_t>* out);                        // imbalanced nodes per slot
+  ww_status finalize(const std::vector<int>& slots, std::vector<int32_t>* statuses);
+  const McfCtr& ctr() const;
+  int64_t tiles_of(int slot) const;
+  ww_status err = WW_OK;
+
+ private:
+  template <bool FWD>
+  ww_status enqueue_pass();
+  Batch batch() const;
+  SolverWs* sv;
+  int64_t* pot;
+  int64_t g_index;
+  cudaStream_t stream;
+  int sm_count = 148, search_grid = 592;
+  std::vector<char> used;
+  std::vector<int> order, pending;
+  int64_t n_total = 0, t_high = 0, max_nodes = 1, n_border = 0;
+  int parity = 0;
+};
+
+Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, int max_passes, cudaStream_t s)
+    : sv(sv_), pot(pot_), g_index(g_index_), stream(s) {
+  int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
-  McfCtr* dctr = reinterpret_cast<McfCtr*>(ws->counters);
-  McfCtr* hctr = reinterpret_cast<McfCtr*>(ws->host_counters);
-  ws->stats = ww_solve_stats{};
-  ws->last_D = 0;
-  WW_CUDA_TRY(cudaMemsetAsync(dctr, 0, sizeof(McfCtr), s));
-  WW_CUDA_TRY(cudaMemsetAsync(flows, 0, 2 * g.P, s));
-  WW_CUDA_TRY(cudaMemsetAsync(pot, 0, (g.N + 1) * sizeof(int64_t), s));
-  k_init_state<<<grid_blocks(g.N, 256, sm_count * 16), 256, 0, s>>>(g, res, ws->excess, ws->cand, dctr);
-  WW_CUDA_TRY(cudaGetLastError());
-  WW_CUDA_TRY(cudaMemcpyAsync(hctr, dctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, s));
-  WW_CUDA_TRY(cudaStreamSynchronize(s));
-  ws->stats.residues = hctr->ncand;
-  ww_status st = WW_OK;
-  int idle = 0;
-  int64_t pass = 0;
-  while (hctr->ncand > 0) {
-    if (pass >= p->max_passes) {
-      st = WW_ERR_TIMEOUT;
+  search_grid = search_grid_size(sm_count);
+  used.assign(sv->p_cap, 0);
+  McfCtr* hc = reinterpret_cast<McfCtr*>(sv->host_ctr);
+  std::memset(hc, 0, sizeof(McfCtr));
+  hc->status = WW_OK;
+  hc->cap = 0xFFFFFFFFu;
+  hc->max_passes = max_passes;
+  hc->n_cap_nodes = sv->n_cap;
+  err = cudaMemcpyAsync(sv->ctr, hc, sizeof(McfCtr), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                cudaMemsetAsync(pot + g_index, 0, 8, s) == cudaSuccess
+            ? WW_OK
+            : WW_ERR_CUDA;
+}
+
+int Session::add(const ProbHost& ph, int64_t node_off, int64_t tile_off) {
+  int slot = -1;
+  for (int k = 0; k < (int)used.size(); ++k)
+    if (!used[k]) {
+      slot = k;
       break;
     }
-    bool fwd = (pass % 2) == 0;
-    st = fwd ? run_pass<true>(g, costs, flows, pot, ws, dctr, hctr, p, sm_count, s)
-             : run_pass<false>(g, costs, flows, pot, ws, dctr, hctr, p, sm_count, s);
-    ++pass;
-    ws->stats.passes = pass;
-    if (st != WW_OK) break;
-    ws->stats.augmentations += hctr->naug;
-    if (hctr->err) break;
-    idle = hctr->naug == 0 ? idle + 1 : 0;
-    if (idle >= 2) {
-      st = WW_ERR_INFEASIBLE;
-      break;
+  if (slot < 0) return -1;
+  ProbDev& d = reinterpret_cast<ProbDev*>(sv->host_probs)[slot];
+  d.m = ph.m;
+  d.n = ph.n;
+  d.R = d.m - 1;
+  d.C = d.n - 1;
+  d.N = d.R * d.C;
+  d.tiles_x = (int32_t)((d.C + TS - 1) / TS);
+  d.tiles_y = (int32_t)((d.R + TS - 1) / TS);
+  d.node_off = node_off;
+  d.tile_off = tile_off;
+  d.res = ph.res;
+  d.ground = ph.ground;
+  d.costs = ph.costs;
+  d.flows = ph.flows;
+  d.pot_out = ph.pot_out;
+  d.total_cost = ph.total_cost;
+  d.status = ph.status;
+  used[slot] = 1;
+  pending.push_back(slot);
+  return slot;
+}
+
+void Session::remove(int slot) {
+  if (slot >= 0 && slot < (int)used.size()) used[slot] = 0;
+}
+
+int64_t Session::tiles_of(int slot) const {
+  const ProbDev& d = reinterpret_cast<const ProbDev*>(sv->host_probs)[slot];
+  return (int64_t)d.tiles_x * d.tiles_y;
+}
+
+ww_status Session::commit() {
+  const ProbDev* hp = reinterpret_cast<const ProbDev*>(sv->host_probs);
+  order.clear();
+  for (int k = 0; k < (int)used.size(); ++k)
+    if (used[k]) order.push_back(k);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return hp[a].node_off < hp[b].node_off; });
+  n_total = 0;
+  t_high = 0;
+  max_nodes = 1;
+  std::vector<int32_t> border;
+  for (int k : order) {
+    const ProbDev& d = hp[k];
+    n_total += d.N;
+    t_high = std::max(t_high, d.tile_off + (int64_t)d.tiles_x * d.tiles_y);
+    max_nodes = std::max(max_nodes, d.N + 1);
+    for (int64_t t = 0; t < (int64_t)d.tiles_x * d.tiles_y; ++t) {
+      int64_t ti = t / d.tiles_x, tj = t % d.tiles_x;
+      if (ti == 0 || tj == 0 || ti == d.tiles_y - 1 || tj == d.tiles_x - 1) border.push_back((int32_t)(d.tile_off + t));
     }
   }
-  ws->stats.passes = pass;
-  ws->stats.ground_net = hctr->g_net;
-  WW_CUDA_TRY(cudaMemsetAsync(&dctr->total_cost, 0, sizeof(long long), s));
-  k_total_cost<<<grid_blocks(g.P, 256, sm_count * 16), 256, 0, s>>>(costs, flows, g.P, &dctr->total_cost);
-  k_write_result<<<1, 1, 0, s>>>(dctr, ground, st, dev_status, total_cost);
+  n_border = (int64_t)border.size();
+  cudaStream_t s = stream;
+  WW_CUDA_TRY(cudaMemcpyAsync(sv->probs, hp, used.size() * sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+  if (!order.empty()) {
+    WW_CUDA_TRY(cudaMemcpyAsync(sv->order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s));
+    WW_CUDA_TRY(cudaMemcpyAsync(sv->border, border.data(), border.size() * 4, cudaMemcpyHostToDevice, s));
+  }
+  // the host vectors above are pageable: those copies complete before returning
+  if (!pending.empty()) {
+    int64_t biggest = 1;
+    for (int k : pending) {
+      const ProbDev& d = hp[k];
+      biggest = std::max(biggest, d.N);
+      k_fill_tiles<<<grid_blocks(tiles_of(k), 256, 1024), 256, 0, s>>>(sv->tile_prob, d.tile_off, tiles_of(k), k);
+      WW_CUDA_TRY(cudaMemsetAsync(d.flows, 0, 2 * d.m * d.n, s));
+      WW_CUDA_TRY(cudaMemsetAsync(sv->prob_left + k, 0, 4, s));
+      WW_CUDA_TRY(cudaMemsetAsync(sv->g_net + k, 0, 8, s));
+      WW_CUDA_TRY(cudaMemsetAsync(sv->tc + k, 0, 8, s));
+    }
+    WW_CUDA_TRY(cudaMemcpyAsync(sv->slot_list, pending.data(), pending.size() * 4, cudaMemcpyHostToDevice, s));
+    dim3 gi(grid_blocks(biggest, 256, std::max(1, sm_count * 16 / (int)pending.size() + 1)), (unsigned)pending.size());
+    k_init_state<<<gi, 256, 0, s>>>(batch(), sv->slot_list, sv->excess, sv->cand, pot, sv->prob_left,
+                                    reinterpret_cast<McfCtr*>(sv->ctr));
+    pending.clear();
+  }
+  k_resume<<<1, 1, 0, s>>>(reinterpret_cast<McfCtr*>(sv->ctr), n_total);
   WW_CUDA_TRY(cudaGetLastError());
-  int32_t hst = 0;
-  WW_CUDA_TRY(cudaMemcpyAsync(&hst, dev_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  return WW_OK;
+}
+
+Batch Session::batch() const {
+  Batch b;
+  b.probs = reinterpret_cast<const ProbDev*>(sv->probs);
+  b.order = sv->order;
+  b.nact = (int)order.size();
+  b.tile_prob = sv->tile_prob;
+  b.g_index = g_index;
+  b.n_total = n_total;
+  b.t_total = t_high;
+  return b;
+}
+
+template <bool FWD>
+ww_status Session::enqueue_pass() {
+  cudaStream_t s = stream;
+  McfCtr* ctr = reinterpret_cast<McfCtr*>(sv->ctr);
+  SearchQ* q = reinterpret_cast<SearchQ*>(sv->q);
+  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(sv->events);
+  const Batch b = batch();
+  const McfCtr* hc = reinterpret_cast<const McfCtr*>(sv->host_ctr);
+  const int grid_cand = grid_blocks(std::max<int64_t>(1, hc->ncand) + n_border, 256, sm_count * 16);
+  const dim3 gn(grid_blocks(max_nodes, 256, std::max(1, sm_count * 16 / std::max(1, b.nact) + 1)),
+                (unsigned)std::max(1, b.nact));
+  const int grid_tiles = grid_blocks(t_high, 256, sm_count * 8);
+  k_pass_setup<<<1, 1, 0, s>>>(ctr, q);
+  k_init_labels<FWD><<<gn, 256, 0, s>>>(b, sv->excess, sv->labels, ctr);
+  k_seed_tiles<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->cand, ctr, sv->prob_left, sv->border,
+                                              (int32_t)n_border, q, sv->slots, sv->inq, search_grid);
+  WW_CUDA_TRY(cudaEventRecord(ev[0], s));
+  for (int band = 0; band < kBands; ++band) {
+    k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped);
+    k_count_found<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->labels, sv->cand, 0, ctr);
+    k_band_decide<<<1, 1, 0, s>>>(ctr, q, band == kBands - 2 ? 1 : 0);
+    if (band + 1 < kBands)
+      k_reseed<<<grid_tiles, 256, 0, s>>>(b, sv->capped, q, sv->slots, sv->inq, search_grid, ctr);
+  }
+  WW_CUDA_TRY(cudaEventRecord(ev[1], s));
+  k_clear_capped<<<grid_tiles, 256, 0, s>>>(b, sv->capped, ctr);
+  k_select<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, ctr);
+  k_augment<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, sv->g_net,
+                                           ctr);
+  k_reset_best<<<grid_cand, 256, 0, s>>>(b, sv->cand_root, sv->best, sv->prob_left, (int)sv->p_cap, ctr);
+  k_potentials<FWD><<<gn, 256, 0, s>>>(b, sv->labels, pot, ctr);
+  k_potential_ground<FWD><<<1, 1, 0, s>>>(b, pot, ctr);
+  k_compact<<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->cand, sv->prob_left, ctr);
+  k_finish_pass<<<1, 1, 0, s>>>(ctr);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}
+
+ww_status Session::pass(ww_solve_stats* st) {
+  McfCtr* hc = reinterpret_cast<McfCtr*>(sv->host_ctr);
+  ww_status e = (parity++ % 2 == 0) ? enqueue_pass<true>() : enqueue_pass<false>();
+  if (e != WW_OK) return e;
+  WW_CUDA_TRY(cudaMemcpyAsync(hc, sv->ctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, stream));
+  WW_CUDA_TRY(cudaStreamSynchronize(stream));
+  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(sv->events);
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && st) st->ms_search_gpu += ms;
+  if (st) {
+    st->augmentations += hc->naug;
+    st->passes = hc->passes;
+    st->search_iterations = hc->passes;
+    st->tile_visits = (int64_t)hc->tile_visits;
+    st->local_rounds = (int64_t)hc->local_rounds;
+    st->visit_cycles = (int64_t)hc->visit_cycles;
+  }
+  if (trace_enabled())
+    std::fprintf(stderr, "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu\n",
+                 hc->passes, hc->cap, ms, hc->naug, hc->D, hc->ncand, (unsigned long long)hc->tile_visits);
+  return WW_OK;
+}
+
+const McfCtr& Session::ctr() const { return *reinterpret_cast<const McfCtr*>(sv->host_ctr); }
+
+ww_status Session::left(std::vector<int32_t>* out) {
+  out->assign(used.size(), 0);
+  WW_CUDA_TRY(cudaMemcpyAsync(out->data(), sv->prob_left, used.size() * 4, cudaMemcpyDeviceToHost, stream));
+  WW_CUDA_TRY(cudaStreamSynchronize(stream));
+  return WW_OK;
+}
+
+ww_status Session::finalize(const std::vector<int>& list, std::vector<int32_t>* statuses) {
+  if (list.empty()) return WW_OK;
+  cudaStream_t s = stream;
+  const ProbDev* hp = reinterpret_cast<const ProbDev*>(sv->host_probs);
+  int64_t biggest = 1;
+  for (int k : list) {
+    biggest = std::max(biggest, hp[k].m * hp[k].n);
+    WW_CUDA_TRY(cudaMemsetAsync(sv->tc + k, 0, 8, s));
+  }
+  WW_CUDA_TRY(cudaMemcpyAsync(sv->slot_list, list.data(), list.size() * 4, cudaMemcpyHostToDevice, s));
+  const Batch b = batch();
+  dim3 gt(grid_blocks(biggest, 256, std::max(1, sm_count * 16 / (int)list.size() + 1)), (unsigned)list.size());
+  k_total_cost<<<gt, 256, 0, s>>>(b, sv->slot_list, sv->tc);
+  k_copy_pot<<<gt, 256, 0, s>>>(b, sv->slot_list, pot);
+  k_write_results<<<grid_blocks((int64_t)list.size(), 256, 64), 256, 0, s>>>(
+      b, sv->slot_list, (int)list.size(), reinterpret_cast<McfCtr*>(sv->ctr), sv->g_net, sv->tc, sv->status_all);
+  WW_CUDA_TRY(cudaGetLastError());
+  statuses->assign(list.size(), 0);
+  WW_CUDA_TRY(cudaMemcpyAsync(statuses->data(), sv->status_all, list.size() * 4, cudaMemcpyDeviceToHost, s));
   WW_CUDA_TRY(cudaStreamSynchronize(s));
-  ws->stats.tile_visits = (int64_t)hctr->tile_visits;
-  ws->stats.local_rounds = (int64_t)hctr->local_rounds;
-  ws->stats.visit_cycles = (int64_t)hctr->visit_cycles;
-  return hst;
+  return WW_OK;
+}
+
+ww_status solve_problems(const ProbHost* ph, int nprob, SolverWs* sv, const ww_params* prm, int64_t* pot_global,
+                         ww_solve_stats* stats, cudaStream_t s) {
+  if (nprob <= 0 || nprob > sv->p_cap) return WW_ERR_INVALID_ARG;
+  if (pot_global && nprob != 1) return WW_ERR_INVALID_ARG;
+  int64_t n_total = 0, t_total = 0;
+  for (int k = 0; k < nprob; ++k) {
+    n_total += (ph[k].m - 1) * (ph[k].n - 1);
+    t_total += tiles_for(ph[k].m, ph[k].n);
+  }
+  if (n_total > sv->n_cap || t_total > sv->t_cap || n_total >= (1ll << 31)) return WW_ERR_INVALID_ARG;
+  // a single problem may keep its potentials in the caller's array (ground last)
+  int64_t* pot = pot_global ? pot_global : sv->pot;
+  const int64_t g_index = pot_global ? (ph[0].m - 1) * (ph[0].n - 1) : sv->n_cap;
+  Session S(sv, pot, g_index, prm->max_passes, s);
+  if (S.err != WW_OK) return S.err;
+  int64_t node_off = 0, tile_off = 0;
+  std::vector<int> all;
+  for (int k = 0; k < nprob; ++k) {
+    ProbHost h = ph[k];
+    if (pot_global) h.pot_out = nullptr;
+    all.push_back(S.add(h, node_off, tile_off));
+    node_off += (h.m - 1) * (h.n - 1);
+    tile_off += tiles_for(h.m, h.n);
+  }
+  ww_status e = S.commit();
+  if (e != WW_OK) return e;
+  ww_solve_stats st{};
+  WW_CUDA_TRY(cudaMemcpyAsync(sv->host_ctr, sv->ctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, s));
+  WW_CUDA_TRY(cudaStreamSynchronize(s));
+  st.residues = S.ctr().ncand;
+  auto t0 = std::chrono::steady_clock::now();
+  while (S.ctr().go_on) {
+    e = S.pass(&st);
+    if (e != WW_OK) return e;
+  }
+  st.ms_other = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  std::vector<int32_t> sts;
+  e = S.finalize(all, &sts);
+  if (e != WW_OK) return e;
+  long long g0 = 0;
+  WW_CUDA_TRY(cudaMemcpy(&g0, sv->g_net + all[0], 8, cudaMemcpyDeviceToHost));
+  st.ground_net = g0;
+  if (stats) *stats = st;
+  for (int32_t x : sts)
+    if (x != WW_OK) return x;
+  return WW_OK;
 }
 
 // ---------------- certificate (harness) ----------------
