@@ -34,6 +34,8 @@ WORKLOADS = {
     "earthquake": dict(name="earthquake 8192x9000 complex64 L=50 (two strike-slip ruptures)", m=8192, n=9000),
     "lobes": dict(name="lobes 2048x2048 complex64 L=6 (decorrelated disk, 10% water)", m=2048, n=2048),
     "small": dict(name="ramp+bumps 256x256 float32 L=9", m=256, n=256),
+    "batched": dict(name="batched: uneven items U[256^2,2048^2], aspect 1:1-1:4, L in {4,9,16}", m=0, n=0),
+    "served": dict(name="served: Poisson arrivals, log-uniform 0.25-32 Mpixel, 150 GB budget", m=0, n=0),
 }
 
 # algorithmic bytes per node per search tile visit: labels read+write (16),
@@ -294,6 +296,190 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def _dev(x, torch):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return (t(x.ifg) if x.is_complex else t(x.phase)), t(x.coh), x.nlooks, t(x.mask)
+
+
+def run_batched(args):
+    """Batched form vs the same items unwrapped one at a time (ww_unwrap)."""
+    import torch
+
+    import paper_2609_36267_b300 as ww
+    from paper_2609_36267_b300 import synth
+
+    pool = [synth.batch_item(i) for i in range(args.pool)]
+    reqs = [_dev(pool[i % len(pool)], torch) for i in range(args.items)]
+    px = sum(r[0].shape[0] * r[0].shape[1] for r in reqs)
+    biggest = max(r[0].shape[0] * r[0].shape[1] for r in reqs)
+    batch = ww.Batch(len(reqs), px, biggest)
+    for L in (4.0, 9.0, 16.0):
+        ww.Lut.build(L)
+    costs = None
+    for _ in range(args.warmup):
+        out = ww.unwrap_batch(reqs, batch)
+        costs = [o[2] for o in out]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            out = ww.unwrap_batch(reqs, batch)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    assert [o[2] for o in out] == costs and all(o[3] == 0 for o in out)
+    st = batch.stats()
+    # plain: one request at a time through ww_unwrap (same items, same workspace size class)
+    m_max = max(r[0].shape[0] for r in reqs)
+    n_max = max(r[0].shape[1] for r in reqs)
+    ws = ww.Workspace(m_max, n_max)
+    plain_costs = []
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for r in reqs:
+        plain_costs.append(ww.unwrap(*r, ws=ws)[2])
+    p1.record()
+    torch.cuda.synchronize()
+    ms_plain = p0.elapsed_time(p1)
+    assert plain_costs == costs
+    line = {"metric": "Mpixel/s unwrapped at oracle-equal optimal cost", "value": px / (ms * 1e-3) / 1e6,
+            "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/fp32",
+            "data": f"synthetic: {args.items} items from a pool of {args.pool} generated items",
+            "config": {"workload": WORKLOADS["batched"]["name"], "items": args.items, "pixels": px},
+            "plain_sequential": {"value": px / (ms_plain * 1e-3) / 1e6, "unit": "Mpixel/s", "ms": ms_plain},
+            "speedup_vs_plain": ms_plain / ms, "solver": st, "clocks": clk.summary(),
+            "total_cost_sum": int(sum(costs))}
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args):
+    """Continuous-batching server vs a one-request-at-a-time loop on the same arrivals."""
+    import threading
+
+    import torch
+
+    import paper_2609_36267_b300 as ww
+    from paper_2609_36267_b300 import synth
+
+    rng = np.random.default_rng(5000)
+    t_gen = time.perf_counter()
+    base = [synth.config2(seed=5000 + i, m=4096, n=8192) for i in range(args.served_pool)]
+    t_gen = time.perf_counter() - t_gen
+    # sizes log-uniform in [0.25, 32] Mpixel, aspect 1:1..1:4 in a random orientation,
+    # cut as random crops (clamped to the 4096 x 8192 scenes) of the pre-generated pool
+    reqs = []
+    crops = {}
+    for k in range(args.requests):
+        npx = float(np.exp(rng.uniform(np.log(0.25e6), np.log(32e6))))
+        a = rng.uniform(1, 4)
+        short = max(16, int(round(np.sqrt(npx / a))))
+        long_ = max(16, int(round(npx / short)))
+        short, long_ = min(short, 4096), min(long_, 8192)
+        b = int(rng.integers(0, len(base)))
+        i0 = int(rng.integers(0, 4096 - short + 1))
+        j0 = int(rng.integers(0, 8192 - long_ + 1))
+        tr = bool(rng.uniform() < 0.5)
+        key = (b, short, long_, i0, j0, tr)
+        if len(crops) < args.distinct or key in crops:
+            if key not in crops:
+                x = base[b]
+                sl = (slice(i0, i0 + short), slice(j0, j0 + long_))
+                f = (lambda a_: np.ascontiguousarray(a_[sl].T if tr else a_[sl]))
+                d = lambda a_: torch.from_numpy(f(a_)).cuda()
+                crops[key] = (d(x.ifg), d(x.coh), x.nlooks, d(x.mask))
+            reqs.append(crops[key])
+        else:
+            reqs.append(list(crops.values())[k % len(crops)])
+    px_list = [r[0].shape[0] * r[0].shape[1] for r in reqs]
+    total_px = sum(px_list)
+    ww.Lut.build(6.0)
+    biggest = max(px_list)
+    ws = ww.Workspace(max(r[0].shape[0] for r in reqs), max(r[0].shape[1] for r in reqs))
+
+    def plain(r):
+        ww.unwrap(*r, ws=ws)
+        torch.cuda.synchronize()
+
+    for r in reqs[:4]:
+        plain(r)
+    t = time.perf_counter()
+    warm = min(32, len(reqs))
+    for r in reqs[:warm]:
+        plain(r)
+    plain_px_s = sum(px_list[:warm]) / (time.perf_counter() - t)
+    results = {}
+    costs_alone = {}
+    for load in args.loads:
+        rate = load * plain_px_s / (total_px / len(reqs))  # requests per second
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+        srv = ww.Server(hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_request_pixels=biggest,
+                        max_active=args.max_active)
+        tickets = [None] * len(reqs)
+        lat = [0.0] * len(reqs)
+        costs = [0] * len(reqs)
+        bad = []
+        ready = threading.Semaphore(0)
+
+        def waiter():
+            for k in range(len(reqs)):
+                ready.acquire()
+                out = srv.wait(tickets[k])
+                if out[3] != 0:
+                    bad.append((k, out[3]))
+                costs[k] = out[2]
+                lat[k] = out[4]
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        start = time.perf_counter()
+        for k, r in enumerate(reqs):
+            now = time.perf_counter() - start
+            if arrivals[k] > now:
+                time.sleep(arrivals[k] - now)
+            tickets[k] = srv.submit(*r)
+            ready.release()
+        th.join()
+        span = time.perf_counter() - start
+        st = srv.stats()
+        srv.close()
+        assert not bad, bad[:4]
+        # plain loop on the same arrivals (FIFO, one at a time); check equality of costs
+        plat = [0.0] * len(reqs)
+        start = time.perf_counter()
+        for k, r in enumerate(reqs):
+            now = time.perf_counter() - start
+            if arrivals[k] > now:
+                time.sleep(arrivals[k] - now)
+            tc = ww.unwrap(*r, ws=ws)[2]
+            torch.cuda.synchronize()
+            plat[k] = (time.perf_counter() - start - arrivals[k]) * 1e3
+            costs_alone[k] = tc
+        pspan = time.perf_counter() - start
+        mism = sum(1 for k in range(len(reqs)) if costs[k] != costs_alone[k])
+        results[f"load_{load:g}"] = {
+            "offered_req_per_s": rate,
+            "served": {"Mpixel_per_s": total_px / span / 1e6, "p50_ms": float(np.percentile(lat, 50)),
+                       "p99_ms": float(np.percentile(lat, 99)), "span_s": span, "stats": st},
+            "plain_loop": {"Mpixel_per_s": total_px / pspan / 1e6, "p50_ms": float(np.percentile(plat, 50)),
+                           "p99_ms": float(np.percentile(plat, 99)), "span_s": pspan},
+            "total_cost_mismatches_vs_alone": mism}
+    best = max(v["served"]["Mpixel_per_s"] for v in results.values())
+    line = {"metric": "Mpixel/s unwrapped at oracle-equal optimal cost", "value": best, "unit": "Mpixel/s",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/fp32",
+            "data": (f"synthetic: {args.requests} requests cropped from {args.served_pool} generated 4096x8192 "
+                     f"two-lobe scenes ({len(crops)} distinct crops, generation {t_gen:.0f} s)"),
+            "config": {"workload": WORKLOADS["served"]["name"], "requests": args.requests,
+                       "mean_Mpixel": total_px / len(reqs) / 1e6, "total_Gpixel": total_px / 1e9,
+                       "budget_gb": args.budget_gb, "max_active": args.max_active,
+                       "plain_loop_Mpixel_per_s_at_start": plain_px_s / 1e6},
+            "loads": results}
+    print(json.dumps(line), flush=True)
+
+
 def launch_count(st, steps):
     """Kernels of this library launched per timed step, times steps."""
     grid = 12  # residues, costs, steep plan/hist x2/find x2/ties/scan/zero, integrate col0/rows
@@ -310,7 +496,19 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="earthquake")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--items", type=int, default=512, help="batched: items per batch")
+    ap.add_argument("--pool", type=int, default=32, help="batched/served: distinct generated inputs")
+    ap.add_argument("--requests", type=int, default=2000, help="served: requests in the stream")
+    ap.add_argument("--served-pool", type=int, default=3, help="served: generated 4096x8192 scenes to crop")
+    ap.add_argument("--distinct", type=int, default=64, help="served: distinct crops kept on the device")
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.7, 1.5], help="served: offered load vs plain")
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--max-active", type=int, default=256)
     args = ap.parse_args()
+    if args.impl == "ours" and args.workload == "batched":
+        return run_batched(args)
+    if args.impl == "ours" and args.workload == "served":
+        return run_served(args)
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -221,6 +221,43 @@ ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* 
                           ww_stream stream);
 ww_status ww_batch_stats(const ww_batch* b, ww_solve_stats* out);
 
+/* ---- Served form: continuous batching ----
+ * A server owns a worker thread, a CUDA stream and one running multi-problem
+ * solve.  Submitted requests wait in FIFO order; between solver passes the
+ * worker admits as many as the device-memory budget and max_active allow
+ * (residues and costs computed on admission, state kept resident), retires the
+ * requests whose imbalance reached zero (integration into the caller's output
+ * buffers, total cost, status) and runs the next pass over all requests in
+ * flight, so new requests join while others are on the GPU.  A request's device
+ * buffers (ww_batch_item fields) must hold their inputs when it is submitted
+ * and stay valid until it completes.  Requests larger than max_request_pixels
+ * or than the budget are rejected at submit (WW_ERR_INVALID_ARG). */
+typedef struct ww_server_config {
+  int64_t hbm_budget_bytes;   /* device memory for resident request state */
+  int64_t max_request_pixels; /* largest request accepted */
+  int32_t max_active;         /* requests in flight at once */
+  int32_t reserved[7];
+} ww_server_config;
+typedef struct ww_server ww_server;
+typedef struct ww_server_stats {
+  int64_t submitted, admitted, completed, rejected, passes, peak_active, peak_resident_bytes;
+  double busy_ms;
+} ww_server_stats;
+ww_status ww_server_create(const ww_server_config* cfg, const ww_params* params, ww_server** out);
+/* Queue a request; *ticket identifies it. */
+ww_status ww_server_submit(ww_server* s, const ww_batch_item* req, int64_t* ticket);
+/* *done = 1 once finished; then result->total_cost / status and *latency_ms
+ * (submit to completion) are filled in (result and latency_ms may be NULL). */
+ww_status ww_server_poll(ww_server* s, int64_t ticket, int32_t* done, ww_batch_item* result, double* latency_ms);
+/* Block until the ticket finishes or timeout_ms passes (WW_ERR_TIMEOUT). */
+ww_status ww_server_wait(ww_server* s, int64_t ticket, double timeout_ms, ww_batch_item* result,
+                         double* latency_ms);
+/* Forget a finished ticket. */
+ww_status ww_server_release(ww_server* s, int64_t ticket);
+ww_status ww_server_get_stats(ww_server* s, ww_server_stats* out);
+/* Finishes the requests already submitted, then stops. */
+void ww_server_destroy(ww_server* s);
+
 /* ---- Harness: optimality certificate on the GPU ----
  * Counts violations into counts (device int64[4]): [0] |dk|>1 or flow on a
  * non-existent edge, [1] nodes (G included) whose out-in flow differs from the

@@ -64,6 +64,20 @@ class BatchItem(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_request_pixels", ctypes.c_int64),
+                ("max_active", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("passes", ctypes.c_int64), ("peak_active", ctypes.c_int64),
+                ("peak_resident_bytes", ctypes.c_int64), ("busy_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -102,9 +116,19 @@ def lib():
         L.ww_batch_bytes.restype = i64
         L.ww_unwrap_batch.argtypes = [ctypes.POINTER(BatchItem), i64, ctypes.POINTER(Params), P, P]
         L.ww_batch_stats.argtypes = [P, ctypes.POINTER(SolveStats)]
+        L.ww_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(Params), ctypes.POINTER(P)]
+        L.ww_server_submit.argtypes = [P, ctypes.POINTER(BatchItem), ctypes.POINTER(i64)]
+        L.ww_server_poll.argtypes = [P, i64, ctypes.POINTER(i32), ctypes.POINTER(BatchItem),
+                                     ctypes.POINTER(ctypes.c_double)]
+        L.ww_server_wait.argtypes = [P, i64, ctypes.c_double, ctypes.POINTER(BatchItem),
+                                     ctypes.POINTER(ctypes.c_double)]
+        L.ww_server_release.argtypes = [P, i64]
+        L.ww_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+        L.ww_server_destroy.argtypes = [P]
         for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
                   "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_get_solve_stats", "ww_integrate", "ww_unwrap",
-                  "ww_certificate", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats"):
+                  "ww_certificate", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_server_create",
+                  "ww_server_submit", "ww_server_poll", "ww_server_wait", "ww_server_release", "ww_server_get_stats"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -386,3 +410,68 @@ def unwrap_batch(requests, batch: Batch | None = None, params: Params | None = N
     if check:
         _check(st, "ww_unwrap_batch")
     return [(u, k, arr[i].total_cost, arr[i].status) for i, (u, k) in enumerate(outs)]
+
+
+class Server:
+    """Continuous-batching unwrap server (library worker thread + CUDA stream).
+
+    submit() synchronises the caller's current stream so the request's inputs are
+    ready, then queues it; wait() returns (unwrapped, cycles, total_cost, status,
+    latency_ms).  Tensors are kept alive until the request completes."""
+
+    def __init__(self, hbm_budget_bytes: int, max_request_pixels: int, max_active: int = 64,
+                 params: Params | None = None):
+        cfg = ServerConfig(int(hbm_budget_bytes), int(max_request_pixels), int(max_active))
+        h = ctypes.c_void_p()
+        prm = params or default_params()
+        _check(lib().ww_server_create(ctypes.byref(cfg), ctypes.byref(prm), ctypes.byref(h)), "ww_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, ifg, coh, nlooks, mask=None, out=None) -> int:
+        torch = _torch()
+        m, n = ifg.shape
+        if out is None:
+            unw = torch.empty((m, n), dtype=torch.float32, device=ifg.device)
+            cyc = torch.empty((m, n), dtype=torch.int32, device=ifg.device)
+        else:
+            unw, cyc = out
+        torch.cuda.current_stream().synchronize()
+        p, c = _ifg(ifg)
+        item = BatchItem(p.value, c, _ptr(coh).value, _ptr(mask).value if mask is not None else None, m, n,
+                         float(nlooks), unw.data_ptr(), cyc.data_ptr(), 0, 0)
+        t = ctypes.c_int64()
+        _check(lib().ww_server_submit(self._h, ctypes.byref(item), ctypes.byref(t)), "ww_server_submit")
+        self._keep[t.value] = (ifg, coh, mask, unw, cyc)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int32()
+        _check(lib().ww_server_poll(self._h, int(ticket), ctypes.byref(d), None, None), "ww_server_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: float = 600000.0):
+        res = BatchItem()
+        lat = ctypes.c_double()
+        _check(lib().ww_server_wait(self._h, int(ticket), float(timeout_ms), ctypes.byref(res), ctypes.byref(lat)),
+               "ww_server_wait")
+        _, _, _, unw, cyc = self._keep.pop(ticket)
+        lib().ww_server_release(self._h, int(ticket))
+        return unw, cyc, res.total_cost, res.status, lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().ww_server_get_stats(self._h, ctypes.byref(st)), "ww_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().ww_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

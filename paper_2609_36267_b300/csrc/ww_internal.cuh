@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/ww.h"
 
 namespace ww {
@@ -237,6 +239,43 @@ ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, co
                            const int8_t* flows, int64_t m, int64_t n, float* unw, int32_t* cyc,
                            cudaStream_t s);
 // ww_mcf.cu
+struct Batch;
+struct McfCtr;
+// A solve over a changing set of problems: problems join (add + commit) and
+// leave (finalize + remove) between passes; passes alternate forward/reverse.
+// All problems share the free ground node (potential at pot[g_index]).
+class Session {
+ public:
+  Session(SolverWs* sv, int64_t* pot, int64_t g_index, int max_passes, cudaStream_t s);
+  int next_slot() const;                                            // slot the next add() takes, -1 if full
+  int add(const ProbHost& ph, int64_t node_off, int64_t tile_off);  // -> slot, or -1 if full
+  void remove(int slot);
+  ww_status commit();                                               // upload layout, initialise joiners
+  ww_status pass(ww_solve_stats* st);                               // one pass, then a host sync
+  ww_status left(std::vector<int32_t>* out);                        // imbalanced nodes per slot
+  ww_status finalize(const std::vector<int>& slots, std::vector<int32_t>* statuses);
+  const McfCtr& ctr() const;
+  int32_t status() const;
+  int32_t ncand() const;
+  bool go_on() const;
+  int64_t tiles_of(int slot) const;
+  ww_status err = WW_OK;
+
+ private:
+  template <bool FWD>
+  ww_status enqueue_pass();
+  Batch batch() const;
+  SolverWs* sv;
+  int64_t* pot;
+  int64_t g_index;
+  cudaStream_t stream;
+  int sm_count = 148, search_grid = 592;
+  std::vector<char> used;
+  std::vector<int> order, pending;
+  int64_t n_total = 0, t_high = 0, max_nodes = 1, n_border = 0;
+  int parity = 0;
+};
+
 ww_status solve_problems(const ProbHost* probs, int nprob, SolverWs* sv, const ww_params* prm, int64_t* pot_global,
                          ww_solve_stats* stats, cudaStream_t s);
 ww_status launch_certificate(const int8_t* res, const int32_t* ground, const int16_t* costs,

@@ -95,8 +95,6 @@ struct McfCtr {
   int64_t n_cap_nodes; // node capacity (the candidate list halves are this far apart)
 };
 
-namespace {
-
 // Problems live in slots (stable ids); `order` lists the active slots sorted by
 // node offset.  The shared ground potential sits at pot[g_index].
 struct Batch {
@@ -118,6 +116,8 @@ __device__ __forceinline__ int prob_of_node(const Batch& b, int64_t v) {
   }
   return b.order[lo];
 }
+
+namespace {
 
 // Raw residual cost of the arc entering node (i,j) from direction dir (forward
 // search: arc u->v) or leaving it toward dir (reverse search: arc v->u).
@@ -940,36 +940,6 @@ __global__ void k_resume(McfCtr* ctr, int64_t n_total) {
 
 }  // namespace
 
-// A solve over a changing set of problems: problems join (add + commit) and
-// leave (finalize + remove) between passes; passes alternate forward/reverse.
-class Session {
- public:
-  Session(SolverWs* sv, int64_t* pot, int64_t g_index, int max_passes, cudaStream_t s);
-  int add(const ProbHost& ph, int64_t node_off, int64_t tile_off);  // -> slot, or -1 if full
-  void remove(int slot);
-  ww_status commit();                                               // upload layout, initialise joiners
-  ww_status pass(ww_solve_stats* st);                               // one pass, then a host sync
-  ww_status left(std::vector<int32_t>* out);                        // imbalanced nodes per slot
-  ww_status finalize(const std::vector<int>& slots, std::vector<int32_t>* statuses);
-  const McfCtr& ctr() const;
-  int64_t tiles_of(int slot) const;
-  ww_status err = WW_OK;
-
- private:
-  template <bool FWD>
-  ww_status enqueue_pass();
-  Batch batch() const;
-  SolverWs* sv;
-  int64_t* pot;
-  int64_t g_index;
-  cudaStream_t stream;
-  int sm_count = 148, search_grid = 592;
-  std::vector<char> used;
-  std::vector<int> order, pending;
-  int64_t n_total = 0, t_high = 0, max_nodes = 1, n_border = 0;
-  int parity = 0;
-};
-
 Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, int max_passes, cudaStream_t s)
     : sv(sv_), pot(pot_), g_index(g_index_), stream(s) {
   int dev = 0;
@@ -1152,6 +1122,14 @@ ww_status Session::pass(ww_solve_stats* st) {
 }
 
 const McfCtr& Session::ctr() const { return *reinterpret_cast<const McfCtr*>(sv->host_ctr); }
+int32_t Session::status() const { return ctr().status; }
+int32_t Session::ncand() const { return ctr().ncand; }
+bool Session::go_on() const { return ctr().go_on != 0; }
+int Session::next_slot() const {
+  for (int k = 0; k < (int)used.size(); ++k)
+    if (!used[k]) return k;
+  return -1;
+}
 
 ww_status Session::left(std::vector<int32_t>* out) {
   out->assign(used.size(), 0);
@@ -1212,9 +1190,9 @@ ww_status solve_problems(const ProbHost* ph, int nprob, SolverWs* sv, const ww_p
   ww_solve_stats st{};
   WW_CUDA_TRY(cudaMemcpyAsync(sv->host_ctr, sv->ctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, s));
   WW_CUDA_TRY(cudaStreamSynchronize(s));
-  st.residues = S.ctr().ncand;
+  st.residues = S.ncand();
   auto t0 = std::chrono::steady_clock::now();
-  while (S.ctr().go_on) {
+  while (S.go_on()) {
     e = S.pass(&st);
     if (e != WW_OK) return e;
   }
