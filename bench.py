@@ -48,9 +48,9 @@ def make_input(workload: str):
     from paper_2609_36267_b300 import synth
 
     if workload == "earthquake":
-        return synth.config3()
+        return synth.cached("config3")
     if workload == "lobes":
-        return synth.config2()
+        return synth.cached("config2")
     return synth.config1()
 
 
@@ -225,9 +225,15 @@ def run_ours(args, rank, world, local):
     host_unw = torch.empty((m, n), dtype=torch.float32).pin_memory()
     ww.Lut.build(x.nlooks)  # one-time FP64 table per number of looks (cached)
     stream = torch.cuda.current_stream()
+    # host-driven pass loop: CUDA events bracket every search launch, which the
+    # roofline below needs (inside the graph-resident loop no event can be recorded)
+    prm = ww.default_params()
+    for k, v in json.loads(args.params).items():
+        setattr(prm, k, int(v))
+    prm.graph_loop = 0
     costs_seen = set()
     for _ in range(args.warmup):
-        _, _, tc = ww.unwrap(ifg, coh, x.nlooks, mask, ws=ws, out=(unw, cyc))
+        _, _, tc = ww.unwrap(ifg, coh, x.nlooks, mask, ws=ws, out=(unw, cyc), params=prm)
         costs_seen.add(tc)
     torch.cuda.synchronize()
     # ---- device-resident timed region ----
@@ -239,7 +245,7 @@ def run_ours(args, rank, world, local):
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            _, _, tc = ww.unwrap(ifg, coh, x.nlooks, mask, ws=ws, out=(unw, cyc))
+            _, _, tc = ww.unwrap(ifg, coh, x.nlooks, mask, ws=ws, out=(unw, cyc), params=prm)
             costs_seen.add(tc)
             stats_acc.append(ws.stats())
         e1.record(stream)
@@ -258,7 +264,7 @@ def run_ours(args, rank, world, local):
         ifg.copy_(host_ifg, non_blocking=True)
         coh.copy_(host_coh, non_blocking=True)
         mask.copy_(host_mask, non_blocking=True)
-        _, _, tc = ww.unwrap(ifg, coh, x.nlooks, mask, ws=ws, out=(unw, cyc))
+        _, _, tc = ww.unwrap(ifg, coh, x.nlooks, mask, ws=ws, out=(unw, cyc), params=prm)
         host_unw.copy_(unw, non_blocking=True)
         costs_seen.add(tc)
     t1.record(stream)
@@ -284,13 +290,16 @@ def run_ours(args, rank, world, local):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/fp32",
                 "data": "synthetic (seeded generator; inputs 0.96 GB > L2, no flush needed)",
                 "config": {"workload": wl["name"], "pixels": px, "replicas": world,
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "schedule": {k: getattr(prm, k) for k in ("full_passes", "band_start_ppm", "band_min",
+                                                                     "band_mult", "band_growth",
+                                                                     "search_ctas_per_sm")}},
                 "e2e": {"value": px * world / (ms_e2e * 1e-3) / 1e6, "unit": "Mpixel/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": None, "roofline": roof, "cpu_baseline": base, "clocks": clk.summary(),
                 "solver": {k: st[k] for k in ("passes", "augmentations", "search_iterations", "tile_visits",
                                                  "residues", "ms_search_gpu", "ms_other", "local_rounds",
-                                                 "visit_cycles")},
+                                                 "visit_cycles", "load_cycles", "relax_cycles")},
                 "total_costs_seen": sorted(costs_seen)}
         line["gpu_launches"] = launch_count(st, args.steps)
         print(json.dumps(line), flush=True)
@@ -301,6 +310,19 @@ def _dev(x, torch):
     return (t(x.ifg) if x.is_complex else t(x.phase)), t(x.coh), x.nlooks, t(x.mask)
 
 
+def _generate(fn, indices):
+    """Generate synthetic inputs in spawned worker processes (safe after CUDA init)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    indices = list(indices)
+    workers = max(1, min(len(indices), (os.cpu_count() or 1), 32))
+    if workers == 1:
+        return [fn(i) for i in indices]
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, indices, chunksize=max(1, len(indices) // (4 * workers))))
+
+
 def run_batched(args):
     """Batched form vs the same items unwrapped one at a time (ww_unwrap)."""
     import torch
@@ -308,28 +330,39 @@ def run_batched(args):
     import paper_2609_36267_b300 as ww
     from paper_2609_36267_b300 import synth
 
-    pool = [synth.batch_item(i) for i in range(args.pool)]
+    pool = _generate(synth.batch_item, range(min(args.pool, args.items)))
     reqs = [_dev(pool[i % len(pool)], torch) for i in range(args.items)]
     px = sum(r[0].shape[0] * r[0].shape[1] for r in reqs)
     biggest = max(r[0].shape[0] * r[0].shape[1] for r in reqs)
     batch = ww.Batch(len(reqs), px, biggest)
     for L in (4.0, 9.0, 16.0):
         ww.Lut.build(L)
+    # schedule picked by the autotuner on a separate sample of the same workload
+    prm, tune = ww.default_params(), None
+    if args.tune_items > 0:
+        sample = [_dev(x, torch) for x in _generate(synth.batch_item, range(100000, 100000 + args.tune_items))]
+        prm, tune = ww.autotune_batch(sample, repeats=2)
+        tune["params"] = {k: getattr(prm, k) for k in ("graph_loop", "search_ctas_per_sm", "band_min", "band_mult",
+                                                        "band_growth", "band_start_ppm", "full_passes")}
+        del sample
     costs = None
     for _ in range(args.warmup):
-        out = ww.unwrap_batch(reqs, batch)
+        out = ww.unwrap_batch(reqs, batch, params=prm)
         costs = [o[2] for o in out]
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         e0.record()
         for _ in range(args.steps):
-            out = ww.unwrap_batch(reqs, batch)
+            out = ww.unwrap_batch(reqs, batch, params=prm)
         e1.record()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     assert [o[2] for o in out] == costs and all(o[3] == 0 for o in out)
     st = batch.stats()
+    if args.skip_plain:
+        print(json.dumps({"workload": "batched", "ms_per_step": ms, "pixels": px, "tune": tune}), flush=True)
+        return
     # plain: one request at a time through ww_unwrap (same items, same workspace size class)
     m_max = max(r[0].shape[0] for r in reqs)
     n_max = max(r[0].shape[1] for r in reqs)
@@ -350,9 +383,15 @@ def run_batched(args):
             "data": f"synthetic: {args.items} items from a pool of {args.pool} generated items",
             "config": {"workload": WORKLOADS["batched"]["name"], "items": args.items, "pixels": px},
             "plain_sequential": {"value": px / (ms_plain * 1e-3) / 1e6, "unit": "Mpixel/s", "ms": ms_plain},
-            "speedup_vs_plain": ms_plain / ms, "solver": st, "clocks": clk.summary(),
+            "speedup_vs_plain": ms_plain / ms, "autotune": tune, "solver": st, "clocks": clk.summary(),
             "total_cost_sum": int(sum(costs))}
     print(json.dumps(line), flush=True)
+
+
+def _served_scene(i):
+    from paper_2609_36267_b300 import synth
+
+    return synth.config2(seed=5000 + i, m=4096, n=8192)
 
 
 def run_served(args):
@@ -366,7 +405,7 @@ def run_served(args):
 
     rng = np.random.default_rng(5000)
     t_gen = time.perf_counter()
-    base = [synth.config2(seed=5000 + i, m=4096, n=8192) for i in range(args.served_pool)]
+    base = _generate(_served_scene, range(args.served_pool))
     t_gen = time.perf_counter() - t_gen
     # sizes log-uniform in [0.25, 32] Mpixel, aspect 1:1..1:4 in a random orientation,
     # cut as random crops (clamped to the 4096 x 8192 scenes) of the pre-generated pool
@@ -481,10 +520,12 @@ def run_served(args):
 
 
 def launch_count(st, steps):
-    """Kernels of this library launched per timed step, times steps."""
+    """Kernels of this library launched per timed step (host-driven pass loop), times steps."""
     grid = 12  # residues, costs, steep plan/hist x2/find x2/ties/scan/zero, integrate col0/rows
-    solver_fixed = 3  # init_state, total_cost, write_result
-    per_pass = 9  # init_labels, seed_tiles, search, select, augment, reset_best, potentials, compact, finish
+    solver_fixed = 6  # join, init_state, resume, total_cost, copy_pot, write_results
+    # pass_setup, init_labels, seed_tiles, 4 bands x (search, count_found, band_decide) + 3 reseeds,
+    # clear_capped, select, augment, reset_best, potentials, potential_ground, compact, finish_pass
+    per_pass = 26
     return int((grid + solver_fixed + st["passes"] * per_pass) * steps)
 
 
@@ -497,11 +538,14 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="earthquake")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--items", type=int, default=512, help="batched: items per batch")
-    ap.add_argument("--pool", type=int, default=32, help="batched/served: distinct generated inputs")
+    ap.add_argument("--pool", type=int, default=512, help="batched: distinct generated items (reused cyclically)")
     ap.add_argument("--requests", type=int, default=2000, help="served: requests in the stream")
     ap.add_argument("--served-pool", type=int, default=3, help="served: generated 4096x8192 scenes to crop")
     ap.add_argument("--distinct", type=int, default=64, help="served: distinct crops kept on the device")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.7, 1.5], help="served: offered load vs plain")
+    ap.add_argument("--tune-items", type=int, default=64, help="batched: autotuner sample size (0 = defaults)")
+    ap.add_argument("--params", default="{}", help="solver schedule overrides, JSON (e.g. '{\"full_passes\": 0}')")
+    ap.add_argument("--skip-plain", action="store_true", help="batched: no one-at-a-time comparison (profiling)")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--max-active", type=int, default=256)
     args = ap.parse_args()

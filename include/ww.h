@@ -79,7 +79,20 @@ typedef struct ww_params {
   int32_t max_sweeps;       /* tile-sweep limit per shortest-path search (default 1000000) */
   int32_t tile_rows;        /* search tile height in nodes (0 = auto) */
   int32_t radius_policy;    /* 0 = full search each pass (default) */
-  int32_t reserved[9];
+  int32_t graph_loop;       /* 1 = the pass loop runs on the device inside one CUDA graph launch
+                               (conditional while node; default), 0 = one host sync per pass */
+  /* search schedule: the optimum does not depend on it (ww_autotune_batch picks it).
+   * A banded pass searches only up to a distance cap; if no imbalanced node is
+   * reached below the cap, the cap widens (x band_growth, at most three times,
+   * the last time to no cap) and the search resumes from the tiles that were cut. */
+  int32_t search_ctas_per_sm; /* persistent search CTAs per SM, 0 = as many as fit (default) */
+  int32_t band_min;         /* smallest cap of a banded pass (default 1024), >= 1 */
+  int32_t band_mult;        /* cap = max(band_min, band_mult x the last augmented distance) (4) */
+  int32_t band_growth;      /* cap widening factor, 2..64 (8) */
+  int32_t band_start_ppm;   /* passes are banded once fewer than this many per million nodes are
+                               imbalanced (default 1000000 = always) */
+  int32_t full_passes;      /* the first passes search without a cap (default 0) */
+  int32_t reserved[2];
 } ww_params;
 void ww_params_default(ww_params* p);
 
@@ -171,6 +184,8 @@ typedef struct ww_solve_stats {
   double ms_search_gpu;  /* device time of the search kernel launches (CUDA events) */
   int64_t local_rounds;  /* directional-scan rounds summed over tile visits */
   int64_t visit_cycles;  /* SM clock cycles summed over tile visits */
+  int64_t load_cycles;   /* of which: loading labels and computing reduced arc costs */
+  int64_t relax_cycles;  /* of which: the local fixed point (directional scans) */
 } ww_solve_stats;
 ww_status ww_get_solve_stats(const ww_workspace* ws, ww_solve_stats* out);
 
@@ -194,8 +209,10 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
  * m x n).  All items are solved together: their node grids are independent
  * (no arcs between items) and they share one free ground node, which leaves
  * each item's optimum unchanged because every item's supplies sum to zero.
- * One persistent search launch per pass covers the tiles of all unfinished
- * items.  Residues, costs and integration run per item on the same stream.
+ * One launch per grid step (residues, costs, integration) covers every item,
+ * and one persistent search launch per pass covers the tiles of all unfinished
+ * items; with params->graph_loop the whole pass loop is a single CUDA graph
+ * launch whose loop condition is set on the device.
  * On return total_cost and status are filled in for every item. */
 typedef struct ww_batch_item {
   const void* ifg;        /* float32 phase or interleaved complex64 [m][n] */
@@ -220,6 +237,25 @@ int64_t ww_batch_bytes(int64_t max_items, int64_t max_pixels, int64_t max_item_p
 ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* params, ww_batch* b,
                           ww_stream stream);
 ww_status ww_batch_stats(const ww_batch* b, ww_solve_stats* out);
+
+/* Autotuner of the search schedule (no counterpart in the paper, whose CPU
+ * solver has fixed settings).  Unwraps `items` (a sample of the workload to
+ * tune for) with the starting parameters, then walks the knobs one at a time
+ * (full_passes, band_start_ppm, band_min, band_mult, band_growth, search CTAs
+ * per SM, graph loop), keeping a value when it lowers the device time of the whole batched
+ * unwrap (CUDA events, best of `repeats` runs).  Every trial must reproduce the
+ * first trial's total cost for every item (the optimum is unique in cost even
+ * where flows tie); otherwise WW_ERR_INTERNAL.  *best receives the chosen
+ * parameters (all other fields copied from *start, or the defaults).  The
+ * items' outputs are overwritten.  Synchronises the stream. */
+typedef struct ww_tune_report {
+  int32_t trials;
+  float default_ms;   /* device time with *start */
+  float best_ms;      /* device time with *best */
+  int32_t reserved[5];
+} ww_tune_report;
+ww_status ww_autotune_batch(ww_batch_item* items, int64_t count, const ww_params* start, ww_batch* b,
+                            int32_t repeats, ww_params* best, ww_tune_report* report, ww_stream stream);
 
 /* ---- Served form: continuous batching ----
  * A server owns a worker thread, a CUDA stream and one running multi-problem

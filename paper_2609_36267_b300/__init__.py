@@ -42,7 +42,11 @@ class Params(ctypes.Structure):
     _fields_ = [("box_half_width", ctypes.c_int32), ("steep_rad", ctypes.c_float),
                 ("steep_cap_ppm", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("max_sweeps", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-                ("radius_policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("radius_policy", ctypes.c_int32), ("graph_loop", ctypes.c_int32),
+                ("search_ctas_per_sm", ctypes.c_int32), ("band_min", ctypes.c_int32),
+                ("band_mult", ctypes.c_int32), ("band_growth", ctypes.c_int32),
+                ("band_start_ppm", ctypes.c_int32), ("full_passes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class SolveStats(ctypes.Structure):
@@ -51,7 +55,8 @@ class SolveStats(ctypes.Structure):
                 ("residues", ctypes.c_int64), ("ground_net", ctypes.c_int64),
                 ("ms_search", ctypes.c_double), ("ms_other", ctypes.c_double),
                 ("ms_search_gpu", ctypes.c_double), ("local_rounds", ctypes.c_int64),
-                ("visit_cycles", ctypes.c_int64)]
+                ("visit_cycles", ctypes.c_int64), ("load_cycles", ctypes.c_int64),
+                ("relax_cycles", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -116,6 +121,8 @@ def lib():
         L.ww_batch_bytes.restype = i64
         L.ww_unwrap_batch.argtypes = [ctypes.POINTER(BatchItem), i64, ctypes.POINTER(Params), P, P]
         L.ww_batch_stats.argtypes = [P, ctypes.POINTER(SolveStats)]
+        L.ww_autotune_batch.argtypes = [ctypes.POINTER(BatchItem), i64, ctypes.POINTER(Params), P, i32,
+                                        ctypes.POINTER(Params), ctypes.POINTER(TuneReport), P]
         L.ww_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(Params), ctypes.POINTER(P)]
         L.ww_server_submit.argtypes = [P, ctypes.POINTER(BatchItem), ctypes.POINTER(i64)]
         L.ww_server_poll.argtypes = [P, i64, ctypes.POINTER(i32), ctypes.POINTER(BatchItem),
@@ -127,7 +134,8 @@ def lib():
         L.ww_server_destroy.argtypes = [P]
         for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
                   "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_get_solve_stats", "ww_integrate", "ww_unwrap",
-                  "ww_certificate", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_server_create",
+                  "ww_certificate", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_autotune_batch",
+                  "ww_server_create",
                   "ww_server_submit", "ww_server_poll", "ww_server_wait", "ww_server_release", "ww_server_get_stats"):
             getattr(L, f).restype = i32
         _lib = L
@@ -385,9 +393,7 @@ class Batch:
             pass
 
 
-def unwrap_batch(requests, batch: Batch | None = None, params: Params | None = None, check=True):
-    """requests: list of (ifg, coh, nlooks, mask) device tensors.  Returns a list
-    of (unwrapped, cycles, total_cost, status) in the same order."""
+def _batch_items(requests):
     torch = _torch()
     outs = []
     arr = (BatchItem * len(requests))()
@@ -403,6 +409,33 @@ def unwrap_batch(requests, batch: Batch | None = None, params: Params | None = N
         outs.append((unw, cyc))
         total += m * n
         biggest = max(biggest, m * n)
+    return arr, outs, total, biggest
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("trials", ctypes.c_int32), ("default_ms", ctypes.c_float), ("best_ms", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+def autotune_batch(requests, batch: Batch | None = None, start: Params | None = None, repeats: int = 2):
+    """Pick the search schedule for a batched workload from a sample of it
+    (requests as for unwrap_batch).  -> (Params, {"trials", "default_ms", "best_ms"})."""
+    arr, outs, total, biggest = _batch_items(requests)
+    if batch is None:
+        batch = Batch(len(requests), total, biggest)
+    best = Params()
+    rep = TuneReport()
+    _check(lib().ww_autotune_batch(arr, len(requests), ctypes.byref(start or default_params()), batch.handle,
+                                   int(repeats), ctypes.byref(best), ctypes.byref(rep), _stream()),
+           "ww_autotune_batch")
+    del outs
+    return best, {"trials": rep.trials, "default_ms": rep.default_ms, "best_ms": rep.best_ms}
+
+
+def unwrap_batch(requests, batch: Batch | None = None, params: Params | None = None, check=True):
+    """requests: list of (ifg, coh, nlooks, mask) device tensors.  Returns a list
+    of (unwrapped, cycles, total_cost, status) in the same order."""
+    arr, outs, total, biggest = _batch_items(requests)
     if batch is None:
         batch = Batch(len(requests), total, biggest)
     prm = params or default_params()

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -44,12 +45,17 @@ bool grid_ok(int64_t m, int64_t n) {
          m * n < (1ll << 40);
 }
 
-bool params_ok(const ww_params* p) {
-  return p && p->box_half_width >= 0 && p->box_half_width <= 3 && p->steep_cap_ppm >= 0 &&
-         p->steep_cap_ppm <= 1000000 && p->max_passes > 0 && p->max_sweeps > 0 && std::isfinite(p->steep_rad);
-}
+bool params_ok(const ww_params* p) { return ww::params_valid(p); }
 
 }  // namespace
+
+bool ww::params_valid(const ww_params* p) {
+  return p && p->box_half_width >= 0 && p->box_half_width <= 3 && p->steep_cap_ppm >= 0 &&
+         p->steep_cap_ppm <= 1000000 && p->max_passes > 0 && p->max_sweeps > 0 && std::isfinite(p->steep_rad) &&
+         (p->graph_loop == 0 || p->graph_loop == 1) && p->search_ctas_per_sm >= 0 && p->search_ctas_per_sm <= 64 &&
+         p->band_min >= 1 && p->band_mult >= 0 && p->band_mult <= 1024 && p->band_growth >= 2 &&
+         p->band_growth <= 64 && p->band_start_ppm >= 0 && p->band_start_ppm <= 1000000 && p->full_passes >= 0;
+}
 
 namespace ww {
 
@@ -109,6 +115,13 @@ void ww_params_default(ww_params* p) {
   p->max_sweeps = 1000000;
   p->tile_rows = 0;
   p->radius_policy = 0;
+  p->graph_loop = 1;
+  p->search_ctas_per_sm = 0;
+  p->band_min = 1024;
+  p->band_mult = 4;
+  p->band_growth = 8;
+  p->band_start_ppm = 1000000;
+  p->full_passes = 0;
 }
 
 ww_status ww_build_lut(double nlooks, ww_lut** out) {
@@ -324,8 +337,8 @@ struct ww_batch {
   int8_t* flows;        // [2 * max_pixels]
   int64_t* total_cost;  // [max_items]
   int32_t* status;      // [max_items]
-  // steep selection scratch, reused item after item (stream-ordered)
-  ww_workspace steep;
+  // item table of the batched grid launches
+  ww::GridBatch grid;
   ww_solve_stats stats;
 };
 
@@ -338,7 +351,7 @@ extern "C" {
 int64_t ww_batch_bytes(int64_t max_items, int64_t max_pixels, int64_t max_item_pixels) {
   if (max_items < 1 || max_pixels < 4 || max_item_pixels < 4) return -1;
   int64_t tiles = batch_tiles(max_items, max_pixels);
-  return max_pixels * (1 + 8 + 2) + max_items * 16 + 65536 * 4 + 64 + ((2 * max_item_pixels + 1023) / 1024) * 4 +
+  return max_pixels * (1 + 8 + 2) + max_items * 16 + ww::grid_batch_bytes((int)max_items, max_pixels) +
          ww::solver_bytes(max_pixels, tiles, max_items);
 }
 
@@ -353,16 +366,13 @@ ww_status ww_batch_create(int64_t max_items, int64_t max_pixels, int64_t max_ite
   b->max_pixels = max_pixels;
   b->max_item_pixels = max_item_pixels;
   const int64_t tiles = batch_tiles(max_items, max_pixels);
-  b->steep.blocksum_len = (2 * max_item_pixels + 1023) / 1024;
   bool ok = cudaMalloc(&b->residues, max_pixels) == cudaSuccess &&
             cudaMalloc(&b->ground, max_items * 4) == cudaSuccess &&
             cudaMalloc(&b->costs, 4 * max_pixels * 2) == cudaSuccess &&
             cudaMalloc(&b->flows, 2 * max_pixels) == cudaSuccess &&
             cudaMalloc(&b->total_cost, max_items * 8) == cudaSuccess &&
-            cudaMalloc(&b->status, max_items * 4) == cudaSuccess &&
-            cudaMalloc(&b->steep.hist, 65536 * 4) == cudaSuccess && cudaMalloc(&b->steep.steep_ctr, 64) == cudaSuccess &&
-            cudaMalloc(&b->steep.blocksum, b->steep.blocksum_len * 4) == cudaSuccess;
-  if (ok) ok = cudaMemset(b->steep.hist, 0, 65536 * 4) == cudaSuccess;
+            cudaMalloc(&b->status, max_items * 4) == cudaSuccess;
+  if (ok) ok = ww::grid_batch_alloc(&b->grid, (int)max_items, max_pixels) == WW_OK;
   ww_status st = ok ? ww::solver_alloc(&b->sv, max_pixels, tiles, max_items) : WW_ERR_OOM;
   if (st != WW_OK) {
     cudaGetLastError();
@@ -381,9 +391,7 @@ void ww_batch_free(ww_batch* b) {
   cudaFree(b->flows);
   cudaFree(b->total_cost);
   cudaFree(b->status);
-  cudaFree(b->steep.hist);
-  cudaFree(b->steep.steep_ctr);
-  cudaFree(b->steep.blocksum);
+  ww::grid_batch_free(&b->grid);
   ww::solver_free(&b->sv);
   delete b;
 }
@@ -427,11 +435,18 @@ ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* 
   }
   std::vector<ww::ProbHost> probs(count);
   int64_t off = 0;
+  // phase timing under WW_TRACE: pre-solve kernels, solve, integration
+  cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+  const bool tr = ww::trace_enabled();
+  if (tr)
+    for (auto& e : tev) cudaEventCreate(&e);
+  if (tr) cudaEventRecord(tev[0], s);
+  int64_t filled = 0;
   for (int64_t k = 0; k < count && st == WW_OK; ++k) {
     const ww_batch_item& it = items[k];
-    const int c = it.is_complex ? 1 : 0;
     const int16_t* dt = ww::lut_device_table(luts[k], s, &st);
     if (!dt) break;
+    ++filled;
     ww::ProbHost& ph = probs[k];
     ph.m = it.m;
     ph.n = it.n;
@@ -442,25 +457,48 @@ ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* 
     ph.pot_out = nullptr;
     ph.total_cost = b->total_cost + k;
     ph.status = b->status + k;
-    st = ww::launch_residues(it.ifg, c, it.coh, it.mask, it.m, it.n, const_cast<int8_t*>(ph.res),
-                             const_cast<int32_t*>(ph.ground), s);
-    if (st == WW_OK)
-      st = ww::launch_costs(it.ifg, c, it.coh, it.mask, it.m, it.n, dt, p, &b->steep, const_cast<int16_t*>(ph.costs), s);
+    ww::GridItem& g = b->grid.h_items[k];
+    g = ww::GridItem{};
+    g.ifg = it.ifg;
+    g.coh = it.coh;
+    g.mask = it.mask;
+    g.m = it.m;
+    g.n = it.n;
+    g.is_complex = it.is_complex ? 1 : 0;
+    g.res = const_cast<int8_t*>(ph.res);
+    g.ground = const_cast<int32_t*>(ph.ground);
+    g.costs = const_cast<int16_t*>(ph.costs);
+    g.table = dt;
+    g.flows = ph.flows;
+    g.unw = it.unwrapped;
+    g.cyc = it.cycles;
     off += it.m * it.n;
   }
+  if (st == WW_OK) st = ww::launch_pre_batch(&b->grid, (int)count, p, s);
+  if (tr) cudaEventRecord(tev[1], s);
   if (st == WW_OK) st = ww::solve_problems(probs.data(), (int)count, &b->sv, p, nullptr, &b->stats, s);
-  for (int64_t k = 0; k < count; ++k) {
-    const ww_batch_item& it = items[k];
-    ww_status s2 = ww::launch_integrate(it.ifg, it.is_complex ? 1 : 0, it.coh, it.mask, probs[k].flows, it.m, it.n,
-                                        it.unwrapped, it.cycles, s);
+  if (tr) cudaEventRecord(tev[2], s);
+  if (filled == count) {
+    // integration runs even after a solver failure (the caller's outputs are always written)
+    ww_status s2 = ww::launch_integrate_batch(&b->grid, (int)count, s);
     if (st == WW_OK) st = s2;
   }
   std::vector<int64_t> tc(count);
   std::vector<int32_t> sts(count);
+  if (tr) cudaEventRecord(tev[3], s);
   if (cudaMemcpyAsync(tc.data(), b->total_cost, count * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(sts.data(), b->status, count * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     st = st == WW_OK ? WW_ERR_CUDA : st;
+  if (tr) {
+    float a = 0, b2 = 0, c = 0;
+    cudaEventElapsedTime(&a, tev[0], tev[1]);
+    cudaEventElapsedTime(&b2, tev[1], tev[2]);
+    cudaEventElapsedTime(&c, tev[2], tev[3]);
+    std::fprintf(stderr, "[ww] batch %lld items: residues+costs %.3f ms, solve %.3f ms, integrate %.3f ms\n",
+                 (long long)count, a, b2, c);
+    for (auto& e : tev) cudaEventDestroy(e);
+  }
   for (int64_t k = 0; k < count; ++k) {
     items[k].total_cost = tc[k];
     items[k].status = st == WW_OK ? sts[k] : st;

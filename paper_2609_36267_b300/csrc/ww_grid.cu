@@ -7,6 +7,8 @@
 // tiles so each pixel is read from HBM once per kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "ww_internal.cuh"
@@ -17,13 +19,13 @@ namespace {
 // ---------------- residues ----------------
 constexpr int RTX = 32, RTY = 8;
 
-__global__ void __launch_bounds__(RTX* RTY) k_residues(const void* __restrict__ ifg, int is_complex,
-                                                        const float* __restrict__ coh,
-                                                        const uint8_t* __restrict__ mask, int64_t m,
-                                                        int64_t n, int8_t* __restrict__ res,
-                                                        int32_t* __restrict__ ground) {
+// One RTY x RTX tile of nodes, tile (by, bx).
+__device__ __forceinline__ void residues_tile(const void* __restrict__ ifg, int is_complex,
+                                              const float* __restrict__ coh, const uint8_t* __restrict__ mask,
+                                              int64_t m, int64_t n, int8_t* __restrict__ res,
+                                              int32_t* __restrict__ ground, int64_t bx, int64_t by) {
   __shared__ float sp[RTY + 1][RTX + 1];
-  const int64_t i0 = (int64_t)blockIdx.y * RTY, j0 = (int64_t)blockIdx.x * RTX;
+  const int64_t i0 = by * RTY, j0 = bx * RTX;
   const int tid = threadIdx.y * RTX + threadIdx.x;
   for (int q = tid; q < (RTY + 1) * (RTX + 1); q += RTX * RTY) {
     int r = q / (RTX + 1), c = q % (RTX + 1);
@@ -57,6 +59,14 @@ __global__ void __launch_bounds__(RTX* RTY) k_residues(const void* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(RTX* RTY) k_residues(const void* __restrict__ ifg, int is_complex,
+                                                        const float* __restrict__ coh,
+                                                        const uint8_t* __restrict__ mask, int64_t m,
+                                                        int64_t n, int8_t* __restrict__ res,
+                                                        int32_t* __restrict__ ground) {
+  residues_tile(ifg, is_complex, coh, mask, m, n, res, ground, blockIdx.x, blockIdx.y);
+}
+
 // ---------------- costs ----------------
 constexpr int CTX = 32, CTY = 16, CW = 3;  // tile, max box half-width
 constexpr int CPX = CTX + 2 * CW + 1, CPY = CTY + 2 * CW + 1;  // pixel tile
@@ -78,11 +88,12 @@ __device__ __forceinline__ float edge_d(float a, float b) {
   return __fsub_rn(dp, __fmul_rn(kTwoPiF, (float)wrap_count(dp)));
 }
 
-__global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int is_complex,
-                                               const float* __restrict__ coh,
-                                               const uint8_t* __restrict__ mask, int64_t m, int64_t n,
-                                               const int16_t* __restrict__ table, int w, float steep_rad,
-                                               int16_t* __restrict__ costs, SteepCtr* ctr) {
+// One CTY x CTX tile of pixels (both edges of each pixel), tile (by, bx).
+__device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_complex,
+                                           const float* __restrict__ coh, const uint8_t* __restrict__ mask,
+                                           int64_t m, int64_t n, const int16_t* __restrict__ table, int w,
+                                           float steep_rad, int16_t* __restrict__ costs, SteepCtr* ctr,
+                                           int64_t bx, int64_t by) {
   __shared__ float sp[CPY][CPX];
   __shared__ float sc[CPY][CPX];
   __shared__ uint8_t sv[CPY][CPX];
@@ -90,7 +101,7 @@ __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int
   __shared__ uint8_t eh[CEY][CEX + 1], ev[CEY][CEX + 1];
   __shared__ int32_t rh[CEY][CTX], rv[CEY][CTX];      // row (horizontal) partial sums
   __shared__ uint8_t nh[CEY][CTX], nv[CEY][CTX];      // row partial counts
-  const int64_t i0 = (int64_t)blockIdx.y * CTY, j0 = (int64_t)blockIdx.x * CTX;
+  const int64_t i0 = by * CTY, j0 = bx * CTX;
   const int tid = threadIdx.x;
   // 1. prepared pixels, tile origin (i0 - CW, j0 - CW)
   for (int q = tid; q < CPY * CPX; q += 256) {
@@ -196,6 +207,14 @@ __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int
     if (cnt_valid) atomicAdd(&ctr->valid_edges, (unsigned long long)cnt_valid);
     if (cnt_cand) atomicAdd(&ctr->candidates, (unsigned long long)cnt_cand);
   }
+}
+
+__global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int is_complex,
+                                               const float* __restrict__ coh,
+                                               const uint8_t* __restrict__ mask, int64_t m, int64_t n,
+                                               const int16_t* __restrict__ table, int w, float steep_rad,
+                                               int16_t* __restrict__ costs, SteepCtr* ctr) {
+  costs_tile(ifg, is_complex, coh, mask, m, n, table, w, steep_rad, costs, ctr, blockIdx.x, blockIdx.y);
 }
 
 // ---- steep-edge bound (Sec. II-B): global selection over candidate edges ----
@@ -392,8 +411,9 @@ __global__ void k_steep_zero(const void* ifg, int is_complex, const float* coh, 
 
 // ---------------- integration ----------------
 // Column 0 (single block): K(i+1,0) = K(i,0) + dk_v(i,0) - n_v(i,0).
-__global__ void k_integrate_col0(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
-                                 const int8_t* flows, int64_t m, int64_t n, int32_t* cycles) {
+__device__ __forceinline__ void integrate_col0(const void* ifg, int is_complex, const float* coh,
+                                               const uint8_t* mask, const int8_t* flows, int64_t m, int64_t n,
+                                               int32_t* cycles) {
   __shared__ int32_t carry_s;
   __shared__ int32_t ws[32];
   const int64_t P = m * n;
@@ -429,16 +449,18 @@ __global__ void k_integrate_col0(const void* ifg, int is_complex, const float* c
   }
 }
 
+__global__ void k_integrate_col0(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
+                                 const int8_t* flows, int64_t m, int64_t n, int32_t* cycles) {
+  integrate_col0(ifg, is_complex, coh, mask, flows, m, n, cycles);
+}
+
 // Rows: one block per row; K(i,j+1) = K(i,j) + dk_h(i,j) - n_h(i,j); then
 // phi = (float)((double)psi + (double)K * 2pi), NaN where invalid.
 constexpr int kRowThreads = 256, kRowItems = 8;
 
-__global__ void __launch_bounds__(kRowThreads) k_integrate_rows(const void* ifg, int is_complex,
-                                                                const float* coh, const uint8_t* mask,
-                                                                const int8_t* flows, int64_t m, int64_t n,
-                                                                float* unw, int32_t* cycles) {
-  const int64_t i = blockIdx.x;
-  if (i >= m) return;
+__device__ __forceinline__ void integrate_row(const void* ifg, int is_complex, const float* coh,
+                                              const uint8_t* mask, const int8_t* flows, int64_t m, int64_t n,
+                                              float* unw, int32_t* cycles, int64_t i) {
   __shared__ int32_t ws[kRowThreads / 32];
   __shared__ float first_psi[kRowThreads];
   __shared__ int32_t carry_s;
@@ -516,6 +538,291 @@ __global__ void __launch_bounds__(kRowThreads) k_integrate_rows(const void* ifg,
   }
 }
 
+__global__ void __launch_bounds__(kRowThreads) k_integrate_rows(const void* ifg, int is_complex,
+                                                                const float* coh, const uint8_t* mask,
+                                                                const int8_t* flows, int64_t m, int64_t n,
+                                                                float* unw, int32_t* cycles) {
+  if ((int64_t)blockIdx.x >= m) return;
+  integrate_row(ifg, is_complex, coh, mask, flows, m, n, unw, cycles, blockIdx.x);
+}
+
+// ---------------- batched launches ----------------
+// One launch covers every item of a batch: the items' blocks are numbered
+// consecutively (GridItem::blk[kind]) and each block finds its item by a
+// binary search over those offsets, then runs the same per-tile code as the
+// single-image kernels.
+
+template <int KIND>
+__device__ __forceinline__ int item_of_block(const GridItem* it, int count, int64_t b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (it[mid].blk[KIND] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(RTX* RTY) k_residues_b(const GridItem* __restrict__ items, int count) {
+  const int64_t b = blockIdx.x;
+  const GridItem& it = items[item_of_block<kBlkRes>(items, count, b)];
+  const int64_t local = b - it.blk[kBlkRes];
+  const int64_t gx = (it.n - 1 + RTX - 1) / RTX;
+  residues_tile(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, it.res, it.ground, local % gx, local / gx);
+}
+
+__global__ void __launch_bounds__(256) k_costs_b(const GridItem* __restrict__ items, int count, int w,
+                                                 float steep_rad) {
+  const int64_t b = blockIdx.x;
+  const GridItem& it = items[item_of_block<kBlkCost>(items, count, b)];
+  const int64_t local = b - it.blk[kBlkCost];
+  const int64_t gx = (it.n + CTX - 1) / CTX;
+  costs_tile(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, it.table, w, steep_rad, it.costs,
+             reinterpret_cast<SteepCtr*>(it.steep), local % gx, local / gx);
+}
+
+// Cap test of every item (one thread per item); mode 1 marks the items that
+// need the selection.
+__global__ void k_steep_plan_b(GridItem* items, int count, int32_t cap_ppm) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    SteepCtr* ctr = reinterpret_cast<SteepCtr*>(items[k].steep);
+    unsigned long long cap = (ctr->valid_edges * (unsigned long long)cap_ppm) / 1000000ull;
+    // 0: zero every candidate; 1: select the cap largest; 3: cap 0, zero nothing
+    ctr->mode = ctr->candidates <= cap ? 0ull : (cap == 0 ? 3ull : 1ull);
+    ctr->pad = cap;
+    ctr->above = 0;
+    ctr->hi_bin = 0;
+  }
+}
+
+// ---- batched exact selection for items over their cap ----
+// Radix select of the cap-th largest |d| among an item's steep candidates.
+// Keys are key = bits(|d|) - bits(steep_rad) (fp32 bits are monotone for
+// values >= 0, and every candidate has |d| > steep_rad), so they span only
+// the range up to bits(PI_F) - bits(steep_rad): three digits of at most 11
+// bits each (shifts and widths from the host, SelDigits) cover it.  Each level
+// histograms the candidates whose higher digits equal the prefix found so far
+// (warp-aggregated shared-memory histogram per block, flushed with one atomic
+// per non-empty bin into the item's 2048 global bins); then one block per item
+// walks its bins from the top.
+constexpr int kSelBins = 2048;
+constexpr int kSelChunk = 16384;  // keys per block of the histogram passes
+
+struct SelDigits {
+  uint32_t base;     // bits(steep_rad), 0 when steep_rad <= 0
+  int shift[3], width[3];
+};
+
+__global__ void __launch_bounds__(256) k_sel_hist_b(const GridItem* __restrict__ items, int count, float steep_rad,
+                                                    uint32_t* hist_all, SelDigits dg, int level) {
+  __shared__ uint32_t h[kSelBins];
+  const int64_t b = blockIdx.x;
+  const int k = item_of_block<kBlkSel>(items, count, b);
+  const GridItem& it = items[k];
+  const SteepCtr* ctr = reinterpret_cast<const SteepCtr*>(it.steep);
+  if (ctr->mode != 1) return;
+  for (int q = threadIdx.x; q < kSelBins; q += blockDim.x) h[q] = 0;
+  __syncthreads();
+  const int sh = dg.shift[level];
+  const uint32_t dmask = (1u << dg.width[level]) - 1u;
+  const int psh = level > 0 ? dg.shift[level - 1] : 0;
+  const uint32_t prefix = (uint32_t)ctr->hi_bin;
+  const int64_t E = 2 * it.m * it.n;
+  const int64_t base = (b - it.blk[kBlkSel]) * kSelChunk;
+  const int64_t end = min(E, base + kSelChunk);
+  const unsigned lane = threadIdx.x & 31;
+  for (int64_t k0 = base; k0 < end; k0 += blockDim.x) {  // same trip count for every thread
+    const int64_t key = k0 + threadIdx.x;
+    int bin = -1;
+    uint32_t bits;
+    if (key < end && steep_edge(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, key, steep_rad, &bits)) {
+      const uint32_t kk = bits - dg.base;
+      if (level == 0 || (kk >> psh) == prefix) bin = (int)((kk >> sh) & dmask);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    if (bin >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[bin], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  uint32_t* g = hist_all + (int64_t)k * kSelBins;
+  for (int q = threadIdx.x; q < kSelBins; q += blockDim.x)
+    if (h[q]) atomicAdd(&g[q], h[q]);
+}
+
+// One block (256 threads, 8 bins each) per item: the bin holding the
+// (cap - above)-th largest candidate of this level; bins are cleared after.
+__global__ void __launch_bounds__(256) k_sel_find_b(const GridItem* __restrict__ items, uint32_t* hist_all,
+                                                    SelDigits dg, int level) {
+  const GridItem& it = items[blockIdx.x];
+  SteepCtr* ctr = reinterpret_cast<SteepCtr*>(it.steep);
+  if (ctr->mode != 1) return;
+  __shared__ unsigned long long part[256];
+  uint32_t* g = hist_all + (int64_t)blockIdx.x * kSelBins;
+  const int t = threadIdx.x;
+  // read before the barriers below: one thread rewrites the counters afterwards
+  const unsigned long long need = ctr->pad - ctr->above;  // >= 1 while selecting
+  const uint64_t prefix_in = ctr->hi_bin;
+  const int hi = kSelBins - 1 - 8 * t;  // this thread's bins hi, hi-1, ..., hi-7 (from the top)
+  unsigned long long sum = 0;
+  for (int q = 0; q < 8; ++q) sum += g[hi - q];
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    unsigned long long v = t >= off ? part[t - off] : 0ull;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  const unsigned long long before = t ? part[t - 1] : 0ull;
+  if (before < need && part[t] >= need) {
+    unsigned long long acc = before;
+    for (int q = 0; q < 8; ++q) {
+      const int bin = hi - q;
+      const unsigned long long c = g[bin];
+      if (acc + c >= need) {
+        const uint64_t prefix = level == 0 ? (uint64_t)bin : ((prefix_in << dg.width[level]) | (uint64_t)bin);
+        ctr->hi_bin = prefix;
+        ctr->above = (ctr->pad - need) + acc;
+        if (level == 2) {
+          ctr->threshold = prefix + dg.base;  // exact |d| bits of the cut
+          ctr->take_at_thr = need - acc;      // candidates equal to it to zero, in key order
+        }
+        break;
+      }
+      acc += c;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < 8; ++q) g[hi - q] = 0;
+}
+
+// Ties at the cut: count per 1024-key chunk (blocksum indexed by the global
+// steep block number).
+__global__ void k_sel_ties_b(const GridItem* __restrict__ items, int count, float steep_rad, uint32_t* blocksum) {
+  const int64_t b = blockIdx.x;
+  const GridItem& it = items[item_of_block<kBlkSteep>(items, count, b)];
+  const SteepCtr* ctr = reinterpret_cast<const SteepCtr*>(it.steep);
+  if (ctr->mode != 1) return;
+  const int64_t E = 2 * it.m * it.n;
+  const int64_t base = (b - it.blk[kBlkSteep]) * kSteepChunk;
+  const uint32_t thr = (uint32_t)ctr->threshold;
+  unsigned c = 0;
+  for (int64_t key = base + threadIdx.x; key < min(E, base + kSteepChunk); key += blockDim.x) {
+    uint32_t bits;
+    if (steep_edge(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, key, steep_rad, &bits) && bits == thr) ++c;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ unsigned sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += sm[q];
+    blocksum[b] = tot;
+  }
+}
+
+// Exclusive scan of one item's chunk tie counts (one block per item).
+__global__ void __launch_bounds__(kFindThreads) k_sel_scan_b(const GridItem* __restrict__ items, uint32_t* blocksum) {
+  const GridItem& it = items[blockIdx.x];
+  const SteepCtr* ctr = reinterpret_cast<const SteepCtr*>(it.steep);
+  if (ctr->mode != 1) return;
+  const int64_t nblocks = (2 * it.m * it.n + kSteepChunk - 1) / kSteepChunk;
+  uint32_t* bs = blocksum + it.blk[kBlkSteep];
+  __shared__ uint32_t part[kFindThreads];
+  const int t = threadIdx.x;
+  const int64_t per = (nblocks + kFindThreads - 1) / kFindThreads;
+  const int64_t b0 = t * per, b1 = min(nblocks, b0 + per);
+  uint32_t sum = 0;
+  for (int64_t q = b0; q < b1; ++q) sum += bs[q];
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < kFindThreads; off <<= 1) {
+    uint32_t v = t >= off ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t acc = t ? part[t - 1] : 0u;
+  for (int64_t q = b0; q < b1; ++q) {
+    uint32_t v = bs[q];
+    bs[q] = acc;
+    acc += v;
+  }
+}
+
+// Zero the selected edges: |d| above the cut, and the first take_at_thr ties
+// in key order (rank = ties in earlier chunks + ties earlier in this chunk).
+__global__ void k_sel_zero_b(const GridItem* __restrict__ items, int count, float steep_rad,
+                             const uint32_t* blocksum) {
+  const int64_t b = blockIdx.x;
+  const GridItem& it = items[item_of_block<kBlkSteep>(items, count, b)];
+  const SteepCtr* ctr = reinterpret_cast<const SteepCtr*>(it.steep);
+  if (ctr->mode != 1) return;
+  const int64_t P = it.m * it.n, E = 2 * P;
+  const int64_t base = (b - it.blk[kBlkSteep]) * kSteepChunk;
+  const uint32_t thr = (uint32_t)ctr->threshold;
+  const unsigned long long take = ctr->take_at_thr;
+  __shared__ unsigned warp_ties[32];
+  unsigned running = blocksum[b];
+  for (int64_t off = 0; off < kSteepChunk; off += blockDim.x) {
+    const int64_t key = base + off + threadIdx.x;
+    uint32_t bits = 0;
+    const bool cand = key < E && steep_edge(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, key, steep_rad, &bits);
+    bool zero = cand && bits > thr;
+    const bool tie = cand && bits == thr;
+    const unsigned bal = __ballot_sync(0xffffffffu, tie);
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_ties[wid] = __popc(bal);
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (unsigned q = 0; q < (blockDim.x >> 5); ++q) {
+      if (q < wid) before += warp_ties[q];
+      total += warp_ties[q];
+    }
+    const unsigned rank = running + before + __popc(bal & ((1u << lane) - 1u));
+    if (tie && rank < take) zero = true;
+    running += total;
+    __syncthreads();
+    if (zero) {
+      const int plane = key >= P;
+      const int64_t k = plane ? key - P : key;
+      it.costs[(2 * plane) * P + k] = 0;
+      it.costs[(2 * plane + 1) * P + k] = 0;
+    }
+  }
+}
+
+// Items within their cap: every steep candidate costs 0 in both directions.
+// Items with no candidate, or over the cap (selected separately), are skipped.
+__global__ void k_steep_zero_all_b(const GridItem* __restrict__ items, int count, float steep_rad) {
+  const int64_t b = blockIdx.x;
+  const GridItem& it = items[item_of_block<kBlkSteep>(items, count, b)];
+  const SteepCtr* ctr = reinterpret_cast<const SteepCtr*>(it.steep);
+  if (ctr->mode != 0 || ctr->candidates == 0) return;
+  const int64_t P = it.m * it.n, E = 2 * P;
+  const int64_t base = (b - it.blk[kBlkSteep]) * kSteepChunk;
+  for (int64_t key = base + threadIdx.x; key < min(E, base + kSteepChunk); key += blockDim.x) {
+    uint32_t bits;
+    if (!steep_edge(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, key, steep_rad, &bits)) continue;
+    const int plane = key >= P;
+    const int64_t k = plane ? key - P : key;
+    it.costs[(2 * plane) * P + k] = 0;
+    it.costs[(2 * plane + 1) * P + k] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_integrate_col0_b(const GridItem* __restrict__ items) {
+  const GridItem& it = items[blockIdx.x];
+  integrate_col0(it.ifg, it.is_complex, it.coh, it.mask, it.flows, it.m, it.n, it.cyc);
+}
+
+__global__ void __launch_bounds__(kRowThreads) k_integrate_rows_b(const GridItem* __restrict__ items, int count) {
+  const int64_t b = blockIdx.x;
+  const GridItem& it = items[item_of_block<kBlkRow>(items, count, b)];
+  integrate_row(it.ifg, it.is_complex, it.coh, it.mask, it.flows, it.m, it.n, it.unw, it.cyc,
+                b - it.blk[kBlkRow]);
+}
+
 }  // namespace
 
 ww_status launch_residues(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
@@ -548,6 +855,119 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
   k_steep_scan<<<1, kFindThreads, 0, s>>>(ctr, ws->blocksum, nb);
   k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum,
                                             costs);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}
+
+int64_t grid_batch_bytes(int cap, int64_t max_pixels) {
+  return (int64_t)cap * ((int64_t)sizeof(GridItem) + (int64_t)sizeof(SteepCtr) + kSelBins * 4) +
+         (2 * max_pixels / kSteepChunk + cap + 1) * 4;
+}
+
+ww_status grid_batch_alloc(GridBatch* gb, int cap, int64_t max_pixels) {
+  *gb = GridBatch{};
+  gb->cap = cap;
+  gb->blocksum_len = 2 * max_pixels / kSteepChunk + cap + 1;  // >= sum of ceil(2 m n / chunk)
+  if (cudaMalloc(&gb->d_items, cap * sizeof(GridItem)) != cudaSuccess ||
+      cudaMallocHost(&gb->h_items, cap * sizeof(GridItem)) != cudaSuccess ||
+      cudaMalloc(&gb->d_steep, cap * sizeof(SteepCtr)) != cudaSuccess ||
+      cudaMalloc(&gb->hist, (int64_t)cap * kSelBins * 4) != cudaSuccess ||
+      cudaMalloc(&gb->blocksum, gb->blocksum_len * 4) != cudaSuccess)
+    return WW_ERR_OOM;
+  // the find pass clears the bins it used, so they stay zero between calls
+  if (cudaMemset(gb->hist, 0, (int64_t)cap * kSelBins * 4) != cudaSuccess) return WW_ERR_CUDA;
+  return WW_OK;
+}
+
+void grid_batch_free(GridBatch* gb) {
+  cudaFree(gb->d_items);
+  cudaFreeHost(gb->h_items);
+  cudaFree(gb->d_steep);
+  cudaFree(gb->hist);
+  cudaFree(gb->blocksum);
+  *gb = GridBatch{};
+}
+
+namespace {
+__global__ void k_prep_b(GridItem* items, int count) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    *items[k].ground = 0;
+    *reinterpret_cast<SteepCtr*>(items[k].steep) = SteepCtr{};
+  }
+}
+}  // namespace
+
+namespace {
+uint32_t float_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+}  // namespace
+
+ww_status launch_pre_batch(GridBatch* gb, int count, const ww_params* p, cudaStream_t s) {
+  if (count < 1 || count > gb->cap) return WW_ERR_INVALID_ARG;
+  GridItem* h = gb->h_items;
+  int64_t off[kBlkKinds] = {};
+  for (int k = 0; k < count; ++k) {
+    GridItem& it = h[k];
+    it.steep = reinterpret_cast<SteepCtr*>(gb->d_steep) + k;
+    for (int q = 0; q < kBlkKinds; ++q) it.blk[q] = off[q];
+    const int64_t E = 2 * it.m * it.n;
+    off[kBlkRes] += ((it.n - 1 + RTX - 1) / RTX) * ((it.m - 1 + RTY - 1) / RTY);
+    off[kBlkCost] += ((it.n + CTX - 1) / CTX) * ((it.m + CTY - 1) / CTY);
+    off[kBlkSteep] += (E + kSteepChunk - 1) / kSteepChunk;
+    off[kBlkRow] += it.m;
+    off[kBlkSel] += (E + kSelChunk - 1) / kSelChunk;
+  }
+  for (int64_t o : off)
+    if (o >= (1ll << 31)) return WW_ERR_INVALID_ARG;
+  if (off[kBlkSteep] > gb->blocksum_len) return WW_ERR_INVALID_ARG;
+  WW_CUDA_TRY(cudaMemcpyAsync(gb->d_items, h, count * sizeof(GridItem), cudaMemcpyHostToDevice, s));
+  const int pb = (count + 255) / 256;
+  k_prep_b<<<pb, 256, 0, s>>>(gb->d_items, count);
+  k_residues_b<<<(unsigned)off[kBlkRes], dim3(RTX, RTY), 0, s>>>(gb->d_items, count);
+  k_costs_b<<<(unsigned)off[kBlkCost], 256, 0, s>>>(gb->d_items, count, p->box_half_width, p->steep_rad);
+  k_steep_plan_b<<<pb, 256, 0, s>>>(gb->d_items, count, p->steep_cap_ppm);
+  // items within their cap
+  k_steep_zero_all_b<<<(unsigned)off[kBlkSteep], 256, 0, s>>>(gb->d_items, count, p->steep_rad);
+  // items over their cap: exact selection, all items at once
+  SelDigits dg;
+  dg.base = p->steep_rad > 0.0f ? float_bits(p->steep_rad) : 0u;
+  {
+    const uint32_t span = 0x40490FDBu - std::min(dg.base, 0x40490FDBu);  // largest key: |d| = PI_F
+    int nb = 1;
+    while (nb < 32 && (span >> nb) != 0) ++nb;
+    dg.shift[0] = std::max(0, nb - 11);
+    dg.shift[1] = std::max(0, dg.shift[0] - 11);
+    dg.shift[2] = 0;
+    dg.width[0] = nb - dg.shift[0];
+    dg.width[1] = dg.shift[0] - dg.shift[1];
+    dg.width[2] = dg.shift[1];
+  }
+  for (int level = 0; level < 3; ++level) {
+    k_sel_hist_b<<<(unsigned)off[kBlkSel], 256, 0, s>>>(gb->d_items, count, p->steep_rad, gb->hist, dg, level);
+    k_sel_find_b<<<count, 256, 0, s>>>(gb->d_items, gb->hist, dg, level);
+  }
+  k_sel_ties_b<<<(unsigned)off[kBlkSteep], 256, 0, s>>>(gb->d_items, count, p->steep_rad, gb->blocksum);
+  k_sel_scan_b<<<count, kFindThreads, 0, s>>>(gb->d_items, gb->blocksum);
+  k_sel_zero_b<<<(unsigned)off[kBlkSteep], 256, 0, s>>>(gb->d_items, count, p->steep_rad, gb->blocksum);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}
+
+ww_status launch_integrate_batch(GridBatch* gb, int count, cudaStream_t s) {
+  if (count < 1 || count > gb->cap) return WW_ERR_INVALID_ARG;
+  GridItem* h = gb->h_items;
+  int64_t rows = 0;
+  for (int k = 0; k < count; ++k) {
+    h[k].blk[kBlkRow] = rows;
+    rows += h[k].m;
+  }
+  if (rows >= (1ll << 31)) return WW_ERR_INVALID_ARG;
+  WW_CUDA_TRY(cudaMemcpyAsync(gb->d_items, h, count * sizeof(GridItem), cudaMemcpyHostToDevice, s));
+  k_integrate_col0_b<<<count, 1024, 0, s>>>(gb->d_items);
+  k_integrate_rows_b<<<(unsigned)rows, kRowThreads, 0, s>>>(gb->d_items, count);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
 }

@@ -238,6 +238,45 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
 ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                            const int8_t* flows, int64_t m, int64_t n, float* unw, int32_t* cyc,
                            cudaStream_t s);
+// Batched launches of the grid steps (ww_grid.cu): one launch per step covers
+// every item; blk[] holds each item's first block per launch kind.
+enum { kBlkRes = 0, kBlkCost = 1, kBlkSteep = 2, kBlkRow = 3, kBlkSel = 4, kBlkKinds = 5 };
+struct GridItem {
+  const void* ifg;
+  const float* coh;
+  const uint8_t* mask;
+  int64_t m, n;
+  int32_t is_complex, pad;
+  int64_t blk[kBlkKinds];
+  int8_t* res;
+  int32_t* ground;
+  int16_t* costs;
+  const int16_t* table;
+  void* steep;  // per-item steep-selection counters (set by launch_pre_batch)
+  const int8_t* flows;
+  float* unw;
+  int32_t* cyc;
+};
+struct GridBatch {
+  GridItem* d_items = nullptr;
+  GridItem* h_items = nullptr;  // pinned; filled by the caller (all but blk and steep)
+  void* d_steep = nullptr;      // per-item steep counters
+  uint32_t* hist = nullptr;     // per-item selection histograms (2048 bins)
+  uint32_t* blocksum = nullptr; // per-chunk tie counts of the selection
+  int64_t blocksum_len = 0;
+  int cap = 0;
+};
+int64_t grid_batch_bytes(int cap, int64_t max_pixels);
+ww_status grid_batch_alloc(GridBatch* gb, int cap, int64_t max_pixels);
+void grid_batch_free(GridBatch* gb);
+// residues + costs (with the steep rule, exact selection for the items over
+// their cap) of items [0, count): a fixed number of launches, no host sync
+ww_status launch_pre_batch(GridBatch* gb, int count, const ww_params* p, cudaStream_t s);
+// integration of items [0, count) (fields ifg, coh, mask, m, n, is_complex,
+// flows, unw, cyc of h_items); uploads the item table
+ww_status launch_integrate_batch(GridBatch* gb, int count, cudaStream_t s);
+// The item table is copied from pinned host memory asynchronously: h_items must
+// not be rewritten before the stream has passed the launch that used it.
 // ww_mcf.cu
 struct Batch;
 struct McfCtr;
@@ -246,12 +285,13 @@ struct McfCtr;
 // All problems share the free ground node (potential at pot[g_index]).
 class Session {
  public:
-  Session(SolverWs* sv, int64_t* pot, int64_t g_index, int max_passes, cudaStream_t s);
+  Session(SolverWs* sv, int64_t* pot, int64_t g_index, const ww_params* prm, cudaStream_t s);
   int next_slot() const;                                            // slot the next add() takes, -1 if full
   int add(const ProbHost& ph, int64_t node_off, int64_t tile_off);  // -> slot, or -1 if full
   void remove(int slot);
   ww_status commit();                                               // upload layout, initialise joiners
   ww_status pass(ww_solve_stats* st);                               // one pass, then a host sync
+  ww_status run_graph(ww_solve_stats* st);  // all remaining passes in one graph launch (device-driven loop)
   ww_status left(std::vector<int32_t>* out);                        // imbalanced nodes per slot
   ww_status finalize(const std::vector<int>& slots, std::vector<int32_t>* statuses);
   const McfCtr& ctr() const;
@@ -274,8 +314,13 @@ class Session {
   std::vector<int> order, pending;
   int64_t n_total = 0, t_high = 0, max_nodes = 1, n_border = 0;
   int parity = 0;
+  bool capturing = false;  // enqueue_pass is being captured into a graph body
 };
 
+// argument check of a ww_params (ww_api.cu)
+bool params_valid(const ww_params* p);
+// WW_TRACE=1 in the environment: per-pass and per-phase timings on stderr
+bool trace_enabled();
 ww_status solve_problems(const ProbHost* probs, int nprob, SolverWs* sv, const ww_params* prm, int64_t* pot_global,
                          ww_solve_stats* stats, cudaStream_t s);
 ww_status launch_certificate(const int8_t* res, const int32_t* ground, const int16_t* costs,

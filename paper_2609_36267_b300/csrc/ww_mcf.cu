@@ -93,6 +93,9 @@ struct McfCtr {
   int32_t max_passes;
   int64_t n_total;     // nodes of the active problems
   int64_t n_cap_nodes; // node capacity (the candidate list halves are this far apart)
+  long long aug_total; // augmentations over all passes
+  uint32_t band_min, band_mult, band_growth, band_start_ppm, full_passes;  // search schedule
+  unsigned long long load_cycles, relax_cycles;              // phases of the tile visits
 };
 
 // Problems live in slots (stable ids); `order` lists the active slots sorted by
@@ -289,7 +292,7 @@ constexpr int LROW = TS + 3;  // padded row stride of the label tile (halo 1 eac
 constexpr int RCOL = TS + 1;  // padded row stride of the arc-weight planes
 
 template <bool FWD>
-__global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch b, const int64_t* __restrict__ pot,
+__global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int64_t* __restrict__ pot,
                                                            uint64_t* labels, SearchQ* q, int32_t* slots,
                                                            int32_t* inq, McfCtr* ctr, int32_t* capped_flag) {
   __shared__ uint64_t lab[TSH][LROW];
@@ -365,6 +368,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch b, const int64_
       }
     }
     __syncthreads();
+    const long long t_loaded = clock64();
     uint64_t orig[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) orig[k] = lab[warp + 8 * k + 1][lane + 1];
@@ -446,6 +450,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch b, const int64_
       __syncthreads();
       if (rowdirty == 0) break;
     }
+    const long long t_relaxed = clock64();
     // write back and note which tile sides changed
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -478,6 +483,8 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_search(Batch b, const int64_
       atomicAdd(&ctr->tile_visits, 1ull);
       atomicAdd(&ctr->local_rounds, (unsigned long long)(round + 1));
       atomicAdd(&ctr->visit_cycles, (unsigned long long)(clock64() - t_start));
+      atomicAdd(&ctr->load_cycles, (unsigned long long)(t_loaded - t_start));
+      atomicAdd(&ctr->relax_cycles, (unsigned long long)(t_relaxed - t_loaded));
       __threadfence();
       atomicSub(&q->pending, 1);
     }
@@ -518,7 +525,7 @@ __global__ void k_init_state(Batch b, const int32_t* slots, int32_t* excess, int
 }
 
 // Per-pass setup: distance cap (full search while many imbalanced nodes
-// remain, a band of 4x the last augmented distance once few are left),
+// remain, a band of band_mult x the last augmented distance once few are left),
 // counters and the worklist.
 __global__ void k_pass_setup(McfCtr* ctr, SearchQ* q) {
   if (!ctr->go_on) return;
@@ -528,9 +535,12 @@ __global__ void k_pass_setup(McfCtr* ctr, SearchQ* q) {
   ctr->capped_any = 0;
   ctr->band_again = 1;
   uint32_t cap = 0xFFFFFFFFu;
-  if (ctr->passes >= 2 && (long long)ctr->ncand * 1000ll < ctr->n_total) {
-    unsigned long long c = 4ull * ctr->last_D;
-    cap = (uint32_t)(c < 4096ull ? 4096ull : (c > 0x7FFFFFFFull ? 0x7FFFFFFFull : c));
+  if ((uint32_t)ctr->passes >= ctr->full_passes &&
+      (long long)ctr->ncand * 1000000ll < (long long)ctr->band_start_ppm * ctr->n_total) {
+    const unsigned long long c = (unsigned long long)ctr->band_mult * ctr->last_D;
+    const unsigned long long lo = ctr->band_min;
+    cap = (uint32_t)(c < lo ? lo : (c > 0x7FFFFFFFull ? 0x7FFFFFFFull : c));
+    if (cap == 0) cap = 1;
   }
   ctr->cap = cap;
   q->head = q->tail = q->pending = 0;
@@ -595,14 +605,15 @@ __global__ void k_count_found(const int32_t* excess, const uint64_t* labels, int
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->found, c);
 }
 
-// After a band: widen (x8, or unbounded on the last band) if no candidate was
+// After a band: widen (x band_growth, or unbounded on the last band) if no candidate was
 // reached and some tile dropped candidates at the cap; otherwise the band loop
 // is over.  Runs on one thread.
 __global__ void k_band_decide(McfCtr* ctr, SearchQ* q, int last_band) {
   if (!ctr->band_again) return;
   bool again = ctr->cap != 0xFFFFFFFFu && ctr->found == 0 && ctr->capped_any;
   if (again) {
-    ctr->cap = (last_band || ctr->cap >= 0x0FFFFFFFu) ? 0xFFFFFFFFu : ctr->cap * 8u;
+    const unsigned long long w = (unsigned long long)ctr->cap * ctr->band_growth;
+    ctr->cap = (last_band || w >= 0x7FFFFFFFull) ? 0xFFFFFFFFu : (uint32_t)w;
     q->head = q->tail = q->pending = 0;
     ctr->capped_any = 0;
   }
@@ -772,6 +783,7 @@ __global__ void k_finish_pass(McfCtr* ctr) {
   ctr->ncand_next = 0;
   ctr->cand_sel ^= 1;
   ctr->passes += 1;
+  ctr->aug_total += ctr->naug;
   if (ctr->naug > 0) {
     ctr->last_D = ctr->D;
     ctr->idle = 0;
@@ -835,6 +847,8 @@ int grid_blocks(int64_t work, int threads, int cap) {
   return (int)b;
 }
 
+}  // namespace
+
 bool trace_enabled() {
   static int on = -1;
   if (on < 0) {
@@ -843,8 +857,6 @@ bool trace_enabled() {
   }
   return on == 1;
 }
-
-}  // namespace
 // ---------------- host side ----------------
 
 int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
@@ -913,7 +925,7 @@ void solver_free(SolverWs* sv) {
 
 namespace {
 
-int search_grid_size(int sm_count) {
+int search_grid_size(int sm_count, int want_per_sm) {
   static int per_sm = 0;
   if (per_sm == 0) {
     int a = 1, b = 1;
@@ -921,14 +933,36 @@ int search_grid_size(int sm_count) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<false>, SEARCH_THREADS, 0);
     per_sm = std::max(1, std::min(a, b));
   }
-  return std::min(sm_count * per_sm, kMaxSearchGrid);
+  const int k = want_per_sm > 0 ? std::min(want_per_sm, per_sm) : per_sm;
+  return std::min(sm_count * k, kMaxSearchGrid);
 }
 
 constexpr int kBands = 4;  // cap c, 8c, 64c, then unbounded
 
-__global__ void k_fill_tiles(int32_t* tile_prob, int64_t tile_off, int64_t count, int32_t slot) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
-    tile_prob[tile_off + t] = slot;
+// Joining problems (grid: x strides, y over the joiners): tile -> problem map,
+// zero flows and per-problem counters.
+__global__ void k_join(const ProbDev* probs, const int32_t* slots, int32_t* tile_prob, int32_t* prob_left,
+                       long long* g_net, long long* tc) {
+  const int slot = slots[blockIdx.y];
+  const ProbDev& p = probs[slot];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t0 == 0) {
+    prob_left[slot] = 0;
+    g_net[slot] = 0;
+    tc[slot] = 0;
+  }
+  const int64_t nt = (int64_t)p.tiles_x * p.tiles_y;
+  for (int64_t t = t0; t < nt; t += stride) tile_prob[p.tile_off + t] = slot;
+  // flows, 2 m n bytes: unaligned head, 16-byte words, tail
+  uint8_t* f = reinterpret_cast<uint8_t*>(p.flows);
+  const int64_t nb = 2 * p.m * p.n;
+  const int64_t head = min(nb, (int64_t)((16 - (reinterpret_cast<uintptr_t>(f) & 15)) & 15));
+  const int64_t nw = (nb - head) / 16;
+  for (int64_t k = t0; k < head; k += stride) f[k] = 0;
+  uint4* w = reinterpret_cast<uint4*>(f + head);
+  for (int64_t k = t0; k < nw; k += stride) w[k] = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t k = head + 16 * nw + t0; k < nb; k += stride) f[k] = 0;
 }
 
 // After membership changes: go on if anything is imbalanced.
@@ -940,19 +974,24 @@ __global__ void k_resume(McfCtr* ctr, int64_t n_total) {
 
 }  // namespace
 
-Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, int max_passes, cudaStream_t s)
+Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params* prm, cudaStream_t s)
     : sv(sv_), pot(pot_), g_index(g_index_), stream(s) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
-  search_grid = search_grid_size(sm_count);
+  search_grid = search_grid_size(sm_count, prm->search_ctas_per_sm);
   used.assign(sv->p_cap, 0);
   McfCtr* hc = reinterpret_cast<McfCtr*>(sv->host_ctr);
   std::memset(hc, 0, sizeof(McfCtr));
   hc->status = WW_OK;
   hc->cap = 0xFFFFFFFFu;
-  hc->max_passes = max_passes;
+  hc->max_passes = prm->max_passes;
   hc->n_cap_nodes = sv->n_cap;
+  hc->band_min = (uint32_t)std::max(1, prm->band_min);
+  hc->band_mult = (uint32_t)std::max(0, prm->band_mult);
+  hc->band_growth = (uint32_t)std::max(2, prm->band_growth);
+  hc->band_start_ppm = (uint32_t)std::max(0, prm->band_start_ppm);
+  hc->full_passes = (uint32_t)std::max(0, prm->full_passes);
   err = cudaMemcpyAsync(sv->ctr, hc, sizeof(McfCtr), cudaMemcpyHostToDevice, s) == cudaSuccess &&
                 cudaMemsetAsync(pot + g_index, 0, 8, s) == cudaSuccess
             ? WW_OK
@@ -991,6 +1030,7 @@ int Session::add(const ProbHost& ph, int64_t node_off, int64_t tile_off) {
 
 void Session::remove(int slot) {
   if (slot >= 0 && slot < (int)used.size()) used[slot] = 0;
+  pending.erase(std::remove(pending.begin(), pending.end(), slot), pending.end());
 }
 
 int64_t Session::tiles_of(int slot) const {
@@ -1013,9 +1053,15 @@ ww_status Session::commit() {
     n_total += d.N;
     t_high = std::max(t_high, d.tile_off + (int64_t)d.tiles_x * d.tiles_y);
     max_nodes = std::max(max_nodes, d.N + 1);
-    for (int64_t t = 0; t < (int64_t)d.tiles_x * d.tiles_y; ++t) {
-      int64_t ti = t / d.tiles_x, tj = t % d.tiles_x;
-      if (ti == 0 || tj == 0 || ti == d.tiles_y - 1 || tj == d.tiles_x - 1) border.push_back((int32_t)(d.tile_off + t));
+    // border tiles: first and last tile row, first and last tile of the rows between
+    const int64_t tx = d.tiles_x, ty = d.tiles_y;
+    for (int64_t ti = 0; ti < ty; ++ti) {
+      if (ti == 0 || ti == ty - 1) {
+        for (int64_t tj = 0; tj < tx; ++tj) border.push_back((int32_t)(d.tile_off + ti * tx + tj));
+      } else {
+        border.push_back((int32_t)(d.tile_off + ti * tx));
+        if (tx > 1) border.push_back((int32_t)(d.tile_off + ti * tx + tx - 1));
+      }
     }
   }
   n_border = (int64_t)border.size();
@@ -1027,18 +1073,13 @@ ww_status Session::commit() {
   }
   // the host vectors above are pageable: those copies complete before returning
   if (!pending.empty()) {
+    if (pending.size() > 65535) return WW_ERR_INVALID_ARG;
     int64_t biggest = 1;
-    for (int k : pending) {
-      const ProbDev& d = hp[k];
-      biggest = std::max(biggest, d.N);
-      k_fill_tiles<<<grid_blocks(tiles_of(k), 256, 1024), 256, 0, s>>>(sv->tile_prob, d.tile_off, tiles_of(k), k);
-      WW_CUDA_TRY(cudaMemsetAsync(d.flows, 0, 2 * d.m * d.n, s));
-      WW_CUDA_TRY(cudaMemsetAsync(sv->prob_left + k, 0, 4, s));
-      WW_CUDA_TRY(cudaMemsetAsync(sv->g_net + k, 0, 8, s));
-      WW_CUDA_TRY(cudaMemsetAsync(sv->tc + k, 0, 8, s));
-    }
+    for (int k : pending) biggest = std::max(biggest, hp[k].N);
     WW_CUDA_TRY(cudaMemcpyAsync(sv->slot_list, pending.data(), pending.size() * 4, cudaMemcpyHostToDevice, s));
     dim3 gi(grid_blocks(biggest, 256, std::max(1, sm_count * 16 / (int)pending.size() + 1)), (unsigned)pending.size());
+    k_join<<<gi, 256, 0, s>>>(reinterpret_cast<const ProbDev*>(sv->probs), sv->slot_list, sv->tile_prob,
+                              sv->prob_left, sv->g_net, sv->tc);
     k_init_state<<<gi, 256, 0, s>>>(batch(), sv->slot_list, sv->excess, sv->cand, pot, sv->prob_left,
                                     reinterpret_cast<McfCtr*>(sv->ctr));
     pending.clear();
@@ -1076,7 +1117,7 @@ ww_status Session::enqueue_pass() {
   k_init_labels<FWD><<<gn, 256, 0, s>>>(b, sv->excess, sv->labels, ctr);
   k_seed_tiles<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->cand, ctr, sv->prob_left, sv->border,
                                               (int32_t)n_border, q, sv->slots, sv->inq, search_grid);
-  WW_CUDA_TRY(cudaEventRecord(ev[0], s));
+  if (!capturing) WW_CUDA_TRY(cudaEventRecord(ev[0], s));
   for (int band = 0; band < kBands; ++band) {
     k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped);
     k_count_found<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->labels, sv->cand, 0, ctr);
@@ -1084,7 +1125,7 @@ ww_status Session::enqueue_pass() {
     if (band + 1 < kBands)
       k_reseed<<<grid_tiles, 256, 0, s>>>(b, sv->capped, q, sv->slots, sv->inq, search_grid, ctr);
   }
-  WW_CUDA_TRY(cudaEventRecord(ev[1], s));
+  if (!capturing) WW_CUDA_TRY(cudaEventRecord(ev[1], s));
   k_clear_capped<<<grid_tiles, 256, 0, s>>>(b, sv->capped, ctr);
   k_select<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, ctr);
   k_augment<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, sv->g_net,
@@ -1108,17 +1149,94 @@ ww_status Session::pass(ww_solve_stats* st) {
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && st) st->ms_search_gpu += ms;
   if (st) {
-    st->augmentations += hc->naug;
+    st->augmentations = hc->aug_total;
     st->passes = hc->passes;
     st->search_iterations = hc->passes;
     st->tile_visits = (int64_t)hc->tile_visits;
     st->local_rounds = (int64_t)hc->local_rounds;
     st->visit_cycles = (int64_t)hc->visit_cycles;
+    st->load_cycles = (int64_t)hc->load_cycles;
+    st->relax_cycles = (int64_t)hc->relax_cycles;
   }
   if (trace_enabled())
     std::fprintf(stderr, "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu\n",
                  hc->passes, hc->cap, ms, hc->naug, hc->D, hc->ncand, (unsigned long long)hc->tile_visits);
   return WW_OK;
+}
+
+namespace {
+// Loop condition of the graph-resident pass loop: go on while the solver does.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const McfCtr* ctr) {
+  cudaGraphSetConditional(h, ctr->go_on ? 1u : 0u);
+}
+}  // namespace
+
+// All remaining passes in one graph launch: a conditional while node whose
+// body is a forward and a reverse pass (a pass after the last one is a no-op:
+// its kernels return when go_on is 0) followed by the loop condition.
+ww_status Session::run_graph(ww_solve_stats* st) {
+  if (parity % 2 != 0) return WW_ERR_INTERNAL;
+  cudaGraph_t g = nullptr, body = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphConditionalHandle h;
+  ww_status e = WW_ERR_CUDA;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  cudaStream_t saved = stream;
+  const McfCtr* hc = reinterpret_cast<const McfCtr*>(sv->host_ctr);
+  const int64_t passes0 = hc->passes;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return WW_ERR_CUDA;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) goto done;
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) goto done;
+  body = np.conditional.phGraph_out[0];
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) goto done;
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    goto done;
+  stream = cs;
+  capturing = true;
+  {
+    ww_status e1 = enqueue_pass<true>();
+    ww_status e2 = e1 == WW_OK ? enqueue_pass<false>() : e1;
+    k_loop_cond<<<1, 1, 0, cs>>>(h, reinterpret_cast<const McfCtr*>(sv->ctr));
+    capturing = false;
+    stream = saved;
+    cudaGraph_t captured = nullptr;
+    const bool cap_ok = cudaStreamEndCapture(cs, &captured) == cudaSuccess;
+    if (e2 != WW_OK || !cap_ok) {
+      e = e2 != WW_OK ? e2 : WW_ERR_CUDA;
+      goto done;
+    }
+  }
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) goto done;
+  if (cudaGraphLaunch(ex, stream) != cudaSuccess) goto done;
+  if (cudaMemcpyAsync(sv->host_ctr, sv->ctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    goto done;
+  parity += 2 * (int)((hc->passes - passes0 + 1) / 2);
+  if (st) {
+    st->augmentations = hc->aug_total;
+    st->passes = hc->passes;
+    st->search_iterations = hc->passes;
+    st->tile_visits = (int64_t)hc->tile_visits;
+    st->local_rounds = (int64_t)hc->local_rounds;
+    st->visit_cycles = (int64_t)hc->visit_cycles;
+    st->load_cycles = (int64_t)hc->load_cycles;
+    st->relax_cycles = (int64_t)hc->relax_cycles;
+  }
+  e = WW_OK;
+done:
+  capturing = false;
+  stream = saved;
+  if (ex) cudaGraphExecDestroy(ex);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != WW_OK) cudaGetLastError();
+  return e;
 }
 
 const McfCtr& Session::ctr() const { return *reinterpret_cast<const McfCtr*>(sv->host_ctr); }
@@ -1173,8 +1291,9 @@ ww_status solve_problems(const ProbHost* ph, int nprob, SolverWs* sv, const ww_p
   if (n_total > sv->n_cap || t_total > sv->t_cap || n_total >= (1ll << 31)) return WW_ERR_INVALID_ARG;
   // a single problem may keep its potentials in the caller's array (ground last)
   int64_t* pot = pot_global ? pot_global : sv->pot;
+  const auto t_setup = std::chrono::steady_clock::now();
   const int64_t g_index = pot_global ? (ph[0].m - 1) * (ph[0].n - 1) : sv->n_cap;
-  Session S(sv, pot, g_index, prm->max_passes, s);
+  Session S(sv, pot, g_index, prm, s);
   if (S.err != WW_OK) return S.err;
   int64_t node_off = 0, tile_off = 0;
   std::vector<int> all;
@@ -1192,6 +1311,13 @@ ww_status solve_problems(const ProbHost* ph, int nprob, SolverWs* sv, const ww_p
   WW_CUDA_TRY(cudaStreamSynchronize(s));
   st.residues = S.ncand();
   auto t0 = std::chrono::steady_clock::now();
+  if (trace_enabled())
+    std::fprintf(stderr, "[ww] session setup %.3f ms for %d problems, %lld nodes\n",
+                 std::chrono::duration<double, std::milli>(t0 - t_setup).count(), nprob, (long long)n_total);
+  if (prm->graph_loop && !trace_enabled() && S.go_on()) {
+    e = S.run_graph(&st);
+    if (e != WW_OK) return e;
+  }
   while (S.go_on()) {
     e = S.pass(&st);
     if (e != WW_OK) return e;

@@ -90,7 +90,7 @@ struct ww_server {
   int32_t* ground = nullptr;
   int64_t* total_cost = nullptr;
   int32_t* status = nullptr;
-  ww_workspace steep;  // steep-selection scratch, reused request after request
+  ww::GridBatch grid;  // item tables of the batched grid launches (admission, retirement)
   Ring pix, node, tile;
   ww::Session* session = nullptr;
   std::thread worker;
@@ -164,33 +164,55 @@ void worker_loop(ww_server* S) {
       }
     }
     auto t_busy = Clock::now();
+    // residues and costs of every admitted request in one set of launches
+    int nq = 0;
+    std::vector<Request*> joined;
     for (Request* r : admitted) {
       const ww_batch_item& it = r->item;
       ww_status st = ww_build_lut(it.nlooks, &r->lut);
       const int16_t* dt = st == WW_OK ? ww::lut_device_table(r->lut, s, &st) : nullptr;
-      const int c = it.is_complex ? 1 : 0;
-      int8_t* res = S->residues + r->pix_off;
-      int16_t* cst = S->costs + 4 * r->pix_off;
-      int8_t* fl = S->flows + 2 * r->pix_off;
       const int slot0 = S->session->next_slot();
       if (!dt || slot0 < 0) {
         release_ranges(S, r);
         fail_request(S, r, st != WW_OK ? st : WW_ERR_INTERNAL);
         continue;
       }
+      int8_t* res = S->residues + r->pix_off;
+      int16_t* cst = S->costs + 4 * r->pix_off;
+      int8_t* fl = S->flows + 2 * r->pix_off;
       // per-slot ground charge, total cost and status words
       ww::ProbHost ph{it.m, it.n, res, S->ground + slot0, cst, fl, nullptr, S->total_cost + slot0, S->status + slot0};
-      st = ww::launch_residues(it.ifg, c, it.coh, it.mask, it.m, it.n, res, S->ground + slot0, s);
-      if (st == WW_OK) st = ww::launch_costs(it.ifg, c, it.coh, it.mask, it.m, it.n, dt, &S->prm, &S->steep, cst, s);
-      const int slot = st == WW_OK ? S->session->add(ph, r->node_off, r->tile_off) : -1;
+      const int slot = S->session->add(ph, r->node_off, r->tile_off);
       if (slot != slot0) {
         if (slot >= 0) S->session->remove(slot);
         release_ranges(S, r);
-        fail_request(S, r, st != WW_OK ? st : WW_ERR_INTERNAL);
+        fail_request(S, r, WW_ERR_INTERNAL);
         continue;
       }
+      ww::GridItem& g = S->grid.h_items[nq++];
+      g = ww::GridItem{};
+      g.ifg = it.ifg;
+      g.coh = it.coh;
+      g.mask = it.mask;
+      g.m = it.m;
+      g.n = it.n;
+      g.is_complex = it.is_complex ? 1 : 0;
+      g.res = res;
+      g.ground = S->ground + slot;
+      g.costs = cst;
+      g.table = dt;
       r->slot = slot;
-      S->by_slot[slot] = r;
+      joined.push_back(r);
+    }
+    ww_status pre = nq > 0 ? ww::launch_pre_batch(&S->grid, nq, &S->prm, s) : WW_OK;
+    for (Request* r : joined) {
+      if (pre != WW_OK) {
+        S->session->remove(r->slot);
+        release_ranges(S, r);
+        fail_request(S, r, pre);
+        continue;
+      }
+      S->by_slot[r->slot] = r;
       ++active;
       std::lock_guard<std::mutex> g(S->mu);
       S->stats.admitted++;
@@ -217,14 +239,29 @@ void worker_loop(ww_server* S) {
     if (!fin.empty()) {
       std::vector<int32_t> sts;
       ww_status fs = S->session->finalize(fin, &sts);
+      // integration of every finished request in one set of launches
       for (size_t q = 0; q < fin.size(); ++q) {
         Request* r = S->by_slot[fin[q]];
         const ww_batch_item& it = r->item;
-        ww_status is = ww::launch_integrate(it.ifg, it.is_complex ? 1 : 0, it.coh, it.mask,
-                                            S->flows + 2 * r->pix_off, it.m, it.n, it.unwrapped, it.cycles, s);
-        int64_t tc = 0;
-        cudaMemcpyAsync(&tc, S->total_cost + fin[q], 8, cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
+        ww::GridItem& g = S->grid.h_items[q];
+        g = ww::GridItem{};
+        g.ifg = it.ifg;
+        g.coh = it.coh;
+        g.mask = it.mask;
+        g.m = it.m;
+        g.n = it.n;
+        g.is_complex = it.is_complex ? 1 : 0;
+        g.flows = S->flows + 2 * r->pix_off;
+        g.unw = it.unwrapped;
+        g.cyc = it.cycles;
+      }
+      ww_status is = ww::launch_integrate_batch(&S->grid, (int)fin.size(), s);
+      std::vector<int64_t> tcs(max_slots, 0);
+      if (cudaMemcpyAsync(tcs.data(), S->total_cost, 8 * (size_t)max_slots, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        is = is == WW_OK ? WW_ERR_CUDA : is;
+      for (size_t q = 0; q < fin.size(); ++q) {
+        Request* r = S->by_slot[fin[q]];
         ww_status rs = st != WW_OK ? st : (fs != WW_OK ? fs : (is != WW_OK ? is : sts[q]));
         S->session->remove(fin[q]);
         S->by_slot[fin[q]] = nullptr;
@@ -234,7 +271,7 @@ void worker_loop(ww_server* S) {
         r->lut = nullptr;
         std::lock_guard<std::mutex> g(S->mu);
         r->item.status = rs;
-        r->item.total_cost = tc;
+        r->item.total_cost = tcs[fin[q]];
         r->done = true;
         r->t_done = Clock::now();
         S->stats.completed++;
@@ -243,7 +280,7 @@ void worker_loop(ww_server* S) {
       if (st != WW_OK) {
         // a failed solve ends this session; start a clean one for later requests
         delete S->session;
-        S->session = new ww::Session(&S->sv, S->sv.pot, S->sv.n_cap, 1 << 30, s);
+        S->session = new ww::Session(&S->sv, S->sv.pot, S->sv.n_cap, &S->prm, s);
       }
     }
     std::lock_guard<std::mutex> g(S->mu);
@@ -256,7 +293,8 @@ void worker_loop(ww_server* S) {
 extern "C" {
 
 ww_status ww_server_create(const ww_server_config* cfg, const ww_params* params, ww_server** out) {
-  if (!cfg || !out || cfg->hbm_budget_bytes < (1 << 20) || cfg->max_request_pixels < 4 || cfg->max_active < 1)
+  if (!cfg || !out || cfg->hbm_budget_bytes < (1 << 20) || cfg->max_request_pixels < 4 || cfg->max_active < 1 ||
+      (params && !ww::params_valid(params)))
     return WW_ERR_INVALID_ARG;
   ww_server* S = new (std::nothrow) ww_server;
   if (!S) return WW_ERR_OOM;
@@ -272,17 +310,13 @@ ww_status ww_server_create(const ww_server_config* cfg, const ww_params* params,
   S->pix.cap = pixels;
   S->node.cap = pixels;
   S->tile.cap = tiles;
-  std::memset(&S->steep, 0, sizeof(S->steep));
-  S->steep.blocksum_len = (2 * cfg->max_request_pixels + 1023) / 1024;
   bool ok = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaMalloc(&S->residues, pixels) == cudaSuccess && cudaMalloc(&S->costs, 8 * pixels) == cudaSuccess &&
             cudaMalloc(&S->flows, 2 * pixels) == cudaSuccess &&
             cudaMalloc(&S->ground, 4 * (int64_t)cfg->max_active) == cudaSuccess &&
             cudaMalloc(&S->total_cost, 8 * (int64_t)cfg->max_active) == cudaSuccess &&
             cudaMalloc(&S->status, 4 * (int64_t)cfg->max_active) == cudaSuccess &&
-            cudaMalloc(&S->steep.hist, 65536 * 4) == cudaSuccess && cudaMalloc(&S->steep.steep_ctr, 64) == cudaSuccess &&
-            cudaMalloc(&S->steep.blocksum, S->steep.blocksum_len * 4) == cudaSuccess &&
-            cudaMemset(S->steep.hist, 0, 65536 * 4) == cudaSuccess;
+            ww::grid_batch_alloc(&S->grid, (int)cfg->max_active, pixels) == WW_OK;
   ww_status st = ok ? ww::solver_alloc(&S->sv, pixels, tiles, cfg->max_active) : WW_ERR_OOM;
   if (st != WW_OK) {
     cudaGetLastError();
@@ -290,7 +324,7 @@ ww_status ww_server_create(const ww_server_config* cfg, const ww_params* params,
     ww_server_destroy(S);
     return st;
   }
-  S->session = new ww::Session(&S->sv, S->sv.pot, S->sv.n_cap, 1 << 30, S->stream);
+  S->session = new ww::Session(&S->sv, S->sv.pot, S->sv.n_cap, &S->prm, S->stream);
   S->worker = std::thread(worker_loop, S);
   *out = S;
   return WW_OK;
@@ -382,9 +416,7 @@ void ww_server_destroy(ww_server* S) {
   cudaFree(S->ground);
   cudaFree(S->total_cost);
   cudaFree(S->status);
-  cudaFree(S->steep.hist);
-  cudaFree(S->steep.steep_ctr);
-  cudaFree(S->steep.blocksum);
+  ww::grid_batch_free(&S->grid);
   if (S->sv.n_cap) ww::solver_free(&S->sv);
   if (S->stream) cudaStreamDestroy(S->stream);
   delete S;

@@ -1,0 +1,98 @@
+// Autotuner of the solver's search schedule for the batched form.  The knobs
+// change only the order and extent of the shortest-path searches, never the
+// optimum, so every trial is checked against the first one item by item.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "ww_internal.cuh"
+
+namespace {
+
+// Device time (ms, best of `repeats`) of one batched unwrap; costs out.
+ww_status time_batch(ww_batch_item* items, int64_t count, const ww_params* p, ww_batch* b, int repeats,
+                     cudaStream_t s, float* best_ms, std::vector<int64_t>* costs) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return WW_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return WW_ERR_CUDA;
+  }
+  ww_status st = WW_OK;
+  float best = -1.0f;
+  for (int r = 0; r < repeats && st == WW_OK; ++r) {
+    cudaEventRecord(e0, s);
+    st = ww_unwrap_batch(items, count, p, b, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = st == WW_OK ? WW_ERR_CUDA : st;
+    float ms = 0.0f;
+    if (st == WW_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best < 0.0f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != WW_OK) return st;
+  costs->resize(count);
+  for (int64_t k = 0; k < count; ++k) (*costs)[k] = items[k].total_cost;
+  *best_ms = best;
+  return WW_OK;
+}
+
+}  // namespace
+
+extern "C" ww_status ww_autotune_batch(ww_batch_item* items, int64_t count, const ww_params* start, ww_batch* b,
+                                       int32_t repeats, ww_params* best, ww_tune_report* report, ww_stream stream) {
+  if (!items || count < 1 || !b || !best || repeats < 1 || repeats > 100) return WW_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  ww_params cur;
+  ww_params_default(&cur);
+  if (start) cur = *start;
+  std::vector<int64_t> ref, got;
+  float cur_ms = 0.0f;
+  int trials = 1;
+  // a first untimed run warms the table cache and the code paths
+  ww_status st = ww_unwrap_batch(items, count, &cur, b, s);
+  if (st != WW_OK) return st;
+  st = time_batch(items, count, &cur, b, repeats, s, &cur_ms, &ref);
+  if (st != WW_OK) return st;
+  const float default_ms = cur_ms;
+  struct Knob {
+    int32_t ww_params::*field;
+    std::vector<int32_t> values;
+  };
+  const std::vector<Knob> knobs = {
+      {&ww_params::full_passes, {0, 1, 2}},
+      {&ww_params::band_start_ppm, {1000000, 10000, 1000}},
+      {&ww_params::band_min, {1024, 256, 4096, 16384}},
+      {&ww_params::band_mult, {4, 2, 8}},
+      {&ww_params::band_growth, {8, 4, 16}},
+      {&ww_params::search_ctas_per_sm, {0, 4, 2}},
+      {&ww_params::graph_loop, {1, 0}},
+  };
+  for (const Knob& k : knobs) {
+    const int32_t keep = cur.*(k.field);
+    int32_t best_v = keep;
+    for (int32_t v : k.values) {
+      if (v == keep) continue;
+      ww_params t = cur;
+      t.*(k.field) = v;
+      float ms = 0.0f;
+      st = time_batch(items, count, &t, b, repeats, s, &ms, &got);
+      ++trials;
+      if (st != WW_OK) return st;
+      if (got != ref) return WW_ERR_INTERNAL;
+      if (ms < cur_ms) {
+        cur_ms = ms;
+        best_v = v;
+      }
+    }
+    cur.*(k.field) = best_v;
+  }
+  *best = cur;
+  if (report) {
+    *report = ww_tune_report{};
+    report->trials = trials;
+    report->default_ms = default_ms;
+    report->best_ms = cur_ms;
+  }
+  return WW_OK;
+}

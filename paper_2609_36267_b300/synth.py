@@ -295,3 +295,30 @@ def batch_item(index: int, base_seed: int = 4000, min_px: int = 256 * 256, max_p
     else:
         mask = np.ones((rows, cols), np.uint8)
     return _finish(rng, truth, gamma, nlooks, mask, False, {"name": f"batch item {index}", "seed": base_seed + index})
+
+
+def cached(name: str, **kwargs) -> Interferogram:
+    """generator `name` (config1/config2/config3/...) with kwargs, memoised as an
+    .npz under $WW_SYNTH_CACHE when that variable names a directory (the big
+    scenes take minutes of single-threaded numpy to generate)."""
+    import hashlib
+    import os
+
+    fn = globals()[name]
+    d = os.environ.get("WW_SYNTH_CACHE")
+    if not d:
+        return fn(**kwargs)
+    key = hashlib.sha1(repr((name, sorted(kwargs.items()))).encode()).hexdigest()[:16]
+    path = os.path.join(d, f"{name}_{key}.npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        ifg = z["ifg"] if z["ifg"].size else None
+        return Interferogram(phase=z["phase"], coh=z["coh"], mask=z["mask"], nlooks=float(z["nlooks"]),
+                             truth=z["truth"], ifg=ifg, meta={"name": str(z["name"])})
+    x = fn(**kwargs)
+    os.makedirs(d, exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, phase=x.phase, coh=x.coh, mask=x.mask, nlooks=np.float64(x.nlooks), truth=x.truth,
+             ifg=x.ifg if x.ifg is not None else np.zeros(0, np.complex64), name=str(x.meta.get("name", name)))
+    os.replace(tmp, path)
+    return x

@@ -102,3 +102,45 @@ def numpy_certificate(res, g, costs, flows, pot):
     if gnet != g:
         return False, total, "ground conservation"
     return True, total, "ok"
+
+
+def band_certificate(res, costs, flows, pot, a, b):
+    """numpy_certificate restricted to pixel rows [a, b): capacity, the reduced
+    cost of every residual arc of the h edges of rows a..b-1 and the v edges of
+    rows a..min(b, m-1)-1, conservation at the nodes of rows a..min(b, m-1)-1.
+    res is the (m-1) x (n-1) residue plane.  Returns the number of violations."""
+    _, m, n = costs.shape
+    R, C = m - 1, n - 1
+    G = R * C
+    pot = np.asarray(pot)
+
+    def node(i, j):  # node index array for row i (scalar) and column array j; G outside
+        i = np.full_like(j, i)
+        inside = (i >= 0) & (i < R) & (j >= 0) & (j < C)
+        return np.where(inside, i * C + j, G)
+
+    bad = 0
+    jh = np.arange(n - 1)
+    jv = np.arange(n)
+    for i in range(a, b):
+        dk = flows[0, i, : n - 1].astype(np.int64)
+        bad += np.count_nonzero(np.abs(dk) > 1)
+        cp, cm = costs[0, i, : n - 1].astype(np.int64), costs[1, i, : n - 1].astype(np.int64)
+        pa, pb = pot[node(i - 1, jh)], pot[node(i, jh)]
+        bad += np.count_nonzero((dk != 1) & (cp - pa + pb < 0))
+        bad += np.count_nonzero((dk == 1) & (-cp - pb + pa < 0))
+        bad += np.count_nonzero((dk != -1) & (cm - pb + pa < 0))
+        bad += np.count_nonzero((dk == -1) & (-cm - pa + pb < 0))
+        if i < m - 1:
+            dk = flows[1, i, :].astype(np.int64)
+            bad += np.count_nonzero(np.abs(dk) > 1)
+            cp, cm = costs[2, i, :].astype(np.int64), costs[3, i, :].astype(np.int64)
+            pa, pb = pot[node(i, jv)], pot[node(i, jv - 1)]
+            bad += np.count_nonzero((dk != 1) & (cp - pa + pb < 0))
+            bad += np.count_nonzero((dk == 1) & (-cp - pb + pa < 0))
+            bad += np.count_nonzero((dk != -1) & (cm - pb + pa < 0))
+            bad += np.count_nonzero((dk == -1) & (-cm - pa + pb < 0))
+            net = (flows[0, i + 1, : n - 1].astype(np.int64) - flows[0, i, : n - 1]
+                   + flows[1, i, : n - 1].astype(np.int64) - flows[1, i, 1:])
+            bad += np.count_nonzero(net != res[i])
+    return bad

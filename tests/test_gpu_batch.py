@@ -80,3 +80,59 @@ def test_batch_small_all_ok():
     xs = items(3, seed=5)
     res = ww.unwrap_batch([dev_request(x) for x in xs], check=False)
     assert all(r[3] == ww.WW_OK for r in res)
+
+
+def noise_item(seed, m, n, nlooks=9.0):
+    """Pure noise: far more steep edges than the 3% cap, so the exact selection runs."""
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(-np.pi, np.pi, (m, n)).astype(np.float32)
+    coh = rng.uniform(0.0, 1.0, (m, n)).astype(np.float32)
+    mask = (rng.uniform(size=(m, n)) > 0.05).astype(np.uint8)
+    return synth.Interferogram(phase=ph, coh=coh, mask=mask, nlooks=nlooks, truth=np.zeros((m, n)))
+
+
+def test_batch_mixes_items_over_and_under_the_steep_cap():
+    """Items over their steep cap take the exact selection, the others zero every
+    steep edge; in one batch each must still reach the oracle's optimum."""
+    xs = [noise_item(11, 40, 57), items(1, seed=7)[0], noise_item(12, 33, 29, nlooks=4.0), items(1, seed=8)[0],
+          noise_item(13, 64, 48, nlooks=16.0)]
+    res = ww.unwrap_batch([dev_request(x) for x in xs])
+    for x, (unw, K, tc, st) in zip(xs, res):
+        assert st == ww.WW_OK
+        ref = oracle_pipeline(x, golden_table(x.nlooks))
+        st_o, _, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+        assert st_o == 0 and tc == tc_o
+
+
+def test_graph_loop_equals_host_loop():
+    """The device-driven pass loop (one graph launch, conditional while node) runs
+    the same passes as the host-driven loop: identical cycle maps and costs."""
+    xs = items(5, seed=21)
+    host = ww.default_params()
+    host.graph_loop = 0
+    graph = ww.default_params()
+    assert graph.graph_loop == 1
+    ws = ww.Workspace(300, 300)
+    for x in xs:
+        req = dev_request(x)
+        _, K0, tc0 = ww.unwrap(*req, ws=ws, params=host)
+        _, K1, tc1 = ww.unwrap(*req, ws=ws, params=graph)
+        assert tc0 == tc1
+        assert np.array_equal(K0.cpu().numpy(), K1.cpu().numpy())
+    r0 = ww.unwrap_batch([dev_request(x) for x in xs], params=host)
+    r1 = ww.unwrap_batch([dev_request(x) for x in xs], params=graph)
+    for a, b in zip(r0, r1):
+        assert a[2] == b[2] and a[3] == b[3] == ww.WW_OK
+        assert np.array_equal(a[1].cpu().numpy(), b[1].cpu().numpy())
+
+
+def test_autotune_keeps_the_optimum():
+    xs = items(6, seed=31)
+    reqs = [dev_request(x) for x in xs]
+    best, rep = ww.autotune_batch(reqs, repeats=1)
+    assert rep["trials"] >= 2
+    assert rep["best_ms"] <= rep["default_ms"]
+    base = ww.unwrap_batch(reqs)
+    tuned = ww.unwrap_batch(reqs, params=best)
+    assert [r[2] for r in base] == [r[2] for r in tuned]
+    assert all(r[3] == ww.WW_OK for r in tuned)
