@@ -187,8 +187,8 @@ int64_t ww_workspace_bytes(int64_t m, int64_t n) {
   if (!grid_ok(m, n)) return -1;
   int64_t P = m * n, N = (m - 1) * (n - 1);
   int64_t grid = N /*residues*/ + 4 * P * 2 /*costs*/ + 2 * P /*flows*/ + (N + 1) * 8 /*potentials*/ + 64;
-  int64_t steep = 65536 * 4 + 64 + ((2 * P + 1023) / 1024) * 4;
-  return grid + steep + ww::solver_bytes(N, ww::tiles_for(m, n), 1);
+  int64_t steep = 65536 * 4 + 64 + ((2 * P + 1023) / 1024) * 4 + ww::steep_list_capacity(P, 30000) * 4;
+  return grid + steep + 4 * P /*phase*/ + ww::solver_bytes(N, ww::tiles_for(m, n), 1);
 }
 
 ww_status ww_workspace_create(int64_t max_rows, int64_t max_cols, ww_workspace** out) {
@@ -201,12 +201,15 @@ ww_status ww_workspace_create(int64_t max_rows, int64_t max_cols, ww_workspace**
   ws->max_cols = max_cols;
   const int64_t m = max_rows, n = max_cols, P = m * n, N = (m - 1) * (n - 1);
   ws->blocksum_len = (2 * P + 1023) / 1024;
+  ws->steep_list_cap = ww::steep_list_capacity(P, 30000);  // the default 3% cap
   bool ok = cudaMalloc(&ws->residues, N) == cudaSuccess && cudaMalloc(&ws->ground, 64) == cudaSuccess &&
             cudaMalloc(&ws->costs, 4 * P * 2) == cudaSuccess && cudaMalloc(&ws->flows, 2 * P) == cudaSuccess &&
             cudaMalloc(&ws->potentials, (N + 1) * 8) == cudaSuccess &&
             cudaMalloc(&ws->total_cost, 64) == cudaSuccess && cudaMalloc(&ws->dev_status, 64) == cudaSuccess &&
             cudaMalloc(&ws->hist, 65536 * 4) == cudaSuccess && cudaMalloc(&ws->steep_ctr, 64) == cudaSuccess &&
-            cudaMalloc(&ws->blocksum, ws->blocksum_len * 4) == cudaSuccess;
+            cudaMalloc(&ws->blocksum, ws->blocksum_len * 4) == cudaSuccess &&
+            cudaMalloc(&ws->steep_list, ws->steep_list_cap * 4) == cudaSuccess &&
+            cudaMalloc(&ws->psi, P * 4) == cudaSuccess;
   if (ok) ok = cudaMemset(ws->hist, 0, 65536 * 4) == cudaSuccess;
   ww_status st = ok ? ww::solver_alloc(&ws->sv, N, ww::tiles_for(m, n), 1) : WW_ERR_OOM;
   if (st != WW_OK) {
@@ -230,6 +233,8 @@ void ww_workspace_free(ww_workspace* ws) {
   cudaFree(ws->hist);
   cudaFree(ws->steep_ctr);
   cudaFree(ws->blocksum);
+  cudaFree(ws->steep_list);
+  cudaFree(ws->psi);
   ww::solver_free(&ws->sv);
   delete ws;
 }
@@ -301,14 +306,21 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
     ww_lut_free(lut);
     return st;
   }
-  const int c = is_complex ? 1 : 0;
-  st = ww::launch_residues(ifg, c, coh, mask, m, n, ws->residues, ws->ground, s);
-  if (st == WW_OK) st = ww::launch_costs(ifg, c, coh, mask, m, n, dt, p, ws, ws->costs, s);
+  int c = is_complex ? 1 : 0;
+  const void* src = ifg;
+  if (c) {
+    // the phase of a complex input once, then every step reads it as a float image
+    st = ww::launch_phase(ifg, m, n, ws->psi, s);
+    src = ws->psi;
+    c = 0;
+  }
+  if (st == WW_OK) st = ww::launch_residues(src, c, coh, mask, m, n, ws->residues, ws->ground, s);
+  if (st == WW_OK) st = ww::launch_costs(src, c, coh, mask, m, n, dt, p, ws, ws->costs, s);
   if (st == WW_OK) {
     ww::ProbHost ph{m, n, ws->residues, ws->ground, ws->costs, ws->flows, nullptr, ws->total_cost, ws->dev_status};
     st = ww::solve_problems(&ph, 1, &ws->sv, p, ws->potentials, &ws->stats, s);
   }
-  ww_status st2 = ww::launch_integrate(ifg, c, coh, mask, ws->flows, m, n, unwrapped, cycles, s);
+  ww_status st2 = ww::launch_integrate(src, c, coh, mask, ws->flows, m, n, unwrapped, cycles, s);
   if (st == WW_OK) st = st2;
   if (total_cost && cudaMemcpyAsync(total_cost, ws->total_cost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     st = WW_ERR_CUDA;
@@ -339,8 +351,99 @@ struct ww_batch {
   int32_t* status;      // [max_items]
   // item table of the batched grid launches
   ww::GridBatch grid;
+  float* psi;  // phase of the complex items [max_pixels]
+  // pinned copies of the per-item results (filled by the whole-batch graph)
+  int64_t* h_total_cost;
+  int32_t* h_status;
   ww_solve_stats stats;
 };
+
+namespace {
+
+// The whole batch as ONE CUDA graph launch:
+//   A (child graph): item table upload, residues, costs and steep rule of every
+//     item, solver join (layout upload, per-problem initialisation);
+//   B (conditional while node): forward + reverse passes until the device
+//     finds nothing left to balance;
+//   C (child graph): per-item totals and statuses, integration of every item,
+//     copies of the results and solver counters into pinned host memory.
+// Host-built tables sit in pinned staging that the host leaves untouched until
+// the launch completes.  A and C both upload the grid item table; it is built
+// once, before capture, so both copies carry the same content.
+ww_status batch_graph(ww_batch* b, int64_t count, const ww_params* p, const std::vector<ww::ProbHost>& probs,
+                      cudaStream_t s) {
+  ww::Session S(&b->sv, b->sv.pot, b->sv.n_cap, p, s);
+  if (S.err != WW_OK) return S.err;
+  std::vector<int> all;
+  int64_t node_off = 0, tile_off = 0;
+  for (int64_t k = 0; k < count; ++k) {
+    const int slot = S.add(probs[k], node_off, tile_off);
+    if (slot != (int)k) return WW_ERR_INTERNAL;
+    all.push_back(slot);
+    node_off += (probs[k].m - 1) * (probs[k].n - 1);
+    tile_off += ww::tiles_for(probs[k].m, probs[k].n);
+  }
+  S.set_ncand_unknown(true);
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr, ga = nullptr, gc = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaGraphNode_t na, nb, nc;
+  ww_status e = WW_ERR_CUDA;
+  auto capture = [&](cudaGraph_t* out, auto&& body) -> ww_status {
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WW_ERR_CUDA;
+    ww_status e1 = body();
+    cudaGraph_t gr = nullptr;
+    const bool ok = cudaStreamEndCapture(cs, &gr) == cudaSuccess;
+    if (e1 != WW_OK || !ok) {
+      if (gr) cudaGraphDestroy(gr);
+      return e1 != WW_OK ? e1 : WW_ERR_CUDA;
+    }
+    *out = gr;
+    return WW_OK;
+  };
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return WW_ERR_CUDA;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) goto done;
+  S.set_stream(cs);
+  e = capture(&ga, [&] {
+    ww_status e1 = ww::launch_pre_batch(&b->grid, (int)count, p, cs);
+    return e1 == WW_OK ? S.commit() : e1;
+  });
+  if (e != WW_OK) goto done;
+  e = WW_ERR_CUDA;
+  if (cudaGraphAddChildGraphNode(&na, g, nullptr, 0, ga) != cudaSuccess) goto done;
+  e = S.add_loop_node(g, &na, &nb);
+  if (e != WW_OK) goto done;
+  e = capture(&gc, [&] {
+    ww_status e1 = S.finalize_enqueue(all);
+    if (e1 == WW_OK) e1 = ww::launch_integrate_batch(&b->grid, (int)count, cs);
+    if (e1 == WW_OK &&
+        (cudaMemcpyAsync(b->h_total_cost, b->total_cost, count * 8, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+         cudaMemcpyAsync(b->h_status, b->status, count * 4, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+         cudaMemcpyAsync(b->sv.host_ctr, b->sv.ctr, S.ctr_bytes(), cudaMemcpyDeviceToHost, cs) != cudaSuccess))
+      e1 = WW_ERR_CUDA;
+    return e1;
+  });
+  if (e != WW_OK) goto done;
+  e = WW_ERR_CUDA;
+  if (cudaGraphAddChildGraphNode(&nc, g, &nb, 1, gc) != cudaSuccess) goto done;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) goto done;
+  if (cudaGraphLaunch(ex, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) goto done;
+  b->stats = ww_solve_stats{};
+  S.fill_stats(&b->stats);
+  b->stats.residues = 0;
+  e = WW_OK;
+done:
+  S.set_stream(s);
+  if (ex) cudaGraphExecDestroy(ex);
+  if (ga) cudaGraphDestroy(ga);
+  if (gc) cudaGraphDestroy(gc);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != WW_OK) cudaGetLastError();
+  return e;
+}
+
+}  // namespace
 
 // Tiles of an m x n item: ceil((m-1)/32) ceil((n-1)/32) <= P/1024 + (m+n)/32 + 1, and
 // m + n <= P/2 + 2 for m, n >= 2, so a batch needs at most P/1024 + P/64 + 2 per item.
@@ -351,7 +454,7 @@ extern "C" {
 int64_t ww_batch_bytes(int64_t max_items, int64_t max_pixels, int64_t max_item_pixels) {
   if (max_items < 1 || max_pixels < 4 || max_item_pixels < 4) return -1;
   int64_t tiles = batch_tiles(max_items, max_pixels);
-  return max_pixels * (1 + 8 + 2) + max_items * 16 + ww::grid_batch_bytes((int)max_items, max_pixels) +
+  return max_pixels * (1 + 8 + 2 + 4) + max_items * 16 + ww::grid_batch_bytes((int)max_items, max_pixels) +
          ww::solver_bytes(max_pixels, tiles, max_items);
 }
 
@@ -371,8 +474,11 @@ ww_status ww_batch_create(int64_t max_items, int64_t max_pixels, int64_t max_ite
             cudaMalloc(&b->costs, 4 * max_pixels * 2) == cudaSuccess &&
             cudaMalloc(&b->flows, 2 * max_pixels) == cudaSuccess &&
             cudaMalloc(&b->total_cost, max_items * 8) == cudaSuccess &&
-            cudaMalloc(&b->status, max_items * 4) == cudaSuccess;
+            cudaMalloc(&b->status, max_items * 4) == cudaSuccess && cudaMalloc(&b->psi, max_pixels * 4) == cudaSuccess;
   if (ok) ok = ww::grid_batch_alloc(&b->grid, (int)max_items, max_pixels) == WW_OK;
+  if (ok)
+    ok = cudaMallocHost(&b->h_total_cost, max_items * 8) == cudaSuccess &&
+         cudaMallocHost(&b->h_status, max_items * 4) == cudaSuccess;
   ww_status st = ok ? ww::solver_alloc(&b->sv, max_pixels, tiles, max_items) : WW_ERR_OOM;
   if (st != WW_OK) {
     cudaGetLastError();
@@ -391,7 +497,10 @@ void ww_batch_free(ww_batch* b) {
   cudaFree(b->flows);
   cudaFree(b->total_cost);
   cudaFree(b->status);
+  cudaFree(b->psi);
   ww::grid_batch_free(&b->grid);
+  cudaFreeHost(b->h_total_cost);
+  cudaFreeHost(b->h_status);
   ww::solver_free(&b->sv);
   delete b;
 }
@@ -465,6 +574,12 @@ ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* 
     g.m = it.m;
     g.n = it.n;
     g.is_complex = it.is_complex ? 1 : 0;
+    if (g.is_complex) {
+      // the phase once, into the batch's phase buffer; every step then reads it
+      g.phase_src = it.ifg;
+      g.ifg = b->psi + off;
+      g.is_complex = 0;
+    }
     g.res = const_cast<int8_t*>(ph.res);
     g.ground = const_cast<int32_t*>(ph.ground);
     g.costs = const_cast<int16_t*>(ph.costs);
@@ -473,6 +588,19 @@ ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* 
     g.unw = it.unwrapped;
     g.cyc = it.cycles;
     off += it.m * it.n;
+  }
+  if (st == WW_OK && p->graph_loop && !tr) {
+    // one graph launch for the whole batch
+    st = batch_graph(b, count, p, probs, s);
+    for (int64_t k = 0; k < count; ++k) {
+      items[k].total_cost = st == WW_OK ? b->h_total_cost[k] : 0;
+      items[k].status = st == WW_OK ? b->h_status[k] : st;
+    }
+    for (auto& kv : by_l) ww_lut_free(kv.second);
+    if (st != WW_OK) return st;
+    for (int64_t k = 0; k < count; ++k)
+      if (items[k].status != WW_OK) return items[k].status;
+    return WW_OK;
   }
   if (st == WW_OK) st = ww::launch_pre_batch(&b->grid, (int)count, p, s);
   if (tr) cudaEventRecord(tev[1], s);

@@ -89,10 +89,13 @@ __device__ __forceinline__ float edge_d(float a, float b) {
 }
 
 // One CTY x CTX tile of pixels (both edges of each pixel), tile (by, bx).
+// Steep candidates are counted, and their edge keys appended to `list` while
+// it has room (`list` may be null).
 __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_complex,
                                            const float* __restrict__ coh, const uint8_t* __restrict__ mask,
                                            int64_t m, int64_t n, const int16_t* __restrict__ table, int w,
                                            float steep_rad, int16_t* __restrict__ costs, SteepCtr* ctr,
+                                           uint32_t* __restrict__ list, unsigned long long list_cap,
                                            int64_t bx, int64_t by) {
   __shared__ float sp[CPY][CPX];
   __shared__ float sc[CPY][CPX];
@@ -156,13 +159,16 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   __syncthreads();
   // 4. vertical sums, slope estimate, LUT gather, mask rule; steep candidates
   const int64_t P = m * n;
-  unsigned cnt_valid = 0, cnt_cand = 0;
-  for (int q = tid; q < CTY * CTX; q += 256) {
+  unsigned cnt_valid = 0;
+  const unsigned lane = tid & 31;
+  for (int q = tid; q < CTY * CTX; q += 256) {  // every thread runs the same number of iterations
     int r = q / CTX, c = q % CTX;
     int64_t i = i0 + r, j = j0 + c;
-    if (i >= m || j >= n) continue;
+    bool hcand = false, vcand = false;
+    const bool inside = i < m && j < n;
     int R = r + CW, C = c + CW;
     int64_t k = i * n + j;
+    if (inside) {
     // h edge (i,j)
     int16_t hp = 0, hm = 0;
     if (eh[R][C]) {
@@ -177,7 +183,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
       hp = __ldg(table + ig * kNAlpha + alpha_index(ah));
       hm = __ldg(table + ig * kNAlpha + alpha_index(-ah));
       ++cnt_valid;
-      if (fabsf(edge_d(sp[R][C], sp[R][C + 1])) > steep_rad) ++cnt_cand;
+      hcand = fabsf(edge_d(sp[R][C], sp[R][C + 1])) > steep_rad;
     }
     costs[k] = hp;
     costs[P + k] = hm;
@@ -194,27 +200,56 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
       vp = __ldg(table + ig * kNAlpha + alpha_index(av));
       vm = __ldg(table + ig * kNAlpha + alpha_index(-av));
       ++cnt_valid;
-      if (fabsf(edge_d(sp[R][C], sp[R + 1][C])) > steep_rad) ++cnt_cand;
+      vcand = fabsf(edge_d(sp[R][C], sp[R + 1][C])) > steep_rad;
     }
     costs[2 * P + k] = vp;
     costs[3 * P + k] = vm;
+    }
+    // warp-aggregated count of the candidates; the returned base places their keys in the list
+    const unsigned bh = __ballot_sync(0xffffffffu, hcand), bv = __ballot_sync(0xffffffffu, vcand);
+    const unsigned n_h = __popc(bh), tot = n_h + __popc(bv);
+    unsigned long long base = 0;
+    if (lane == 0 && tot) base = atomicAdd(&ctr->candidates, (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (list) {
+      const unsigned below = (1u << lane) - 1u;
+      if (hcand) {
+        const unsigned long long at = base + __popc(bh & below);
+        if (at < list_cap) list[at] = (uint32_t)k;
+      }
+      if (vcand) {
+        const unsigned long long at = base + n_h + __popc(bv & below);
+        if (at < list_cap) list[at] = (uint32_t)(P + k);
+      }
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    cnt_valid += __shfl_xor_sync(0xffffffffu, cnt_valid, o);
-    cnt_cand += __shfl_xor_sync(0xffffffffu, cnt_cand, o);
-  }
-  if ((tid & 31) == 0) {
-    if (cnt_valid) atomicAdd(&ctr->valid_edges, (unsigned long long)cnt_valid);
-    if (cnt_cand) atomicAdd(&ctr->candidates, (unsigned long long)cnt_cand);
-  }
+  for (int o = 16; o > 0; o >>= 1) cnt_valid += __shfl_xor_sync(0xffffffffu, cnt_valid, o);
+  if (lane == 0 && cnt_valid) atomicAdd(&ctr->valid_edges, (unsigned long long)cnt_valid);
 }
 
 __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int is_complex,
                                                const float* __restrict__ coh,
                                                const uint8_t* __restrict__ mask, int64_t m, int64_t n,
                                                const int16_t* __restrict__ table, int w, float steep_rad,
-                                               int16_t* __restrict__ costs, SteepCtr* ctr) {
-  costs_tile(ifg, is_complex, coh, mask, m, n, table, w, steep_rad, costs, ctr, blockIdx.x, blockIdx.y);
+                                               int16_t* __restrict__ costs, SteepCtr* ctr, uint32_t* list,
+                                               unsigned long long list_cap) {
+  costs_tile(ifg, is_complex, coh, mask, m, n, table, w, steep_rad, costs, ctr, list, list_cap, blockIdx.x,
+             blockIdx.y);
+}
+
+// Within the cap (mode 0) with every candidate in the list: zero the listed edges.
+__global__ void k_steep_zero_list(const SteepCtr* ctr, const uint32_t* list, unsigned long long list_cap,
+                                  int64_t P, int16_t* costs) {
+  if (ctr->mode != 0 || ctr->candidates > list_cap) return;
+  const unsigned long long nc = ctr->candidates;
+  for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < nc;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const int64_t key = list[q];
+    const int plane = key >= P;
+    const int64_t k = plane ? key - P : key;
+    costs[(2 * plane) * P + k] = 0;
+    costs[(2 * plane + 1) * P + k] = 0;
+  }
 }
 
 // ---- steep-edge bound (Sec. II-B): global selection over candidate edges ----
@@ -368,9 +403,10 @@ __global__ void __launch_bounds__(kFindThreads) k_steep_scan(const SteepCtr* ctr
 
 __global__ void k_steep_zero(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                              int64_t m, int64_t n, float steep_rad, const SteepCtr* ctr,
-                             const uint32_t* blocksum, int16_t* costs) {
+                             const uint32_t* blocksum, int16_t* costs, unsigned long long list_cap) {
   const int64_t E = 2 * m * n, P = m * n;
   const int mode = (int)ctr->mode;
+  if (mode == 0 && ctr->candidates <= list_cap) return;  // the candidate list covered it
   const uint32_t thr = (uint32_t)ctr->threshold;
   const unsigned long long take = ctr->take_at_thr;
   int64_t base = (int64_t)blockIdx.x * kSteepChunk;
@@ -563,6 +599,21 @@ __device__ __forceinline__ int item_of_block(const GridItem* it, int count, int6
   return lo;
 }
 
+constexpr int kPhasePerBlock = 256 * 8;
+
+__global__ void k_phase_b(const GridItem* __restrict__ items, int count) {
+  const int64_t b = blockIdx.x;
+  const GridItem& it = items[item_of_block<kBlkPhase>(items, count, b)];
+  const int64_t P = it.m * it.n;
+  const int64_t base = (b - it.blk[kBlkPhase]) * kPhasePerBlock;
+  const float2* z = reinterpret_cast<const float2*>(it.phase_src);
+  float* psi = const_cast<float*>(reinterpret_cast<const float*>(it.ifg));
+  for (int64_t k = base + threadIdx.x; k < min(P, base + kPhasePerBlock); k += blockDim.x) {
+    const float2 v = __ldg(z + k);
+    psi[k] = (isfinite(v.x) && isfinite(v.y)) ? cordic_phase(v.x, v.y) : __int_as_float(0x7fc00000);
+  }
+}
+
 __global__ void __launch_bounds__(RTX* RTY) k_residues_b(const GridItem* __restrict__ items, int count) {
   const int64_t b = blockIdx.x;
   const GridItem& it = items[item_of_block<kBlkRes>(items, count, b)];
@@ -578,7 +629,8 @@ __global__ void __launch_bounds__(256) k_costs_b(const GridItem* __restrict__ it
   const int64_t local = b - it.blk[kBlkCost];
   const int64_t gx = (it.n + CTX - 1) / CTX;
   costs_tile(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, it.table, w, steep_rad, it.costs,
-             reinterpret_cast<SteepCtr*>(it.steep), local % gx, local / gx);
+             reinterpret_cast<SteepCtr*>(it.steep), it.cand_list, (unsigned long long)it.cand_cap, local % gx,
+             local / gx);
 }
 
 // Cap test of every item (one thread per item); mode 1 marks the items that
@@ -793,12 +845,31 @@ __global__ void k_sel_zero_b(const GridItem* __restrict__ items, int count, floa
 }
 
 // Items within their cap: every steep candidate costs 0 in both directions.
+// Grid: x strides over an item's candidate list, y over the items.
+__global__ void k_steep_zero_list_b(const GridItem* __restrict__ items) {
+  const GridItem& it = items[blockIdx.y];
+  const SteepCtr* ctr = reinterpret_cast<const SteepCtr*>(it.steep);
+  if (ctr->mode != 0 || !it.cand_list || ctr->candidates > (unsigned long long)it.cand_cap) return;
+  const unsigned long long nc = ctr->candidates;
+  const int64_t P = it.m * it.n;
+  for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < nc;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const int64_t key = it.cand_list[q];
+    const int plane = key >= P;
+    const int64_t k = plane ? key - P : key;
+    it.costs[(2 * plane) * P + k] = 0;
+    it.costs[(2 * plane + 1) * P + k] = 0;
+  }
+}
+
+// The same for items without a complete list: a pass over every edge.
 // Items with no candidate, or over the cap (selected separately), are skipped.
 __global__ void k_steep_zero_all_b(const GridItem* __restrict__ items, int count, float steep_rad) {
   const int64_t b = blockIdx.x;
   const GridItem& it = items[item_of_block<kBlkSteep>(items, count, b)];
   const SteepCtr* ctr = reinterpret_cast<const SteepCtr*>(it.steep);
   if (ctr->mode != 0 || ctr->candidates == 0) return;
+  if (it.cand_list && ctr->candidates <= (unsigned long long)it.cand_cap) return;  // listed
   const int64_t P = it.m * it.n, E = 2 * P;
   const int64_t base = (b - it.blk[kBlkSteep]) * kSteepChunk;
   for (int64_t key = base + threadIdx.x; key < min(E, base + kSteepChunk); key += blockDim.x) {
@@ -834,16 +905,47 @@ ww_status launch_residues(const void* ifg, int is_complex, const float* coh, con
   return WW_OK;
 }
 
+namespace {
+// Wrapped phase of a complex interferogram, once per pixel (R16 CORDIC); a
+// non-finite sample gives NaN, which the float-input kernels treat as invalid
+// exactly as the complex-input kernels treat the non-finite sample.
+__global__ void k_phase(const float2* __restrict__ z, int64_t P, float* __restrict__ psi) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = __ldg(z + k);
+    psi[k] = (isfinite(v.x) && isfinite(v.y)) ? cordic_phase(v.x, v.y) : __int_as_float(0x7fc00000);
+  }
+}
+}  // namespace
+
+ww_status launch_phase(const void* ifg, int64_t m, int64_t n, float* psi, cudaStream_t s) {
+  const int64_t P = m * n;
+  int blocks = (int)std::min<int64_t>((P + 255) / 256, 148 * 16);
+  k_phase<<<blocks, 256, 0, s>>>(reinterpret_cast<const float2*>(ifg), P, psi);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}
+
+int64_t steep_list_capacity(int64_t pixels, int32_t cap_ppm) {
+  return (2 * pixels) / 1000000 * cap_ppm + ((2 * pixels) % 1000000) * cap_ppm / 1000000 + 2;
+}
+
 ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                        int64_t m, int64_t n, const int16_t* dtable, const ww_params* p,
                        ww_workspace* ws, int16_t* costs, cudaStream_t s) {
   SteepCtr* ctr = reinterpret_cast<SteepCtr*>(ws->steep_ctr);
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
   dim3 grid((unsigned)((n + CTX - 1) / CTX), (unsigned)((m + CTY - 1) / CTY));
+  // candidate list: within the cap every candidate fits (cap + 1 <= capacity), so the
+  // common case zeroes the listed edges instead of scanning every edge again
+  const int64_t need = steep_list_capacity(m * n, p->steep_cap_ppm);
+  const bool use_list = ws->steep_list && need <= ws->steep_list_cap && 2 * m * n < (1ll << 32);
+  uint32_t* list = use_list ? ws->steep_list : nullptr;
+  const unsigned long long list_cap = use_list ? (unsigned long long)ws->steep_list_cap : 0ull;
   k_costs<<<grid, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad,
-                               costs, ctr);
+                               costs, ctr, list, list_cap);
   WW_CUDA_TRY(cudaGetLastError());
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
+  if (use_list) k_steep_zero_list<<<148 * 4, 256, 0, s>>>(ctr, list, list_cap, m * n, costs);
   const int64_t E = 2 * m * n;
   int hist_blocks = 148 * 8;
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->hist, 0);
@@ -854,14 +956,14 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
   k_steep_ties<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum);
   k_steep_scan<<<1, kFindThreads, 0, s>>>(ctr, ws->blocksum, nb);
   k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum,
-                                            costs);
+                                            costs, list_cap);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
 }
 
 int64_t grid_batch_bytes(int cap, int64_t max_pixels) {
   return (int64_t)cap * ((int64_t)sizeof(GridItem) + (int64_t)sizeof(SteepCtr) + kSelBins * 4) +
-         (2 * max_pixels / kSteepChunk + cap + 1) * 4;
+         (2 * max_pixels / kSteepChunk + cap + 1) * 4 + (steep_list_capacity(max_pixels, 30000) + 2 * cap) * 4;
 }
 
 ww_status grid_batch_alloc(GridBatch* gb, int cap, int64_t max_pixels) {
@@ -874,6 +976,9 @@ ww_status grid_batch_alloc(GridBatch* gb, int cap, int64_t max_pixels) {
       cudaMalloc(&gb->hist, (int64_t)cap * kSelBins * 4) != cudaSuccess ||
       cudaMalloc(&gb->blocksum, gb->blocksum_len * 4) != cudaSuccess)
     return WW_ERR_OOM;
+  // candidate lists for the default 3% cap: sum over items of (cap_k + 2) <= this
+  gb->list_pool_cap = steep_list_capacity(max_pixels, 30000) + 2 * (int64_t)cap;
+  if (cudaMalloc(&gb->list_pool, gb->list_pool_cap * 4) != cudaSuccess) return WW_ERR_OOM;
   // the find pass clears the bins it used, so they stay zero between calls
   if (cudaMemset(gb->hist, 0, (int64_t)cap * kSelBins * 4) != cudaSuccess) return WW_ERR_CUDA;
   return WW_OK;
@@ -885,6 +990,7 @@ void grid_batch_free(GridBatch* gb) {
   cudaFree(gb->d_steep);
   cudaFree(gb->hist);
   cudaFree(gb->blocksum);
+  cudaFree(gb->list_pool);
   *gb = GridBatch{};
 }
 
@@ -906,12 +1012,22 @@ uint32_t float_bits(float f) {
 }  // namespace
 
 ww_status launch_pre_batch(GridBatch* gb, int count, const ww_params* p, cudaStream_t s) {
-  if (count < 1 || count > gb->cap) return WW_ERR_INVALID_ARG;
+  if (count < 1 || count > gb->cap || count > 65535) return WW_ERR_INVALID_ARG;
   GridItem* h = gb->h_items;
   int64_t off[kBlkKinds] = {};
+  int64_t list_off = 0;
   for (int k = 0; k < count; ++k) {
     GridItem& it = h[k];
     it.steep = reinterpret_cast<SteepCtr*>(gb->d_steep) + k;
+    const int64_t need = steep_list_capacity(it.m * it.n, p->steep_cap_ppm);
+    if (list_off + need <= gb->list_pool_cap && 2 * it.m * it.n < (1ll << 32)) {
+      it.cand_list = gb->list_pool + list_off;
+      it.cand_cap = need;
+      list_off += need;
+    } else {
+      it.cand_list = nullptr;
+      it.cand_cap = 0;
+    }
     for (int q = 0; q < kBlkKinds; ++q) it.blk[q] = off[q];
     const int64_t E = 2 * it.m * it.n;
     off[kBlkRes] += ((it.n - 1 + RTX - 1) / RTX) * ((it.m - 1 + RTY - 1) / RTY);
@@ -919,17 +1035,25 @@ ww_status launch_pre_batch(GridBatch* gb, int count, const ww_params* p, cudaStr
     off[kBlkSteep] += (E + kSteepChunk - 1) / kSteepChunk;
     off[kBlkRow] += it.m;
     off[kBlkSel] += (E + kSelChunk - 1) / kSelChunk;
+    it.blk[kBlkPhase] = off[kBlkPhase];
+    if (it.phase_src) {
+      if (it.is_complex) return WW_ERR_INVALID_ARG;  // ifg must be the float phase buffer
+      off[kBlkPhase] += (it.m * it.n + kPhasePerBlock - 1) / kPhasePerBlock;
+    }
   }
   for (int64_t o : off)
     if (o >= (1ll << 31)) return WW_ERR_INVALID_ARG;
   if (off[kBlkSteep] > gb->blocksum_len) return WW_ERR_INVALID_ARG;
   WW_CUDA_TRY(cudaMemcpyAsync(gb->d_items, h, count * sizeof(GridItem), cudaMemcpyHostToDevice, s));
   const int pb = (count + 255) / 256;
+  // phase of the complex items once (their ifg is the float buffer it lands in)
+  if (off[kBlkPhase] > 0) k_phase_b<<<(unsigned)off[kBlkPhase], 256, 0, s>>>(gb->d_items, count);
   k_prep_b<<<pb, 256, 0, s>>>(gb->d_items, count);
   k_residues_b<<<(unsigned)off[kBlkRes], dim3(RTX, RTY), 0, s>>>(gb->d_items, count);
   k_costs_b<<<(unsigned)off[kBlkCost], 256, 0, s>>>(gb->d_items, count, p->box_half_width, p->steep_rad);
   k_steep_plan_b<<<pb, 256, 0, s>>>(gb->d_items, count, p->steep_cap_ppm);
   // items within their cap
+  k_steep_zero_list_b<<<dim3(4, (unsigned)count), 256, 0, s>>>(gb->d_items);
   k_steep_zero_all_b<<<(unsigned)off[kBlkSteep], 256, 0, s>>>(gb->d_items, count, p->steep_rad);
   // items over their cap: exact selection, all items at once
   SelDigits dg;
@@ -1049,7 +1173,8 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   WW_CUDA_TRY(cudaMemsetAsync(hist, 0, 65536 * sizeof(uint32_t), s));
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
   dim3 grid((unsigned)((n + CTX - 1) / CTX), (unsigned)((m + CTY - 1) / CTY));
-  k_costs<<<grid, 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad, costs, ctr);
+  k_costs<<<grid, 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad, costs, ctr,
+                               nullptr, 0ull);
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
   const int hist_blocks = 148 * 8;
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, hist, 0);
@@ -1059,7 +1184,7 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   const int64_t nb = (2 * m * n + kSteepChunk - 1) / kSteepChunk;
   k_steep_ties<<<(unsigned)nb, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum);
   k_steep_scan<<<1, kFindThreads, 0, s>>>(ctr, blocksum, nb);
-  k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum, costs);
+  k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum, costs, 0ull);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
 }

@@ -181,6 +181,10 @@ struct SolverWs {
   void* q;             // SearchQ
   void* host_ctr;      // pinned McfCtr mirror
   void* events[2];     // search timing
+  // pinned staging of the host-built lists (so uploads can sit in a CUDA graph):
+  // order [p_cap] | border [nb_cap] | joiners [p_cap] | finalize list [p_cap] | statuses [p_cap]
+  int32_t* h_lists;
+  int64_t nb_cap;
 };
 
 // One problem handed to the solver (all pointers on the device).
@@ -213,6 +217,9 @@ struct ww_workspace {
   uint64_t* steep_ctr;  // [8]
   uint32_t* blocksum;   // per-block tie counts
   int64_t blocksum_len;
+  uint32_t* steep_list;  // keys of the steep candidates (while within capacity)
+  int64_t steep_list_cap;
+  float* psi;            // wrapped phase of a complex input, computed once per unwrap
   // statistics of the last solve
   ww_solve_stats stats;
 };
@@ -238,9 +245,13 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
 ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                            const int8_t* flows, int64_t m, int64_t n, float* unw, int32_t* cyc,
                            cudaStream_t s);
+// psi[k] = CORDIC phase of a complex64 image (NaN where a sample is not finite)
+ww_status launch_phase(const void* ifg, int64_t m, int64_t n, float* psi, cudaStream_t s);
+// candidate-list entries needed for an image of `pixels` pixels at cap_ppm (cap + 2)
+int64_t steep_list_capacity(int64_t pixels, int32_t cap_ppm);
 // Batched launches of the grid steps (ww_grid.cu): one launch per step covers
 // every item; blk[] holds each item's first block per launch kind.
-enum { kBlkRes = 0, kBlkCost = 1, kBlkSteep = 2, kBlkRow = 3, kBlkSel = 4, kBlkKinds = 5 };
+enum { kBlkRes = 0, kBlkCost = 1, kBlkSteep = 2, kBlkRow = 3, kBlkSel = 4, kBlkPhase = 5, kBlkKinds = 6 };
 struct GridItem {
   const void* ifg;
   const float* coh;
@@ -253,6 +264,10 @@ struct GridItem {
   int16_t* costs;
   const int16_t* table;
   void* steep;  // per-item steep-selection counters (set by launch_pre_batch)
+  uint32_t* cand_list;  // steep candidate keys (set by launch_pre_batch; null: no list)
+  int64_t cand_cap;
+  const void* phase_src;  // complex64 image whose phase launch_pre_batch writes into ifg (a float
+                          // buffer, is_complex 0), or null
   const int8_t* flows;
   float* unw;
   int32_t* cyc;
@@ -264,13 +279,16 @@ struct GridBatch {
   uint32_t* hist = nullptr;     // per-item selection histograms (2048 bins)
   uint32_t* blocksum = nullptr; // per-chunk tie counts of the selection
   int64_t blocksum_len = 0;
+  uint32_t* list_pool = nullptr; // steep candidate lists of all items
+  int64_t list_pool_cap = 0;
   int cap = 0;
 };
 int64_t grid_batch_bytes(int cap, int64_t max_pixels);
 ww_status grid_batch_alloc(GridBatch* gb, int cap, int64_t max_pixels);
 void grid_batch_free(GridBatch* gb);
 // residues + costs (with the steep rule, exact selection for the items over
-// their cap) of items [0, count): a fixed number of launches, no host sync
+// their cap) of items [0, count): a fixed number of launches, no host sync.
+// Items with phase_src get their phase computed once into ifg first.
 ww_status launch_pre_batch(GridBatch* gb, int count, const ww_params* p, cudaStream_t s);
 // integration of items [0, count) (fields ifg, coh, mask, m, n, is_complex,
 // flows, unw, cyc of h_items); uploads the item table
@@ -294,6 +312,17 @@ class Session {
   ww_status run_graph(ww_solve_stats* st);  // all remaining passes in one graph launch (device-driven loop)
   ww_status left(std::vector<int32_t>* out);                        // imbalanced nodes per slot
   ww_status finalize(const std::vector<int>& slots, std::vector<int32_t>* statuses);
+  // finalize without the host sync: statuses land in finalized_status() once the stream has passed
+  ww_status finalize_enqueue(const std::vector<int>& slots);
+  const int32_t* finalized_status() const;
+  // the remaining passes as one conditional while node of graph g (after dep, if any)
+  ww_status add_loop_node(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphNode_t* out);
+  void set_stream(cudaStream_t s) { stream = s; }
+  cudaStream_t get_stream() const { return stream; }
+  // the host does not know the number of imbalanced nodes (whole-graph capture)
+  void set_ncand_unknown(bool v) { ncand_unknown = v; }
+  void fill_stats(ww_solve_stats* st) const;  // counters from the host mirror of the device state
+  int64_t ctr_bytes() const;                   // size of the device counter block (host mirror)
   const McfCtr& ctr() const;
   int32_t status() const;
   int32_t ncand() const;
@@ -315,6 +344,7 @@ class Session {
   int64_t n_total = 0, t_high = 0, max_nodes = 1, n_border = 0;
   int parity = 0;
   bool capturing = false;  // enqueue_pass is being captured into a graph body
+  bool ncand_unknown = false;
 };
 
 // argument check of a ww_params (ww_api.cu)

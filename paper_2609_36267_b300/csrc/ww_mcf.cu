@@ -96,6 +96,10 @@ struct McfCtr {
   long long aug_total; // augmentations over all passes
   uint32_t band_min, band_mult, band_growth, band_start_ppm, full_passes;  // search schedule
   unsigned long long load_cycles, relax_cycles;              // phases of the tile visits
+  // first negative reduced cost seen (diagnostics): flag, node, direction, value, pass
+  int32_t dbg_set, dbg_dir;
+  long long dbg_node, dbg_red;
+  int32_t dbg_pass, dbg_pad;
 };
 
 // Problems live in slots (stable ids); `order` lists the active slots sorted by
@@ -357,6 +361,12 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
           int64_t red = FWD ? (int64_t)c - pu + pv : (int64_t)c - pv + pu;
           if (red < 0) {
             err |= kErrInternal;
+            if (atomicCAS(&ctr->dbg_set, 0, 1) == 0) {
+              ctr->dbg_node = p.node_off + i * p.C + j;
+              ctr->dbg_dir = d;
+              ctr->dbg_red = red;
+              ctr->dbg_pass = ctr->passes;
+            }
             red = 0;
           }
           if (red >= (int64_t)kNoArc)
@@ -579,7 +589,17 @@ __global__ void k_seed_tiles(Batch b, const int32_t* excess, int32_t* cand_base,
       if (!(FWD ? e > 0 : e < 0)) continue;
       const ProbDev& p = b.probs[prob_of_node(b, v)];
       int64_t loc = v - p.node_off, i = loc / p.C, j = loc % p.C;
-      tile = (int)(p.tile_off + (i / TS) * p.tiles_x + j / TS);
+      const int64_t ti = i / TS, tj = j / TS;
+      tile = (int)(p.tile_off + ti * p.tiles_x + tj);
+      // a root's label is set before the search, not by a tile visit, so no visit
+      // reports it as changed: a root on a tile edge also seeds the tile across
+      // that edge, which reads it as halo
+      bool ok = true;
+      if (i % TS == 0 && ti > 0) ok &= q_push(tile - p.tiles_x, ring, q, slots, inq);
+      if (i % TS == TS - 1 && ti + 1 < p.tiles_y) ok &= q_push(tile + p.tiles_x, ring, q, slots, inq);
+      if (j % TS == 0 && tj > 0) ok &= q_push(tile - 1, ring, q, slots, inq);
+      if (j % TS == TS - 1 && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq);
+      if (!ok) atomicOr(&ctr_err(ctr), kErrSpin);
     } else {
       tile = border[k - nc];
       if (prob_left[b.tile_prob[tile]] == 0) continue;
@@ -883,7 +903,9 @@ ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n
             cudaMalloc(&sv->status_all, n_probs * 4) == cudaSuccess &&
             cudaMalloc(&sv->q, sizeof(SearchQ)) == cudaSuccess &&
             cudaMallocHost(&sv->host_ctr, sizeof(McfCtr)) == cudaSuccess &&
-            cudaMallocHost(&sv->host_probs, n_probs * sizeof(ProbDev)) == cudaSuccess;
+            cudaMallocHost(&sv->host_probs, n_probs * sizeof(ProbDev)) == cudaSuccess &&
+            cudaMallocHost(&sv->h_lists, (4 * n_probs + nb) * 4) == cudaSuccess;
+  sv->nb_cap = nb;
   if (!ok) return WW_ERR_OOM;
   // best labels start unreached; worklist flags, ring slots and cap flags start (and end every search) zero
   if (cudaMemset(sv->best, 0xFF, n_nodes * 8) != cudaSuccess || cudaMemset(sv->inq, 0, n_tiles * 4) != cudaSuccess ||
@@ -918,6 +940,7 @@ void solver_free(SolverWs* sv) {
   cudaFree(sv->q);
   cudaFreeHost(sv->host_ctr);
   cudaFreeHost(sv->host_probs);
+  cudaFreeHost(sv->h_lists);
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(sv->events);
   if (ev[0]) cudaEventDestroy(ev[0]);
   if (ev[1]) cudaEventDestroy(ev[1]);
@@ -1047,6 +1070,9 @@ ww_status Session::commit() {
   n_total = 0;
   t_high = 0;
   max_nodes = 1;
+  int32_t* h_order = sv->h_lists;
+  int32_t* h_border = h_order + sv->p_cap;
+  int32_t* h_join = h_border + sv->nb_cap;
   std::vector<int32_t> border;
   for (int k : order) {
     const ProbDev& d = hp[k];
@@ -1065,18 +1091,22 @@ ww_status Session::commit() {
     }
   }
   n_border = (int64_t)border.size();
+  if (n_border > sv->nb_cap) return WW_ERR_INTERNAL;
+  std::copy(order.begin(), order.end(), h_order);
+  std::copy(border.begin(), border.end(), h_border);
   cudaStream_t s = stream;
+  // uploads from pinned staging: the caller syncs the stream before the next commit
   WW_CUDA_TRY(cudaMemcpyAsync(sv->probs, hp, used.size() * sizeof(ProbDev), cudaMemcpyHostToDevice, s));
   if (!order.empty()) {
-    WW_CUDA_TRY(cudaMemcpyAsync(sv->order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s));
-    WW_CUDA_TRY(cudaMemcpyAsync(sv->border, border.data(), border.size() * 4, cudaMemcpyHostToDevice, s));
+    WW_CUDA_TRY(cudaMemcpyAsync(sv->order, h_order, order.size() * 4, cudaMemcpyHostToDevice, s));
+    WW_CUDA_TRY(cudaMemcpyAsync(sv->border, h_border, border.size() * 4, cudaMemcpyHostToDevice, s));
   }
-  // the host vectors above are pageable: those copies complete before returning
   if (!pending.empty()) {
     if (pending.size() > 65535) return WW_ERR_INVALID_ARG;
     int64_t biggest = 1;
     for (int k : pending) biggest = std::max(biggest, hp[k].N);
-    WW_CUDA_TRY(cudaMemcpyAsync(sv->slot_list, pending.data(), pending.size() * 4, cudaMemcpyHostToDevice, s));
+    std::copy(pending.begin(), pending.end(), h_join);
+    WW_CUDA_TRY(cudaMemcpyAsync(sv->slot_list, h_join, pending.size() * 4, cudaMemcpyHostToDevice, s));
     dim3 gi(grid_blocks(biggest, 256, std::max(1, sm_count * 16 / (int)pending.size() + 1)), (unsigned)pending.size());
     k_join<<<gi, 256, 0, s>>>(reinterpret_cast<const ProbDev*>(sv->probs), sv->slot_list, sv->tile_prob,
                               sv->prob_left, sv->g_net, sv->tc);
@@ -1109,7 +1139,8 @@ ww_status Session::enqueue_pass() {
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(sv->events);
   const Batch b = batch();
   const McfCtr* hc = reinterpret_cast<const McfCtr*>(sv->host_ctr);
-  const int grid_cand = grid_blocks(std::max<int64_t>(1, hc->ncand) + n_border, 256, sm_count * 16);
+  const int64_t nc_bound = ncand_unknown ? n_total : std::max<int64_t>(1, hc->ncand);
+  const int grid_cand = grid_blocks(nc_bound + n_border, 256, sm_count * 16);
   const dim3 gn(grid_blocks(max_nodes, 256, std::max(1, sm_count * 16 / std::max(1, b.nact) + 1)),
                 (unsigned)std::max(1, b.nact));
   const int grid_tiles = grid_blocks(t_high, 256, sm_count * 8);
@@ -1148,19 +1179,16 @@ ww_status Session::pass(ww_solve_stats* st) {
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(sv->events);
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && st) st->ms_search_gpu += ms;
-  if (st) {
-    st->augmentations = hc->aug_total;
-    st->passes = hc->passes;
-    st->search_iterations = hc->passes;
-    st->tile_visits = (int64_t)hc->tile_visits;
-    st->local_rounds = (int64_t)hc->local_rounds;
-    st->visit_cycles = (int64_t)hc->visit_cycles;
-    st->load_cycles = (int64_t)hc->load_cycles;
-    st->relax_cycles = (int64_t)hc->relax_cycles;
+  fill_stats(st);
+  if (trace_enabled()) {
+    std::fprintf(stderr,
+                 "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu, status %d, go_on %d\n",
+                 hc->passes, hc->cap, ms, hc->naug, hc->D, hc->ncand, (unsigned long long)hc->tile_visits, hc->status,
+                 hc->go_on);
+    if (hc->err)
+      std::fprintf(stderr, "[ww]   error flags %d; first negative reduced cost: node %lld dir %d value %lld (pass %d)\n",
+                   hc->err, hc->dbg_node, hc->dbg_dir, hc->dbg_red, hc->dbg_pass);
   }
-  if (trace_enabled())
-    std::fprintf(stderr, "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu\n",
-                 hc->passes, hc->cap, ms, hc->naug, hc->D, hc->ncand, (unsigned long long)hc->tile_visits);
   return WW_OK;
 }
 
@@ -1171,35 +1199,28 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, const McfCtr* ctr) {
 }
 }  // namespace
 
-// All remaining passes in one graph launch: a conditional while node whose
-// body is a forward and a reverse pass (a pass after the last one is a no-op:
-// its kernels return when go_on is 0) followed by the loop condition.
-ww_status Session::run_graph(ww_solve_stats* st) {
+// The remaining passes as one conditional while node of graph g: its body is
+// a forward and a reverse pass (a pass after the last one is a no-op: its
+// kernels return when go_on is 0) followed by the loop condition, which is
+// set on the device.  The body is captured from enqueue_pass on a side stream.
+ww_status Session::add_loop_node(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphNode_t* out) {
   if (parity % 2 != 0) return WW_ERR_INTERNAL;
-  cudaGraph_t g = nullptr, body = nullptr;
-  cudaGraphExec_t ex = nullptr;
-  cudaStream_t cs = nullptr;
   cudaGraphConditionalHandle h;
-  ww_status e = WW_ERR_CUDA;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) return WW_ERR_CUDA;
   cudaGraphNodeParams np = {};
-  cudaGraphNode_t node;
-  cudaStream_t saved = stream;
-  const McfCtr* hc = reinterpret_cast<const McfCtr*>(sv->host_ctr);
-  const int64_t passes0 = hc->passes;
-  if (cudaGraphCreate(&g, 0) != cudaSuccess) return WW_ERR_CUDA;
-  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) goto done;
   np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = h;
   np.conditional.type = cudaGraphCondTypeWhile;
   np.conditional.size = 1;
-  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) goto done;
-  body = np.conditional.phGraph_out[0];
-  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) goto done;
-  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-    goto done;
-  stream = cs;
-  capturing = true;
-  {
+  if (cudaGraphAddNode(out, g, dep, nullptr, dep ? 1 : 0, &np) != cudaSuccess) return WW_ERR_CUDA;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return WW_ERR_CUDA;
+  ww_status e = WW_ERR_CUDA;
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    cudaStream_t saved = stream;
+    stream = cs;
+    capturing = true;
     ww_status e1 = enqueue_pass<true>();
     ww_status e2 = e1 == WW_OK ? enqueue_pass<false>() : e1;
     k_loop_cond<<<1, 1, 0, cs>>>(h, reinterpret_cast<const McfCtr*>(sv->ctr));
@@ -1207,37 +1228,54 @@ ww_status Session::run_graph(ww_solve_stats* st) {
     stream = saved;
     cudaGraph_t captured = nullptr;
     const bool cap_ok = cudaStreamEndCapture(cs, &captured) == cudaSuccess;
-    if (e2 != WW_OK || !cap_ok) {
-      e = e2 != WW_OK ? e2 : WW_ERR_CUDA;
-      goto done;
-    }
+    e = e2 != WW_OK ? e2 : (cap_ok ? WW_OK : WW_ERR_CUDA);
   }
-  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) goto done;
-  if (cudaGraphLaunch(ex, stream) != cudaSuccess) goto done;
-  if (cudaMemcpyAsync(sv->host_ctr, sv->ctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-      cudaStreamSynchronize(stream) != cudaSuccess)
-    goto done;
-  parity += 2 * (int)((hc->passes - passes0 + 1) / 2);
-  if (st) {
-    st->augmentations = hc->aug_total;
-    st->passes = hc->passes;
-    st->search_iterations = hc->passes;
-    st->tile_visits = (int64_t)hc->tile_visits;
-    st->local_rounds = (int64_t)hc->local_rounds;
-    st->visit_cycles = (int64_t)hc->visit_cycles;
-    st->load_cycles = (int64_t)hc->load_cycles;
-    st->relax_cycles = (int64_t)hc->relax_cycles;
-  }
-  e = WW_OK;
-done:
-  capturing = false;
-  stream = saved;
-  if (ex) cudaGraphExecDestroy(ex);
-  if (g) cudaGraphDestroy(g);
-  if (cs) cudaStreamDestroy(cs);
+  cudaStreamDestroy(cs);
   if (e != WW_OK) cudaGetLastError();
   return e;
 }
+
+// All remaining passes in one graph launch.
+ww_status Session::run_graph(ww_solve_stats* st) {
+  const McfCtr* hc = reinterpret_cast<const McfCtr*>(sv->host_ctr);
+  const int64_t passes0 = hc->passes;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaGraphNode_t node;
+  ww_status e = WW_ERR_CUDA;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return WW_ERR_CUDA;
+  e = add_loop_node(g, nullptr, &node);
+  if (e == WW_OK) {
+    e = WW_ERR_CUDA;
+    if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess && cudaGraphLaunch(ex, stream) == cudaSuccess &&
+        cudaMemcpyAsync(sv->host_ctr, sv->ctr, sizeof(McfCtr), cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
+        cudaStreamSynchronize(stream) == cudaSuccess)
+      e = WW_OK;
+  }
+  if (e == WW_OK) {
+    parity += 2 * (int)((hc->passes - passes0 + 1) / 2);
+    fill_stats(st);
+  }
+  if (ex) cudaGraphExecDestroy(ex);
+  if (g) cudaGraphDestroy(g);
+  if (e != WW_OK) cudaGetLastError();
+  return e;
+}
+
+void Session::fill_stats(ww_solve_stats* st) const {
+  const McfCtr* hc = reinterpret_cast<const McfCtr*>(sv->host_ctr);
+  if (!st) return;
+  st->augmentations = hc->aug_total;
+  st->passes = hc->passes;
+  st->search_iterations = hc->passes;
+  st->tile_visits = (int64_t)hc->tile_visits;
+  st->local_rounds = (int64_t)hc->local_rounds;
+  st->visit_cycles = (int64_t)hc->visit_cycles;
+  st->load_cycles = (int64_t)hc->load_cycles;
+  st->relax_cycles = (int64_t)hc->relax_cycles;
+}
+
+int64_t Session::ctr_bytes() const { return (int64_t)sizeof(McfCtr); }
 
 const McfCtr& Session::ctr() const { return *reinterpret_cast<const McfCtr*>(sv->host_ctr); }
 int32_t Session::status() const { return ctr().status; }
@@ -1256,26 +1294,53 @@ ww_status Session::left(std::vector<int32_t>* out) {
   return WW_OK;
 }
 
-ww_status Session::finalize(const std::vector<int>& list, std::vector<int32_t>* statuses) {
+namespace {
+__global__ void k_zero_slots(const int32_t* slots, int count, long long* tc) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) tc[slots[q]] = 0;
+}
+}  // namespace
+
+const int32_t* Session::finalized_status() const { return sv->h_lists + 3 * sv->p_cap + sv->nb_cap; }
+
+ww_status Session::finalize_enqueue(const std::vector<int>& list) {
   if (list.empty()) return WW_OK;
+  if (list.size() > 65535 || (int64_t)list.size() > sv->p_cap) return WW_ERR_INVALID_ARG;
   cudaStream_t s = stream;
   const ProbDev* hp = reinterpret_cast<const ProbDev*>(sv->host_probs);
+  int32_t* h_fin = sv->h_lists + 2 * sv->p_cap + sv->nb_cap;
+  int32_t* h_st = h_fin + sv->p_cap;
   int64_t biggest = 1;
-  for (int k : list) {
-    biggest = std::max(biggest, hp[k].m * hp[k].n);
-    WW_CUDA_TRY(cudaMemsetAsync(sv->tc + k, 0, 8, s));
-  }
-  WW_CUDA_TRY(cudaMemcpyAsync(sv->slot_list, list.data(), list.size() * 4, cudaMemcpyHostToDevice, s));
+  for (int k : list) biggest = std::max(biggest, hp[k].m * hp[k].n);
+  std::copy(list.begin(), list.end(), h_fin);
+  WW_CUDA_TRY(cudaMemcpyAsync(sv->slot_list, h_fin, list.size() * 4, cudaMemcpyHostToDevice, s));
   const Batch b = batch();
-  dim3 gt(grid_blocks(biggest, 256, std::max(1, sm_count * 16 / (int)list.size() + 1)), (unsigned)list.size());
+  const int nl = (int)list.size();
+  k_zero_slots<<<grid_blocks(nl, 256, 64), 256, 0, s>>>(sv->slot_list, nl, sv->tc);
+  dim3 gt(grid_blocks(biggest, 256, std::max(1, sm_count * 16 / nl + 1)), (unsigned)nl);
   k_total_cost<<<gt, 256, 0, s>>>(b, sv->slot_list, sv->tc);
   k_copy_pot<<<gt, 256, 0, s>>>(b, sv->slot_list, pot);
-  k_write_results<<<grid_blocks((int64_t)list.size(), 256, 64), 256, 0, s>>>(
-      b, sv->slot_list, (int)list.size(), reinterpret_cast<McfCtr*>(sv->ctr), sv->g_net, sv->tc, sv->status_all);
+  k_write_results<<<grid_blocks((int64_t)nl, 256, 64), 256, 0, s>>>(
+      b, sv->slot_list, nl, reinterpret_cast<McfCtr*>(sv->ctr), sv->g_net, sv->tc, sv->status_all);
   WW_CUDA_TRY(cudaGetLastError());
-  statuses->assign(list.size(), 0);
-  WW_CUDA_TRY(cudaMemcpyAsync(statuses->data(), sv->status_all, list.size() * 4, cudaMemcpyDeviceToHost, s));
-  WW_CUDA_TRY(cudaStreamSynchronize(s));
+  WW_CUDA_TRY(cudaMemcpyAsync(h_st, sv->status_all, list.size() * 4, cudaMemcpyDeviceToHost, s));
+  return WW_OK;
+}
+
+ww_status Session::finalize(const std::vector<int>& list, std::vector<int32_t>* statuses) {
+  if (list.empty()) return WW_OK;
+  ww_status e = finalize_enqueue(list);
+  if (e != WW_OK) return e;
+  WW_CUDA_TRY(cudaStreamSynchronize(stream));
+  const int32_t* h_st = finalized_status();
+  statuses->assign(h_st, h_st + list.size());
+  if (trace_enabled()) {
+    std::vector<long long> gn(sv->p_cap);
+    cudaMemcpy(gn.data(), sv->g_net, sv->p_cap * 8, cudaMemcpyDeviceToHost);
+    const McfCtr* hc = reinterpret_cast<const McfCtr*>(sv->host_ctr);
+    for (size_t q = 0; q < list.size(); ++q)
+      std::fprintf(stderr, "[ww] finalize slot %d: status %d, ground net %lld (solver status %d)\n", list[q], h_st[q],
+                   gn[list[q]], hc->status);
+  }
   return WW_OK;
 }
 

@@ -72,9 +72,9 @@ struct Request {
   ww_lut* lut = nullptr;
 };
 
-// bytes of resident state per pixel: residues 1, costs 8, flows 2, and per
-// node excess 4, labels 8, best 8, two list entries 8, root 4, potential 8
-constexpr int64_t kBytesPerPixel = 51;
+// bytes of resident state per pixel: residues 1, costs 8, flows 2, phase 4, and
+// per node excess 4, labels 8, best 8, two list entries 8, root 4, potential 8
+constexpr int64_t kBytesPerPixel = 55;
 
 }  // namespace
 
@@ -87,6 +87,7 @@ struct ww_server {
   int8_t* residues = nullptr;
   int16_t* costs = nullptr;
   int8_t* flows = nullptr;
+  float* psi = nullptr;  // phase of complex requests, by pixel range
   int32_t* ground = nullptr;
   int64_t* total_cost = nullptr;
   int32_t* status = nullptr;
@@ -197,6 +198,11 @@ void worker_loop(ww_server* S) {
       g.m = it.m;
       g.n = it.n;
       g.is_complex = it.is_complex ? 1 : 0;
+      if (g.is_complex) {
+        g.phase_src = it.ifg;
+        g.ifg = S->psi + r->pix_off;
+        g.is_complex = 0;
+      }
       g.res = res;
       g.ground = S->ground + slot;
       g.costs = cst;
@@ -251,6 +257,10 @@ void worker_loop(ww_server* S) {
         g.m = it.m;
         g.n = it.n;
         g.is_complex = it.is_complex ? 1 : 0;
+        if (g.is_complex) {  // the phase computed on admission
+          g.ifg = S->psi + r->pix_off;
+          g.is_complex = 0;
+        }
         g.flows = S->flows + 2 * r->pix_off;
         g.unw = it.unwrapped;
         g.cyc = it.cycles;
@@ -312,7 +322,7 @@ ww_status ww_server_create(const ww_server_config* cfg, const ww_params* params,
   S->tile.cap = tiles;
   bool ok = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaMalloc(&S->residues, pixels) == cudaSuccess && cudaMalloc(&S->costs, 8 * pixels) == cudaSuccess &&
-            cudaMalloc(&S->flows, 2 * pixels) == cudaSuccess &&
+            cudaMalloc(&S->flows, 2 * pixels) == cudaSuccess && cudaMalloc(&S->psi, 4 * pixels) == cudaSuccess &&
             cudaMalloc(&S->ground, 4 * (int64_t)cfg->max_active) == cudaSuccess &&
             cudaMalloc(&S->total_cost, 8 * (int64_t)cfg->max_active) == cudaSuccess &&
             cudaMalloc(&S->status, 4 * (int64_t)cfg->max_active) == cudaSuccess &&
@@ -413,6 +423,7 @@ void ww_server_destroy(ww_server* S) {
   cudaFree(S->residues);
   cudaFree(S->costs);
   cudaFree(S->flows);
+  cudaFree(S->psi);
   cudaFree(S->ground);
   cudaFree(S->total_cost);
   cudaFree(S->status);

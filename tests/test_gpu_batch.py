@@ -136,3 +136,31 @@ def test_autotune_keeps_the_optimum():
     tuned = ww.unwrap_batch(reqs, params=best)
     assert [r[2] for r in base] == [r[2] for r in tuned]
     assert all(r[3] == ww.WW_OK for r in tuned)
+
+
+def test_schedules_agree_on_the_optimum():
+    """Small distance bands, batch-wide distances and both pass loops: every
+    schedule must reach each item's optimal cost (the optimum is unique in cost).
+    These items once exposed a root on a tile edge whose label never reached
+    the tile across the edge when nothing else in its own tile changed."""
+    xs = [synth.batch_item(100000 + i) for i in (0, 7, 4)]
+    reqs = [dev_request(x) for x in xs]
+    ws = ww.Workspace(max(x.shape[0] for x in xs), max(x.shape[1] for x in xs))
+    unbanded = ww.default_params()
+    unbanded.full_passes = 1000
+    unbanded.band_start_ppm = 0
+    ref = [ww.unwrap(*r, ws=ws, params=unbanded)[2] for r in reqs]
+    for band_min in (64, 256, 1024):
+        for graph_loop in (0, 1):
+            prm = ww.default_params()
+            prm.band_min = band_min
+            prm.graph_loop = graph_loop
+            out = ww.unwrap_batch(reqs, params=prm, check=False)
+            assert [o[3] for o in out] == [ww.WW_OK] * len(xs), (band_min, graph_loop)
+            assert [o[2] for o in out] == ref, (band_min, graph_loop)
+            assert [ww.unwrap(*r, ws=ws, params=prm)[2] for r in reqs] == ref
+    # one item against the oracle's optimum (the smallest)
+    k = min(range(len(xs)), key=lambda q: xs[q].shape[0] * xs[q].shape[1])
+    ref_o = oracle_pipeline(xs[k], golden_table(xs[k].nlooks))
+    st_o, _, _, tc_o = oracle.solve_mcf(ref_o["res"], ref_o["g"], ref_o["costs"])
+    assert st_o == 0 and tc_o == ref[k]
