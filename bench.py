@@ -292,7 +292,7 @@ def run_ours(args, rank, world, local):
                 "config": {"workload": wl["name"], "pixels": px, "replicas": world,
                            "parallelism": "replicas" if world > 1 else "single",
                            "schedule": {k: getattr(prm, k) for k in ("full_passes", "band_start_ppm", "band_min",
-                                                                     "band_mult", "band_growth",
+                                                                     "band_mult", "band_growth", "ground_sink_below",
                                                                      "search_ctas_per_sm")}},
                 "e2e": {"value": px * world / (ms_e2e * 1e-3) / 1e6, "unit": "Mpixel/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -343,7 +343,8 @@ def run_batched(args):
         sample = [_dev(x, torch) for x in _generate(synth.batch_item, range(100000, 100000 + args.tune_items))]
         prm, tune = ww.autotune_batch(sample, repeats=2)
         tune["params"] = {k: getattr(prm, k) for k in ("graph_loop", "search_ctas_per_sm", "band_min", "band_mult",
-                                                        "band_growth", "band_start_ppm", "full_passes")}
+                                                        "band_growth", "band_start_ppm", "full_passes",
+                                                        "ground_sink_below")}
         del sample
     costs = None
     for _ in range(args.warmup):

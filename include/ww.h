@@ -92,7 +92,10 @@ typedef struct ww_params {
   int32_t band_start_ppm;   /* passes are banded once fewer than this many per million nodes are
                                imbalanced (default 1000000 = always) */
   int32_t full_passes;      /* the first passes search without a cap (default 0) */
-  int32_t reserved[2];
+  int32_t ground_sink_below; /* while at most this many nodes are imbalanced, the ground is no
+                               root of the search but a sink reached through the border arcs
+                               (a pass then augments only up to the ground's distance); 0 = never */
+  int32_t reserved[1];
 } ww_params;
 void ww_params_default(ww_params* p);
 
@@ -241,8 +244,8 @@ ww_status ww_batch_stats(const ww_batch* b, ww_solve_stats* out);
 /* Autotuner of the search schedule (no counterpart in the paper, whose CPU
  * solver has fixed settings).  Unwraps `items` (a sample of the workload to
  * tune for) with the starting parameters, then walks the knobs one at a time
- * (full_passes, band_start_ppm, band_min, band_mult, band_growth, search CTAs
- * per SM, graph loop), keeping a value when it lowers the device time of the whole batched
+ * (full_passes, band_start_ppm, band_min, band_mult, band_growth,
+ * ground_sink_below, search CTAs per SM, graph loop), keeping a value when it lowers the device time of the whole batched
  * unwrap (CUDA events, best of `repeats` runs).  Every trial must reproduce the
  * first trial's total cost for every item (the optimum is unique in cost even
  * where flows tie); otherwise WW_ERR_INTERNAL.  *best receives the chosen

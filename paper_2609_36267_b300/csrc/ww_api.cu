@@ -54,7 +54,8 @@ bool ww::params_valid(const ww_params* p) {
          p->steep_cap_ppm <= 1000000 && p->max_passes > 0 && p->max_sweeps > 0 && std::isfinite(p->steep_rad) &&
          (p->graph_loop == 0 || p->graph_loop == 1) && p->search_ctas_per_sm >= 0 && p->search_ctas_per_sm <= 64 &&
          p->band_min >= 1 && p->band_mult >= 0 && p->band_mult <= 1024 && p->band_growth >= 2 &&
-         p->band_growth <= 64 && p->band_start_ppm >= 0 && p->band_start_ppm <= 1000000 && p->full_passes >= 0;
+         p->band_growth <= 64 && p->band_start_ppm >= 0 && p->band_start_ppm <= 1000000 && p->full_passes >= 0 &&
+         p->ground_sink_below >= 0;
 }
 
 namespace ww {
@@ -122,6 +123,7 @@ void ww_params_default(ww_params* p) {
   p->band_growth = 8;
   p->band_start_ppm = 1000000;
   p->full_passes = 0;
+  p->ground_sink_below = 0;
 }
 
 ww_status ww_build_lut(double nlooks, ww_lut** out) {

@@ -341,7 +341,7 @@ class Session {
   int sm_count = 148, search_grid = 592;
   std::vector<char> used;
   std::vector<int> order, pending;
-  int64_t n_total = 0, t_high = 0, max_nodes = 1, n_border = 0;
+  int64_t n_total = 0, t_high = 0, max_nodes = 1, n_border = 0, max_garcs = 1;
   int parity = 0;
   bool capturing = false;  // enqueue_pass is being captured into a graph body
   bool ncand_unknown = false;

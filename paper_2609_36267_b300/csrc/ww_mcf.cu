@@ -58,6 +58,7 @@ enum : int32_t { kErrOverflow = 1, kErrInternal = 2, kErrWalk = 4, kErrSpin = 8 
 struct ProbDev {
   int64_t m, n, R, C, N;
   int64_t node_off, tile_off;
+  int64_t garc_off;      // first index of this problem's ground arcs (2C + 2R of them)
   int32_t tiles_x, tiles_y;
   const int8_t* res;
   const int32_t* ground;
@@ -96,6 +97,12 @@ struct McfCtr {
   long long aug_total; // augmentations over all passes
   uint32_t band_min, band_mult, band_growth, band_start_ppm, full_passes;  // search schedule
   unsigned long long load_cycles, relax_cycles;              // phases of the tile visits
+  // ground as a sink (late passes): the ground is no root; it is reached through
+  // border arcs at distance dG, and augmentation is limited to distance <= dG
+  int32_t gsink;
+  uint32_t dG;
+  uint32_t ground_sink_below;  // use it while at most this many nodes are imbalanced
+  int32_t gsink_pad;
   // first negative reduced cost seen (diagnostics): flag, node, direction, value, pass
   int32_t dbg_set, dbg_dir;
   long long dbg_node, dbg_red;
@@ -310,6 +317,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
   const int64_t pG = pot[b.g_index];
   const uint32_t cap = ctr->cap;
   const uint64_t capK = cap == 0xFFFFFFFFu ? KINF : ((uint64_t)cap << 29);
+  const bool gsink = ctr->gsink != 0;
   int err = 0;
   if (tid == 0) {
     rowdirty_next = 0;
@@ -338,7 +346,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       uint64_t v;
       if (i < 0 || j < 0 || i >= p.R || j >= p.C) {
         bool ring = (i >= -1 && i <= p.R && j >= -1 && j <= p.C);
-        v = ring ? 0ull : kInf;
+        v = (ring && !gsink) ? 0ull : kInf;
       } else {
         v = *((volatile const uint64_t*)&plab[i * p.C + j]);
       }
@@ -553,6 +561,8 @@ __global__ void k_pass_setup(McfCtr* ctr, SearchQ* q) {
     if (cap == 0) cap = 1;
   }
   ctr->cap = cap;
+  ctr->gsink = (uint32_t)ctr->ncand <= ctr->ground_sink_below ? 1 : 0;
+  ctr->dG = 0xFFFFFFFFu;
   q->head = q->tail = q->pending = 0;
 }
 
@@ -601,6 +611,7 @@ __global__ void k_seed_tiles(Batch b, const int32_t* excess, int32_t* cand_base,
       if (j % TS == TS - 1 && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq);
       if (!ok) atomicOr(&ctr_err(ctr), kErrSpin);
     } else {
+      if (ctr->gsink) continue;  // the ground is no root in this pass
       tile = border[k - nc];
       if (prob_left[b.tile_prob[tile]] == 0) continue;
     }
@@ -621,6 +632,7 @@ __global__ void k_count_found(const int32_t* excess, const uint64_t* labels, int
     int32_t e = excess[t];
     if ((FWD ? e < 0 : e > 0) && labels[t] != kInf) ++c;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && ctr->gsink && ctr->dG != 0xFFFFFFFFu) ++c;  // the ground
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->found, c);
 }
@@ -675,6 +687,93 @@ __device__ __forceinline__ int64_t walk_root(const ProbDev& p, const uint64_t* p
   return -1;
 }
 
+// Ground arc k of a problem (k < 2C + 2R): its border node (local) and the side
+// of the node the ground lies on.
+__device__ __forceinline__ void ground_arc(const ProbDev& p, int64_t k, int64_t* v, int* side) {
+  if (k < p.C) {
+    *v = k;
+    *side = kDirUp;
+  } else if (k < 2 * p.C) {
+    *v = (p.R - 1) * p.C + (k - p.C);
+    *side = kDirDown;
+  } else if (k < 2 * p.C + p.R) {
+    *v = (k - 2 * p.C) * p.C;
+    *side = kDirLeft;
+  } else {
+    *v = (k - 2 * p.C - p.R) * p.C + p.C - 1;
+    *side = kDirRight;
+  }
+}
+
+// Distance through ground arc k (forward search: v -> G; reverse: G -> v), or
+// 0xFFFFFFFF when v is unreached or the arc is not residual.
+template <bool FWD>
+__device__ __forceinline__ uint32_t ground_arc_dist(const ProbDev& p, const uint64_t* plab, const int64_t* ppot,
+                                                    int64_t pG, int64_t k, int64_t* vout, int* sout) {
+  int64_t v;
+  int side;
+  ground_arc(p, k, &v, &side);
+  *vout = v;
+  *sout = side;
+  const uint64_t l = plab[v];
+  if (l == kInf) return 0xFFFFFFFFu;
+  int32_t c;
+  // forward search: the arc leaving v toward the ground; reverse: entering v from it
+  if (!arc_cost<!FWD>(p, v / p.C, v % p.C, side, &c)) return 0xFFFFFFFFu;
+  const int64_t red = FWD ? (int64_t)c - ppot[v] + pG : (int64_t)c - pG + ppot[v];
+  const int64_t d = (int64_t)(l >> 32) + (red < 0 ? 0 : red);
+  return d >= 0xFFFFFFFFll ? 0xFFFFFFFEu : (uint32_t)d;
+}
+
+// Ground-sink passes: dG = the ground's distance (below the band cap).
+// Grid: x over a problem's ground arcs, y over the active problems.
+template <bool FWD>
+__global__ void k_ground_dist(Batch b, const uint64_t* labels, const int64_t* pot, McfCtr* ctr) {
+  if (!ctr->go_on || !ctr->gsink || !ctr->band_again) return;
+  const ProbDev& p = b.probs[b.order[blockIdx.y]];
+  const int64_t na = 2 * (p.C + p.R), pG = pot[b.g_index];
+  const uint32_t cap = ctr->cap;
+  uint32_t best_d = 0xFFFFFFFFu;
+  bool beyond = false;  // the ground is reachable, but only at or past the cap
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < na; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v;
+    int side;
+    const uint32_t d = ground_arc_dist<FWD>(p, labels + p.node_off, pot + p.node_off, pG, k, &v, &side);
+    if (d < cap && d < best_d) best_d = d;
+    if (d != 0xFFFFFFFFu && d >= cap) beyond = true;
+  }
+  for (int o = 16; o > 0; o >>= 1) best_d = min(best_d, __shfl_xor_sync(0xffffffffu, best_d, o));
+  if ((threadIdx.x & 31) == 0 && best_d != 0xFFFFFFFFu) atomicMin(&ctr->dG, best_d);
+  // like a label dropped at the cap: a wider band may reach the ground
+  if (__any_sync(0xffffffffu, beyond) && (threadIdx.x & 31) == 0) ctr->capped_any = 1;
+}
+
+__device__ __forceinline__ uint32_t ground_vid(const ProbDev& p, int64_t k) {
+  return 0x80000000u | (uint32_t)(p.garc_off + k);
+}
+
+// Trees that reach the ground at exactly dG propose it (ground candidates farther
+// away could not augment: the pass radius is at most dG).
+template <bool FWD>
+__global__ void k_select_ground(Batch b, const uint64_t* labels, const int64_t* pot, uint64_t* best, McfCtr* ctr) {
+  if (!ctr->go_on || !ctr->gsink || ctr->dG == 0xFFFFFFFFu) return;
+  const ProbDev& p = b.probs[b.order[blockIdx.y]];
+  const int64_t na = 2 * (p.C + p.R), pG = pot[b.g_index];
+  const uint64_t* plab = labels + p.node_off;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < na; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v;
+    int side;
+    const uint32_t d = ground_arc_dist<FWD>(p, plab, pot + p.node_off, pG, k, &v, &side);
+    if (d != ctr->dG) continue;
+    const int64_t r = walk_root(p, plab, v);
+    if (r < 0) {
+      atomicOr(&ctr->err, kErrWalk);
+      continue;
+    }
+    atomicMin((unsigned long long*)&best[p.node_off + r], ((uint64_t)d << 32) | ground_vid(p, k));
+  }
+}
+
 template <bool FWD>
 __global__ void k_select(Batch b, const int32_t* excess, const uint64_t* labels, int32_t* cand_base,
                          int32_t* cand_root, uint64_t* best, McfCtr* ctr) {
@@ -700,6 +799,36 @@ __global__ void k_select(Batch b, const int32_t* excess, const uint64_t* labels,
   }
 }
 
+// s = +1 if a move u -> v along the parent direction d of v (u is v's parent) raises dk
+__device__ __forceinline__ void dir_edge(const ProbDev& p, int64_t i, int64_t j, int d, int64_t* e, int* plane,
+                                         int* s) {
+  switch (d) {
+    case kDirUp: *e = i * p.n + j; *plane = 0; *s = 1; break;
+    case kDirDown: *e = (i + 1) * p.n + j; *plane = 0; *s = -1; break;
+    case kDirLeft: *e = i * p.n + j; *plane = 1; *s = -1; break;
+    default: *e = i * p.n + j + 1; *plane = 1; *s = 1; break;
+  }
+}
+
+// Flip dk along the path from local node v to its tree root (forward: the flow
+// runs root -> v; reverse: v -> root), stopping at the root or the ground.
+template <bool FWD>
+__device__ __forceinline__ void flip_path(const ProbDev& p, const uint64_t* plab, int64_t v) {
+  const int64_t P = p.m * p.n;
+  for (int64_t steps = 0; steps <= p.N; ++steps) {
+    int d = label_dir(plab[v]);
+    if (d == kDirRoot) break;
+    int64_t i = v / p.C, j = v % p.C;
+    int64_t e;
+    int plane, s;
+    dir_edge(p, i, j, d, &e, &plane, &s);
+    p.flows[plane * P + e] += (int8_t)(FWD ? s : -s);
+    int64_t u = nb_local(p, i, j, d);
+    if (u < 0) break;
+    v = u;
+  }
+}
+
 template <bool FWD>
 __global__ void k_augment(Batch b, int32_t* excess, const uint64_t* labels, int32_t* cand_base,
                           const int32_t* cand_root, const uint64_t* best, long long* g_net, McfCtr* ctr) {
@@ -712,31 +841,12 @@ __global__ void k_augment(Batch b, int32_t* excess, const uint64_t* labels, int3
     int32_t t = cand[q];
     uint64_t l = labels[t];
     if (best[r] != (((l >> 32) << 32) | (uint64_t)(uint32_t)t)) continue;
+    if (ctr->gsink && (uint32_t)(l >> 32) > ctr->dG) continue;  // beyond the ground: not this pass
     atomicMax(&ctr->D, (uint32_t)(l >> 32));
     atomicAdd(&ctr->naug, 1);
     const int pi = prob_of_node(b, t);
     const ProbDev& p = b.probs[pi];
-    const uint64_t* plab = labels + p.node_off;
-    const int64_t P = p.m * p.n;
-    // flip dk along the path t -> ... -> r (-> ground)
-    int64_t v = t - p.node_off;
-    for (int64_t steps = 0; steps <= p.N; ++steps) {
-      int d = label_dir(plab[v]);
-      if (d == kDirRoot) break;
-      int64_t i = v / p.C, j = v % p.C;
-      int64_t e;
-      int plane, s;  // s = +1 if the move u -> v raises dk
-      switch (d) {
-        case kDirUp: e = i * p.n + j; plane = 0; s = 1; break;
-        case kDirDown: e = (i + 1) * p.n + j; plane = 0; s = -1; break;
-        case kDirLeft: e = i * p.n + j; plane = 1; s = -1; break;
-        default: e = i * p.n + j + 1; plane = 1; s = 1; break;
-      }
-      p.flows[plane * P + e] += (int8_t)(FWD ? s : -s);
-      int64_t u = nb_local(p, i, j, d);
-      if (u < 0) break;
-      v = u;
-    }
+    flip_path<FWD>(p, labels + p.node_off, t - p.node_off);
     bool real_root = label_dir(labels[r]) == kDirRoot;
     if (FWD) {
       excess[t] += 1;
@@ -761,6 +871,45 @@ __global__ void k_reset_best(Batch b, const int32_t* cand_root, uint64_t* best, 
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nslots; q += gridDim.x * blockDim.x) prob_left[q] = 0;
 }
 
+// Trees whose best candidate is the ground: one unit through the ground arc
+// (forward: root -> ... -> v -> G, the ground absorbs; reverse: G -> v -> ... -> root).
+template <bool FWD>
+__global__ void k_augment_ground(Batch b, int32_t* excess, const uint64_t* labels, const int64_t* pot,
+                                 uint64_t* best, long long* g_net, McfCtr* ctr) {
+  if (!ctr->go_on || !ctr->gsink || ctr->dG == 0xFFFFFFFFu) return;
+  const int slot = b.order[blockIdx.y];
+  const ProbDev& p = b.probs[slot];
+  const int64_t na = 2 * (p.C + p.R), pG = pot[b.g_index], P = p.m * p.n;
+  const uint64_t* plab = labels + p.node_off;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < na; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v;
+    int side;
+    const uint32_t d = ground_arc_dist<FWD>(p, plab, pot + p.node_off, pG, k, &v, &side);
+    if (d != ctr->dG) continue;
+    const int64_t r = walk_root(p, plab, v);
+    if (r < 0 || best[p.node_off + r] != (((uint64_t)d << 32) | ground_vid(p, k))) continue;
+    // clear the tree's word here: once the ground arc is flipped it is no longer
+    // residual, so no later pass over the arcs could tell which trees proposed it
+    best[p.node_off + r] = kInf;
+    atomicMax(&ctr->D, d);
+    atomicAdd(&ctr->naug, 1);
+    // the ground arc: on the move v -> G, v is the parent of G, which lies on `side` of v
+    const int64_t i = v / p.C, j = v % p.C;
+    int64_t e;
+    int plane, sgn;
+    dir_edge(p, i, j, side, &e, &plane, &sgn);
+    p.flows[plane * P + e] += (int8_t)(FWD ? -sgn : sgn);
+    flip_path<FWD>(p, plab, v);
+    if (FWD) {
+      excess[p.node_off + r] -= 1;
+      atomicAdd((unsigned long long*)&g_net[slot], ~0ull);  // the ground absorbed a unit
+    } else {
+      excess[p.node_off + r] += 1;
+      atomicAdd((unsigned long long*)&g_net[slot], 1ull);  // the ground emitted a unit
+    }
+  }
+}
+
 // Grid: x over a problem's nodes, y over the active problems.
 template <bool FWD>
 __global__ void k_potentials(Batch b, const uint64_t* labels, int64_t* pot, const McfCtr* ctr) {
@@ -778,7 +927,7 @@ __global__ void k_potentials(Batch b, const uint64_t* labels, int64_t* pot, cons
 // The ground node is a root of every search (distance 0).
 template <bool FWD>
 __global__ void k_potential_ground(Batch b, int64_t* pot, const McfCtr* ctr) {
-  if (!ctr->go_on || ctr->naug == 0) return;
+  if (!ctr->go_on || ctr->naug == 0 || ctr->gsink) return;  // a sink ground lies at distance >= D
   pot[b.g_index] += FWD ? (int64_t)ctr->D : -(int64_t)ctr->D;
 }
 
@@ -1015,6 +1164,7 @@ Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params
   hc->band_growth = (uint32_t)std::max(2, prm->band_growth);
   hc->band_start_ppm = (uint32_t)std::max(0, prm->band_start_ppm);
   hc->full_passes = (uint32_t)std::max(0, prm->full_passes);
+  hc->ground_sink_below = (uint32_t)std::max(0, prm->ground_sink_below);
   err = cudaMemcpyAsync(sv->ctr, hc, sizeof(McfCtr), cudaMemcpyHostToDevice, s) == cudaSuccess &&
                 cudaMemsetAsync(pot + g_index, 0, 8, s) == cudaSuccess
             ? WW_OK
@@ -1074,6 +1224,15 @@ ww_status Session::commit() {
   int32_t* h_border = h_order + sv->p_cap;
   int32_t* h_join = h_border + sv->nb_cap;
   std::vector<int32_t> border;
+  int64_t garcs = 0;
+  max_garcs = 1;
+  for (int k : order) {
+    ProbDev& dm = reinterpret_cast<ProbDev*>(sv->host_probs)[k];
+    dm.garc_off = garcs;
+    garcs += 2 * (dm.R + dm.C);
+    max_garcs = std::max(max_garcs, 2 * (dm.R + dm.C));
+  }
+  if (garcs >= (1ll << 31)) return WW_ERR_INVALID_ARG;
   for (int k : order) {
     const ProbDev& d = hp[k];
     n_total += d.N;
@@ -1149,8 +1308,11 @@ ww_status Session::enqueue_pass() {
   k_seed_tiles<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->cand, ctr, sv->prob_left, sv->border,
                                               (int32_t)n_border, q, sv->slots, sv->inq, search_grid);
   if (!capturing) WW_CUDA_TRY(cudaEventRecord(ev[0], s));
+  const dim3 ga(grid_blocks(max_garcs, 256, std::max(1, sm_count * 4 / std::max(1, b.nact) + 1)),
+                (unsigned)std::max(1, b.nact));
   for (int band = 0; band < kBands; ++band) {
     k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped);
+    k_ground_dist<FWD><<<ga, 256, 0, s>>>(b, sv->labels, pot, ctr);
     k_count_found<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->labels, sv->cand, 0, ctr);
     k_band_decide<<<1, 1, 0, s>>>(ctr, q, band == kBands - 2 ? 1 : 0);
     if (band + 1 < kBands)
@@ -1159,8 +1321,10 @@ ww_status Session::enqueue_pass() {
   if (!capturing) WW_CUDA_TRY(cudaEventRecord(ev[1], s));
   k_clear_capped<<<grid_tiles, 256, 0, s>>>(b, sv->capped, ctr);
   k_select<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, ctr);
+  k_select_ground<FWD><<<ga, 256, 0, s>>>(b, sv->labels, pot, sv->best, ctr);
   k_augment<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, sv->g_net,
                                            ctr);
+  k_augment_ground<FWD><<<ga, 256, 0, s>>>(b, sv->excess, sv->labels, pot, sv->best, sv->g_net, ctr);
   k_reset_best<<<grid_cand, 256, 0, s>>>(b, sv->cand_root, sv->best, sv->prob_left, (int)sv->p_cap, ctr);
   k_potentials<FWD><<<gn, 256, 0, s>>>(b, sv->labels, pot, ctr);
   k_potential_ground<FWD><<<1, 1, 0, s>>>(b, pot, ctr);
@@ -1182,9 +1346,10 @@ ww_status Session::pass(ww_solve_stats* st) {
   fill_stats(st);
   if (trace_enabled()) {
     std::fprintf(stderr,
-                 "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu, status %d, go_on %d\n",
+                 "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu, status %d, go_on %d, "
+                 "ground sink %d (dG %u)\n",
                  hc->passes, hc->cap, ms, hc->naug, hc->D, hc->ncand, (unsigned long long)hc->tile_visits, hc->status,
-                 hc->go_on);
+                 hc->go_on, hc->gsink, hc->dG);
     if (hc->err)
       std::fprintf(stderr, "[ww]   error flags %d; first negative reduced cost: node %lld dir %d value %lld (pass %d)\n",
                    hc->err, hc->dbg_node, hc->dbg_dir, hc->dbg_red, hc->dbg_pass);

@@ -150,17 +150,34 @@ def test_schedules_agree_on_the_optimum():
     unbanded.full_passes = 1000
     unbanded.band_start_ppm = 0
     ref = [ww.unwrap(*r, ws=ws, params=unbanded)[2] for r in reqs]
-    for band_min in (64, 256, 1024):
+    for band_min, sink in ((64, 0), (256, 0), (1024, 0), (256, 1024), (1024, 64)):
         for graph_loop in (0, 1):
             prm = ww.default_params()
             prm.band_min = band_min
+            prm.ground_sink_below = sink
             prm.graph_loop = graph_loop
             out = ww.unwrap_batch(reqs, params=prm, check=False)
-            assert [o[3] for o in out] == [ww.WW_OK] * len(xs), (band_min, graph_loop)
-            assert [o[2] for o in out] == ref, (band_min, graph_loop)
+            assert [o[3] for o in out] == [ww.WW_OK] * len(xs), (band_min, sink, graph_loop)
+            assert [o[2] for o in out] == ref, (band_min, sink, graph_loop)
             assert [ww.unwrap(*r, ws=ws, params=prm)[2] for r in reqs] == ref
     # one item against the oracle's optimum (the smallest)
     k = min(range(len(xs)), key=lambda q: xs[q].shape[0] * xs[q].shape[1])
     ref_o = oracle_pipeline(xs[k], golden_table(xs[k].nlooks))
     st_o, _, _, tc_o = oracle.solve_mcf(ref_o["res"], ref_o["g"], ref_o["costs"])
     assert st_o == 0 and tc_o == ref[k]
+
+
+def test_ground_as_sink_in_every_pass_reaches_the_optimum():
+    """With the ground a sink from the first pass (augmentation limited to the
+    ground's distance in every pass) each item still reaches the oracle's optimum."""
+    xs = items(6, seed=41)
+    prm = ww.default_params()
+    prm.ground_sink_below = 1 << 30
+    res = ww.unwrap_batch([dev_request(x) for x in xs], params=prm)
+    ws = ww.Workspace(300, 300)
+    for x, (unw, K, tc, st) in zip(xs, res):
+        assert st == ww.WW_OK
+        ref = oracle_pipeline(x, golden_table(x.nlooks))
+        st_o, _, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+        assert st_o == 0 and tc == tc_o
+        assert ww.unwrap(*dev_request(x), ws=ws, params=prm)[2] == tc_o
