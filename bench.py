@@ -522,11 +522,14 @@ def run_served(args):
 
 def launch_count(st, steps):
     """Kernels of this library launched per timed step (host-driven pass loop), times steps."""
-    grid = 12  # residues, costs, steep plan/hist x2/find x2/ties/scan/zero, integrate col0/rows
-    solver_fixed = 6  # join, init_state, resume, total_cost, copy_pot, write_results
-    # pass_setup, init_labels, seed_tiles, 4 bands x (search, count_found, band_decide) + 3 reseeds,
-    # clear_capped, select, augment, reset_best, potentials, potential_ground, compact, finish_pass
-    per_pass = 26
+    # phase (complex input), residues, costs, steep plan/zero_list/hist x2/find x2/ties/scan/zero,
+    # integrate col0/rows
+    grid = 14
+    solver_fixed = 7  # join, init_state, resume, zero_slots, total_cost, copy_pot, write_results
+    # pass_setup, init_labels, seed_tiles, 4 bands x (search, ground_dist, count_found, band_decide)
+    # + 3 reseeds, clear_capped, select, select_ground, augment, augment_ground, reset_best,
+    # potentials, potential_ground, compact, finish_pass
+    per_pass = 32
     return int((grid + solver_fixed + st["passes"] * per_pass) * steps)
 
 

@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
                                                            int32_t* inq, McfCtr* ctr, int32_t* capped_flag) {
   __shared__ uint64_t lab[TSH][LROW];
   __shared__ uint32_t rc[4][TS][RCOL];
+  __shared__ int64_t spot[TSH][TSH];  // potentials with halo (the ground outside the grid)
   __shared__ int side[4];
   __shared__ int s_tile;
   __shared__ unsigned rowdirty, coldirty, rowdirty_next, coldirty_next;
@@ -344,45 +345,90 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       int r = qd / TSH, c = qd % TSH;
       int64_t i = i0 + r - 1, j = j0 + c - 1;
       uint64_t v;
+      int64_t pv;
       if (i < 0 || j < 0 || i >= p.R || j >= p.C) {
         bool ring = (i >= -1 && i <= p.R && j >= -1 && j <= p.C);
         v = (ring && !gsink) ? 0ull : kInf;
+        pv = pG;
       } else {
         v = *((volatile const uint64_t*)&plab[i * p.C + j]);
+        pv = ppot[i * p.C + j];
       }
       lab[r][c] = v;
+      spot[r][c] = pv;
     }
-    // reduced costs of the four arcs of every node (row = warp + 8k, col = lane)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      int ly = warp + 8 * k;
-      int64_t i = i0 + ly, j = j0 + lane;
-      bool ex = i < p.R && j < p.C;
-      int64_t pv = ex ? ppot[i * p.C + j] : 0;
-#pragma unroll
-      for (int d = 1; d <= 4; ++d) {
-        uint32_t r = kNoArc;
-        int32_t c;
-        if (ex && arc_cost<FWD>(p, i, j, d, &c)) {
-          int64_t u = nb_local(p, i, j, d);
-          int64_t pu = u >= 0 ? ppot[u] : pG;
-          int64_t red = FWD ? (int64_t)c - pu + pv : (int64_t)c - pv + pu;
-          if (red < 0) {
-            err |= kErrInternal;
-            if (atomicCAS(&ctr->dbg_set, 0, 1) == 0) {
-              ctr->dbg_node = p.node_off + i * p.C + j;
-              ctr->dbg_dir = d;
-              ctr->dbg_red = red;
-              ctr->dbg_pass = ctr->passes;
-            }
-            red = 0;
+    __syncthreads();
+    // reduced costs of the four arcs of every node, edge by edge: each edge's flow
+    // and two costs are read once and give the arcs of both of its nodes.
+    // rc[dir-1][node] is the arc entering the node from dir (forward search) or
+    // leaving it toward dir (reverse search); kNoArc where there is none.
+    {
+      const int64_t P = p.m * p.n;
+      // h edges h(i, j), i = i0 + er (er = 0..TS), j = j0 + lx: node A = (i-1, j) above, B = (i, j) below
+      for (int q = tid; q < (TS + 1) * TS; q += SEARCH_THREADS) {
+        const int er = q / TS, lx = q % TS;
+        const int64_t i = i0 + er, j = j0 + lx;
+        const bool a_in = i - 1 >= 0 && i - 1 < p.R && j < p.C;
+        const bool b_in = i < p.R && j < p.C;
+        uint32_t up_b = kNoArc, down_a = kNoArc;  // rc[Up][B], rc[Down][A]
+        if (a_in || b_in) {
+          const int64_t e = i * p.n + j;
+          const int dk = p.flows[e];
+          const int32_t cp = p.costs[e], cm = p.costs[P + e];
+          const int64_t pa = spot[er][lx + 1], pb = spot[er + 1][lx + 1];
+          // A->B raises dk (available unless dk = +1); B->A lowers it (unless dk = -1)
+          const bool ab_ok = dk <= 0, ba_ok = dk >= 0;
+          const int64_t ab = ab_ok ? (int64_t)(dk == 0 ? cp : -cm) - pa + pb : 0;
+          const int64_t ba = ba_ok ? (int64_t)(dk == 0 ? cm : -cp) - pb + pa : 0;
+          // forward: entering B from above = A->B, entering A from below = B->A; reverse: the opposite arcs
+          const bool ok_ub = FWD ? ab_ok : ba_ok, ok_da = FWD ? ba_ok : ab_ok;
+          const int64_t r_ub = FWD ? ab : ba, r_da = FWD ? ba : ab;
+          if (b_in && ok_ub) {
+            if (r_ub < 0) err |= kErrInternal;
+            if (r_ub >= (int64_t)kNoArc) err |= kErrOverflow;
+            else up_b = (uint32_t)max(r_ub, (int64_t)0);
           }
-          if (red >= (int64_t)kNoArc)
-            err |= kErrOverflow;
-          else
-            r = (uint32_t)red;
+          if (a_in && ok_da) {
+            if (r_da < 0) err |= kErrInternal;
+            if (r_da >= (int64_t)kNoArc) err |= kErrOverflow;
+            else down_a = (uint32_t)max(r_da, (int64_t)0);
+          }
         }
-        rc[d - 1][ly][lane] = r;
+        if (er < TS) rc[kDirUp - 1][er][lx] = up_b;
+        if (er > 0) rc[kDirDown - 1][er - 1][lx] = down_a;
+      }
+      // v edges v(i, j), i = i0 + ly, j = j0 + ec (ec = 0..TS): node L = (i, j-1) left, Rn = (i, j) right
+      for (int q = tid; q < TS * (TS + 1); q += SEARCH_THREADS) {
+        const int ly = q / (TS + 1), ec = q % (TS + 1);
+        const int64_t i = i0 + ly, j = j0 + ec;
+        const bool l_in = i < p.R && j - 1 >= 0 && j - 1 < p.C;
+        const bool r_in = i < p.R && j < p.C;
+        uint32_t left_r = kNoArc, right_l = kNoArc;  // rc[Left][Rn], rc[Right][L]
+        if (l_in || r_in) {
+          const int64_t e = i * p.n + j;
+          const int dk = p.flows[P + e];
+          const int32_t cp = p.costs[2 * P + e], cm = p.costs[3 * P + e];
+          const int64_t pl = spot[ly + 1][ec], pr = spot[ly + 1][ec + 1];
+          // Rn->L raises dk (available unless dk = +1); L->Rn lowers it (unless dk = -1)
+          const bool rl_ok = dk <= 0, lr_ok = dk >= 0;
+          const int64_t rl = rl_ok ? (int64_t)(dk == 0 ? cp : -cm) - pr + pl : 0;
+          const int64_t lr = lr_ok ? (int64_t)(dk == 0 ? cm : -cp) - pl + pr : 0;
+          // forward: entering Rn from the left = L->Rn, entering L from the right = Rn->L
+          const bool ok_lr = FWD ? lr_ok : rl_ok, ok_rl = FWD ? rl_ok : lr_ok;
+          const int64_t r_lr = FWD ? lr : rl, r_rl = FWD ? rl : lr;
+          if (r_in && ok_lr) {
+            if (r_lr < 0) err |= kErrInternal;
+            if (r_lr >= (int64_t)kNoArc) err |= kErrOverflow;
+            else left_r = (uint32_t)max(r_lr, (int64_t)0);
+          }
+          if (l_in && ok_rl) {
+            if (r_rl < 0) err |= kErrInternal;
+            if (r_rl >= (int64_t)kNoArc) err |= kErrOverflow;
+            else right_l = (uint32_t)max(r_rl, (int64_t)0);
+          }
+        }
+        if (ec < TS) rc[kDirLeft - 1][ly][ec] = left_r;
+        if (ec > 0) rc[kDirRight - 1][ly][ec - 1] = right_l;
       }
     }
     __syncthreads();
