@@ -95,7 +95,10 @@ typedef struct ww_params {
   int32_t ground_sink_below; /* while at most this many nodes are imbalanced, the ground is no
                                root of the search but a sink reached through the border arcs
                                (a pass then augments only up to the ground's distance); 0 = never */
-  int32_t reserved[1];
+  int32_t zero_stop_below;  /* while at most this many nodes are imbalanced, a banded pass first
+                               searches at distance 0 only and stops at the first imbalanced node
+                               it reaches (augmenting along zero-cost paths, no potential change);
+                               default 64; 0 = never */
 } ww_params;
 void ww_params_default(ww_params* p);
 

@@ -150,15 +150,17 @@ def test_schedules_agree_on_the_optimum():
     unbanded.full_passes = 1000
     unbanded.band_start_ppm = 0
     ref = [ww.unwrap(*r, ws=ws, params=unbanded)[2] for r in reqs]
-    for band_min, sink in ((64, 0), (256, 0), (1024, 0), (256, 1024), (1024, 64)):
+    for band_min, sink, zstop in ((64, 0, 0), (256, 0, 0), (1024, 0, 0), (256, 1024, 0), (1024, 64, 0),
+                                  (1024, 0, 1024), (256, 64, 1 << 30)):
         for graph_loop in (0, 1):
             prm = ww.default_params()
             prm.band_min = band_min
             prm.ground_sink_below = sink
+            prm.zero_stop_below = zstop
             prm.graph_loop = graph_loop
             out = ww.unwrap_batch(reqs, params=prm, check=False)
-            assert [o[3] for o in out] == [ww.WW_OK] * len(xs), (band_min, sink, graph_loop)
-            assert [o[2] for o in out] == ref, (band_min, sink, graph_loop)
+            assert [o[3] for o in out] == [ww.WW_OK] * len(xs), (band_min, sink, zstop, graph_loop)
+            assert [o[2] for o in out] == ref, (band_min, sink, zstop, graph_loop)
             assert [ww.unwrap(*r, ws=ws, params=prm)[2] for r in reqs] == ref
     # one item against the oracle's optimum (the smallest)
     k = min(range(len(xs)), key=lambda q: xs[q].shape[0] * xs[q].shape[1])
@@ -173,6 +175,22 @@ def test_ground_as_sink_in_every_pass_reaches_the_optimum():
     xs = items(6, seed=41)
     prm = ww.default_params()
     prm.ground_sink_below = 1 << 30
+    res = ww.unwrap_batch([dev_request(x) for x in xs], params=prm)
+    ws = ww.Workspace(300, 300)
+    for x, (unw, K, tc, st) in zip(xs, res):
+        assert st == ww.WW_OK
+        ref = oracle_pipeline(x, golden_table(x.nlooks))
+        st_o, _, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+        assert st_o == 0 and tc == tc_o
+        assert ww.unwrap(*dev_request(x), ws=ws, params=prm)[2] == tc_o
+
+
+def test_zero_distance_early_stop_in_every_pass_reaches_the_optimum():
+    """Every pass starting with a distance-0 band that stops at the first
+    imbalanced node reached: each item still reaches the oracle's optimum."""
+    xs = items(6, seed=43)
+    prm = ww.default_params()
+    prm.zero_stop_below = 1 << 30
     res = ww.unwrap_batch([dev_request(x) for x in xs], params=prm)
     ws = ww.Workspace(300, 300)
     for x, (unw, K, tc, st) in zip(xs, res):
