@@ -1645,7 +1645,8 @@ ww_status solve_problems(const ProbHost* ph, int nprob, SolverWs* sv, const ww_p
   e = S.finalize(all, &sts);
   if (e != WW_OK) return e;
   long long g0 = 0;
-  WW_CUDA_TRY(cudaMemcpy(&g0, sv->g_net + all[0], 8, cudaMemcpyDeviceToHost));
+  WW_CUDA_TRY(cudaMemcpyAsync(&g0, sv->g_net + all[0], 8, cudaMemcpyDeviceToHost, s));
+  WW_CUDA_TRY(cudaStreamSynchronize(s));
   st.ground_net = g0;
   if (stats) *stats = st;
   for (int32_t x : sts)
