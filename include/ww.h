@@ -96,9 +96,10 @@ typedef struct ww_params {
                                root of the search but a sink reached through the border arcs
                                (a pass then augments only up to the ground's distance); 0 = never */
   int32_t zero_stop_below;  /* while at most this many nodes are imbalanced, a banded pass first
-                               searches at distance 0 only and stops at the first imbalanced node
-                               it reaches (augmenting along zero-cost paths, no potential change);
-                               default 64; 0 = never */
+                               searches at distance 0 only, within zero_band_hops hops of the
+                               roots, and augments there if it reaches an imbalanced node
+                               (zero-cost paths, no potential change); default 64; 0 = never */
+  int32_t zero_band_hops;   /* hop radius of that first band (default 512) */
 } ww_params;
 void ww_params_default(ww_params* p);
 

@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("search_ctas_per_sm", ctypes.c_int32), ("band_min", ctypes.c_int32),
                 ("band_mult", ctypes.c_int32), ("band_growth", ctypes.c_int32),
                 ("band_start_ppm", ctypes.c_int32), ("full_passes", ctypes.c_int32),
-                ("ground_sink_below", ctypes.c_int32), ("zero_stop_below", ctypes.c_int32)]
+                ("ground_sink_below", ctypes.c_int32), ("zero_stop_below", ctypes.c_int32),
+                ("zero_band_hops", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):

@@ -55,7 +55,7 @@ bool ww::params_valid(const ww_params* p) {
          (p->graph_loop == 0 || p->graph_loop == 1) && p->search_ctas_per_sm >= 0 && p->search_ctas_per_sm <= 64 &&
          p->band_min >= 1 && p->band_mult >= 0 && p->band_mult <= 1024 && p->band_growth >= 2 &&
          p->band_growth <= 64 && p->band_start_ppm >= 0 && p->band_start_ppm <= 1000000 && p->full_passes >= 0 &&
-         p->ground_sink_below >= 0 && p->zero_stop_below >= 0;
+         p->ground_sink_below >= 0 && p->zero_stop_below >= 0 && p->zero_band_hops >= 1;
 }
 
 namespace ww {
@@ -125,6 +125,7 @@ void ww_params_default(ww_params* p) {
   p->full_passes = 0;
   p->ground_sink_below = 0;
   p->zero_stop_below = 64;
+  p->zero_band_hops = 512;
 }
 
 ww_status ww_build_lut(double nlooks, ww_lut** out) {

@@ -103,11 +103,10 @@ struct McfCtr {
   uint32_t dG;
   uint32_t ground_sink_below;  // use it while at most this many nodes are imbalanced
   int32_t gsink_pad;
-  // zero-distance first band (late passes): the band keeps only distance-0 labels
-  // and the search stops at the first imbalanced node it reaches; no potential
-  // changes follow (D = 0), so labels left unsettled elsewhere do no harm
+  // zero-distance first band (late passes): the band keeps only labels of distance
+  // 0 and fewer than zero_hops hops; augmenting inside it changes no potential (D = 0)
   int32_t zstop;       // this pass starts with such a band
-  int32_t stop;        // the search saw a candidate at distance 0: drain the worklist
+  uint32_t zero_hops;
   uint32_t zero_stop_below;  // use it while at most this many nodes are imbalanced
   uint32_t cap0;       // the pass's ordinary first cap (after the zero band)
   // first negative reduced cost seen (diagnostics): flag, node, direction, value, pass
@@ -312,42 +311,34 @@ constexpr int RCOL = TS + 1;  // padded row stride of the arc-weight planes
 template <bool FWD>
 __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int64_t* __restrict__ pot,
                                                            uint64_t* labels, SearchQ* q, int32_t* slots,
-                                                           int32_t* inq, McfCtr* ctr, int32_t* capped_flag,
-                                                           const int32_t* __restrict__ excess) {
+                                                           int32_t* inq, McfCtr* ctr, int32_t* capped_flag) {
   __shared__ uint64_t lab[TSH][LROW];
   __shared__ uint32_t rc[4][TS][RCOL];
   __shared__ int64_t spot[TSH][TSH];  // potentials with halo (the ground outside the grid)
   __shared__ int side[4];
-  __shared__ int s_tile, s_stop;
+  __shared__ int s_tile;
   __shared__ unsigned rowdirty, coldirty, rowdirty_next, coldirty_next;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;  // 8 warps
   const int ring = (int)b.t_total + (int)gridDim.x + 64;
   const int64_t pG = pot[b.g_index];
   const uint32_t cap = ctr->cap;
-  const uint64_t capK = cap == 0xFFFFFFFFu ? KINF : ((uint64_t)cap << 29);
+  // the zero band keeps keys (0, hops < zero_hops): distance 0 within a hop radius
+  const uint64_t capK = (ctr->zstop != 0 && cap == 1u) ? (uint64_t)ctr->zero_hops
+                        : (cap == 0xFFFFFFFFu ? KINF : ((uint64_t)cap << 29));
   const bool gsink = ctr->gsink != 0;
-  const bool zstop = ctr->zstop != 0 && cap == 1u;
   int err = 0;
   if (tid == 0) {
     rowdirty_next = 0;
     coldirty_next = 0;
   }
   for (;;) {
-    if (tid == 0) {
-      s_tile = q_pop(ring, q, slots, inq);
-      s_stop = zstop ? *((volatile const int32_t*)&ctr->stop) : 0;
-    }
+    if (tid == 0) s_tile = q_pop(ring, q, slots, inq);
     __syncthreads();
     const int tile = s_tile;
     if (tile < 0) {
       if (tid == 0 && tile == -2) atomicOr(&ctr->err, kErrSpin);
       break;
-    }
-    if (s_stop) {  // stopping: drop the tile (q_pop cleared its slot and flag)
-      if (tid == 0) atomicSub(&q->pending, 1);
-      __syncthreads();
-      continue;
     }
     const ProbDev& p = b.probs[b.tile_prob[tile]];
     const int64_t lt = tile - p.tile_off;
@@ -552,20 +543,6 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       capped_flag[tile] = 1;
       ctr->capped_any = 1;
     }
-    if (zstop) {
-      // an imbalanced node on the other side reached at distance 0 ends the search
-      bool hit = false;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int ly = warp + 8 * k;
-        const int64_t i = i0 + ly, j = j0 + lane;
-        if (i < p.R && j < p.C && lab[ly + 1][lane + 1] != kInf) {
-          const int32_t e = excess[p.node_off + i * p.C + j];
-          hit |= FWD ? e < 0 : e > 0;
-        }
-      }
-      if (__syncthreads_or(hit) && tid == 0) atomicExch(&ctr->stop, 1);
-    }
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -638,7 +615,6 @@ __global__ void k_pass_setup(McfCtr* ctr, SearchQ* q) {
     if (cap == 0) cap = 1;
   }
   ctr->cap0 = cap;
-  ctr->stop = 0;
   ctr->zstop = (cap != 0xFFFFFFFFu && (uint32_t)ctr->ncand <= ctr->zero_stop_below) ? 1 : 0;
   if (ctr->zstop) cap = 1;  // distance 0 only: the zero band first
   ctr->cap = cap;
@@ -999,7 +975,7 @@ __global__ void k_augment_ground(Batch b, int32_t* excess, const uint64_t* label
 // Grid: x over a problem's nodes, y over the active problems.
 template <bool FWD>
 __global__ void k_potentials(Batch b, const uint64_t* labels, int64_t* pot, const McfCtr* ctr) {
-  if (!ctr->go_on || ctr->naug == 0) return;
+  if (!ctr->go_on || ctr->naug == 0 || ctr->D == 0) return;  // D = 0: no node lies below it
   const uint32_t D = ctr->D;
   const ProbDev& p = b.probs[b.order[blockIdx.y]];
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.N; v += (int64_t)gridDim.x * blockDim.x) {
@@ -1252,6 +1228,7 @@ Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params
   hc->full_passes = (uint32_t)std::max(0, prm->full_passes);
   hc->ground_sink_below = (uint32_t)std::max(0, prm->ground_sink_below);
   hc->zero_stop_below = (uint32_t)std::max(0, prm->zero_stop_below);
+  hc->zero_hops = (uint32_t)std::max(1, std::min(prm->zero_band_hops, (1 << 29) - 1));
   err = cudaMemcpyAsync(sv->ctr, hc, sizeof(McfCtr), cudaMemcpyHostToDevice, s) == cudaSuccess &&
                 cudaMemsetAsync(pot + g_index, 0, 8, s) == cudaSuccess
             ? WW_OK
@@ -1398,8 +1375,7 @@ ww_status Session::enqueue_pass() {
   const dim3 ga(grid_blocks(max_garcs, 256, std::max(1, sm_count * 4 / std::max(1, b.nact) + 1)),
                 (unsigned)std::max(1, b.nact));
   for (int band = 0; band < kBands; ++band) {
-    k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped,
-                                                         sv->excess);
+    k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped);
     k_ground_dist<FWD><<<ga, 256, 0, s>>>(b, sv->labels, pot, ctr);
     k_count_found<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->labels, sv->cand, 0, ctr);
     k_band_decide<<<1, 1, 0, s>>>(ctr, q, band == kBands - 2 ? 1 : 0);

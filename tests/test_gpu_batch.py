@@ -185,13 +185,17 @@ def test_ground_as_sink_in_every_pass_reaches_the_optimum():
         assert ww.unwrap(*dev_request(x), ws=ws, params=prm)[2] == tc_o
 
 
-def test_zero_distance_early_stop_in_every_pass_reaches_the_optimum():
-    """Every pass starting with a distance-0 band that stops at the first
-    imbalanced node reached: each item still reaches the oracle's optimum."""
+def test_zero_distance_band_in_every_pass_reaches_the_optimum():
+    """Every pass starting with a band of distance 0 and a short hop radius: each
+    item still reaches the oracle's optimum, and a repeat gives the same flows."""
     xs = items(6, seed=43)
     prm = ww.default_params()
     prm.zero_stop_below = 1 << 30
+    prm.zero_band_hops = 64
     res = ww.unwrap_batch([dev_request(x) for x in xs], params=prm)
+    again = ww.unwrap_batch([dev_request(x) for x in xs], params=prm)
+    for a, b in zip(res, again):
+        assert a[2] == b[2] and np.array_equal(a[1].cpu().numpy(), b[1].cpu().numpy())
     ws = ww.Workspace(300, 300)
     for x, (unw, K, tc, st) in zip(xs, res):
         assert st == ww.WW_OK
