@@ -160,8 +160,13 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   // 4. vertical sums, slope estimate, LUT gather, mask rule; steep candidates
   const int64_t P = m * n;
   unsigned cnt_valid = 0;
-  const unsigned lane = tid & 31;
-  for (int q = tid; q < CTY * CTX; q += 256) {  // every thread runs the same number of iterations
+  const unsigned lane = tid & 31, warp = tid >> 5;
+  // block-level counting: one global atomic per block and iteration, not per warp
+  __shared__ unsigned s_wtot[2][8];
+  __shared__ unsigned long long s_base[2];
+  __shared__ unsigned s_valid[8];
+  int it = 0;
+  for (int q = tid; q < CTY * CTX; q += 256, it ^= 1) {  // every thread runs the same number of iterations
     int r = q / CTX, c = q % CTX;
     int64_t i = i0 + r, j = j0 + c;
     bool hcand = false, vcand = false;
@@ -205,12 +210,20 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     costs[2 * P + k] = vp;
     costs[3 * P + k] = vm;
     }
-    // warp-aggregated count of the candidates; the returned base places their keys in the list
+    // count the candidates (warp ballots, then the block); the block's base in the
+    // list plus the earlier warps' counts place each warp's keys
     const unsigned bh = __ballot_sync(0xffffffffu, hcand), bv = __ballot_sync(0xffffffffu, vcand);
     const unsigned n_h = __popc(bh), tot = n_h + __popc(bv);
-    unsigned long long base = 0;
-    if (lane == 0 && tot) base = atomicAdd(&ctr->candidates, (unsigned long long)tot);
-    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lane == 0) s_wtot[it][warp] = tot;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned bt = 0;
+      for (int w2 = 0; w2 < 8; ++w2) bt += s_wtot[it][w2];
+      s_base[it] = bt ? atomicAdd(&ctr->candidates, (unsigned long long)bt) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long base = s_base[it];
+    for (unsigned w2 = 0; w2 < warp; ++w2) base += s_wtot[it][w2];
     if (list) {
       const unsigned below = (1u << lane) - 1u;
       if (hcand) {
@@ -224,7 +237,13 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     }
   }
   for (int o = 16; o > 0; o >>= 1) cnt_valid += __shfl_xor_sync(0xffffffffu, cnt_valid, o);
-  if (lane == 0 && cnt_valid) atomicAdd(&ctr->valid_edges, (unsigned long long)cnt_valid);
+  if (lane == 0) s_valid[warp] = cnt_valid;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long v = 0;
+    for (int w2 = 0; w2 < 8; ++w2) v += s_valid[w2];
+    if (v) atomicAdd(&ctr->valid_edges, v);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int is_complex,
