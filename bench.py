@@ -326,7 +326,8 @@ def run_ours(args, rank, world, local):
                            "parallelism": "replicas" if world > 1 else "single",
                            "schedule": {k: getattr(prm, k) for k in ("full_passes", "band_start_ppm", "band_min",
                                                                      "band_mult", "band_growth", "ground_sink_below",
-                                                                     "zero_stop_below", "search_ctas_per_sm")}},
+                                                                     "zero_stop_below", "zero_band_hops",
+                                                                     "search_ctas_per_sm")}},
                 "e2e": {"value": px * world / (ms_e2e * 1e-3) / 1e6, "unit": "Mpixel/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": None, "roofline": roof, "cpu_baseline": base, "clocks": clk.summary(),
@@ -377,7 +378,7 @@ def run_batched(args):
         prm, tune = ww.autotune_batch(sample, repeats=2)
         tune["params"] = {k: getattr(prm, k) for k in ("graph_loop", "search_ctas_per_sm", "band_min", "band_mult",
                                                         "band_growth", "band_start_ppm", "full_passes",
-                                                        "ground_sink_below", "zero_stop_below")}
+                                                        "ground_sink_below", "zero_stop_below", "zero_band_hops")}
         del sample
     costs = None
     for _ in range(args.warmup):

@@ -925,7 +925,7 @@ ww_status launch_residues(const void* ifg, int is_complex, const float* coh, con
 }
 
 namespace {
-// Wrapped phase of a complex interferogram, once per pixel (R16 CORDIC); a
+// Wrapped phase of a complex interferogram, once per pixel (fixed-point CORDIC); a
 // non-finite sample gives NaN, which the float-input kernels treat as invalid
 // exactly as the complex-input kernels treat the non-finite sample.
 __global__ void k_phase(const float2* __restrict__ z, int64_t P, float* __restrict__ psi) {

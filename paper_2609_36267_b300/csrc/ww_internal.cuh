@@ -28,8 +28,10 @@ constexpr uint32_t kNoArc = 0xFFFFFFFFu;  // reduced cost of a missing residual 
 __host__ __device__ inline uint32_t label_dist(uint64_t k) { return (uint32_t)(k >> 32); }
 __host__ __device__ inline int label_dir(uint64_t k) { return (int)(k & 7); }
 
-// Fixed-point CORDIC atan2 (R16 of the design): 30 vectoring iterations, angle
-// unit 2^-29 rad; table entries are round(atan(2^-i) 2^29).
+// Fixed-point CORDIC atan2, the phase of a complex sample: the two fp32 parts
+// scaled exactly to integers with the larger below 2^30, a quadrant step, then
+// 30 vectoring iterations with angle unit 2^-29 rad; table entries are
+// round(atan(2^-i) 2^29).  Integer-only, so every build gives the same bits.
 static __constant__ int32_t kAtanQ[30] = {
     421657428, 248918915, 131521918, 66762579, 33510843, 16771758, 8387925, 4194219,
     2097141,   1048575,   524288,    262144,   131072,   65536,    32768,    16384,
@@ -37,65 +39,66 @@ static __constant__ int32_t kAtanQ[30] = {
     32,        16,        8,         4,        2,        1};
 constexpr int64_t kHalfPiQ = 843314857;  // round(pi/2 * 2^29)
 
-__device__ __forceinline__ void f32_split(float v, int64_t* M, int* E, int* neg) {
+// |v| = M 2^E for a finite fp32 value (M < 2^24), with its sign bit.
+__device__ __forceinline__ void f32_split(float v, int32_t* M, int* E, int* neg) {
   uint32_t b = __float_as_uint(v);
   *neg = (int)(b >> 31);
   int be = (int)((b >> 23) & 0xFF);
   uint32_t fr = b & 0x7FFFFFu;
-  if (be == 0) {
-    *M = fr;
-    *E = -149;
-  } else {
-    *M = (int64_t)(fr | 0x800000u);
-    *E = be - 150;
-  }
+  *M = (int32_t)(be == 0 ? fr : (fr | 0x800000u));
+  *E = be == 0 ? -149 : be - 150;
 }
 
-__device__ __forceinline__ int64_t fixed_scale(int64_t M, int E, int top, int neg) {
-  if (M == 0) return 0;
+// M 2^(E + 30 - top) truncated toward zero, negated when neg.  top is the
+// larger component's E + bit length, so the shift never exceeds 29 and the
+// larger component lands in [2^29, 2^30): every result fits 32 bits.
+__device__ __forceinline__ int32_t fixed_scale(int32_t M, int E, int top, int neg) {
   int sh = E + 30 - top;
-  int64_t r = sh >= 0 ? (M << sh) : (-sh >= 63 ? 0 : (M >> (-sh)));
+  int32_t r = sh >= 0 ? (sh >= 31 ? 0 : (M << sh)) : (-sh >= 24 ? 0 : (M >> (-sh)));
   return neg ? -r : r;
 }
 
 __device__ __forceinline__ float cordic_phase(float re, float im) {
-  int64_t Mx, My;
+  int32_t Mx, My;
   int Ex, Ey, nx, ny;
   f32_split(re, &Mx, &Ex, &nx);
   f32_split(im, &My, &Ey, &ny);
-  if (Mx == 0 && My == 0) return 0.0f;
-  int tx = Mx ? Ex + (64 - __clzll(Mx)) : -100000;
-  int ty = My ? Ey + (64 - __clzll(My)) : -100000;
+  if ((Mx | My) == 0) return 0.0f;
+  int tx = Mx ? Ex + (32 - __clz(Mx)) : -100000;
+  int ty = My ? Ey + (32 - __clz(My)) : -100000;
   int top = max(tx, ty);
-  int64_t X = fixed_scale(Mx, Ex, top, nx);
-  int64_t Y = fixed_scale(My, Ey, top, ny);
-  int64_t Z = 0;
+  int32_t X = fixed_scale(Mx, Ex, top, nx);
+  int32_t Y = fixed_scale(My, Ey, top, ny);
+  int32_t Z = 0;
   if (X < 0) {
-    int64_t t = X;
+    int32_t t = X;
     if (Y >= 0) {
       X = Y;
       Y = -t;
-      Z = kHalfPiQ;
+      Z = (int32_t)kHalfPiQ;
     } else {
       X = -Y;
       Y = t;
-      Z = -kHalfPiQ;
+      Z = -(int32_t)kHalfPiQ;
     }
   }
+  // Vectoring iterations in 32-bit registers.  With |X|, |Y| < 2^30 and X >= 0
+  // here, X only grows, to at most the CORDIC gain (1.647) times |(X, Y)| <
+  // 2^32 (unsigned); |Y| stays below max(|Y|, X >> i) < 2^31; |Z| <= pi 2^29.
+  // s is -1 when Y < 0 and 0 otherwise, and (v ^ s) - s is v negated when
+  // Y < 0, so each step is one branch-free sequence: X += |Y >> i| rounded
+  // as the arithmetic shift does, Y -= sign(Y) (X >> i), Z += sign(Y) atan(2^-i).
+  uint32_t x = (uint32_t)X;
+  int32_t y = Y, z = Z;
 #pragma unroll
   for (int i = 0; i < 30; ++i) {
-    int64_t xs = X >> i, ys = Y >> i;
-    if (Y >= 0) {
-      X += ys;
-      Y -= xs;
-      Z += kAtanQ[i];
-    } else {
-      X -= ys;
-      Y += xs;
-      Z -= kAtanQ[i];
-    }
+    const int32_t s = y >> 31;
+    const int32_t xs = (int32_t)(x >> i);
+    x += (uint32_t)(((y >> i) ^ s) - s);
+    y -= (xs ^ s) - s;
+    z += (kAtanQ[i] ^ s) - s;
   }
-  float psi = __fmul_rn(__ll2float_rn(Z), 1.0f / 536870912.0f);
+  float psi = __fmul_rn(__int2float_rn(z), 1.0f / 536870912.0f);
   return fminf(fmaxf(psi, -kPiF), kPiF);
 }
 
@@ -133,7 +136,7 @@ __device__ __forceinline__ Pix load_pixel(const void* ifg, int is_complex, const
   return p;
 }
 
-// LUT indices (R8): fp32, every operation rounded separately.
+// LUT indices: fp32, every operation rounded separately.
 __device__ __forceinline__ int alpha_index(float a) {
   float t = __fmul_rn(__fadd_rn(a, kPiF), kAlphaScale);
   int k = (int)floorf(t);

@@ -239,3 +239,34 @@ def test_unwrap_end_to_end(name, ws):
     exact = ref["psi"].astype(np.float64) + 2 * np.pi * Kn
     assert np.max(np.abs(u[v] - exact[v]), initial=0.0) <= 1e-5
     assert Kn[0, 0] == 0
+
+
+def test_complex_phase_bit_exact_extremes(ws):
+    """Phase of complex samples over the whole fp32 range (random bit patterns,
+    subnormals, signed zeros, axes, equal parts, parts 2^100 apart): the
+    unwrapped output equals fp32(psi + 2 pi K) in fp64 with the oracle's psi
+    and the returned K, bit for bit, at every valid pixel."""
+    rng = np.random.default_rng(31)
+    m, n = 96, 80
+    bits = rng.integers(0, 2**32, size=(m, n, 2), dtype=np.uint64).astype(np.uint32)
+    bits[(bits & 0x7F800000) == 0x7F800000] &= 0xBF7FFFFF  # keep every part finite
+    z = bits.view(np.float32).copy()
+    special = np.array([0.0, -0.0, 1.0, -1.0, 1e-45, -1e-45, 1.1754942e-38, 3.4028235e38, -3.4028235e38,
+                        1e-30, 1e30, 0.5, -3.0], np.float32)
+    k = 0
+    for a in special:
+        for b in special:
+            z[k // n, k % n] = (a, b)
+            k += 1
+    t = rng.uniform(-1, 1, size=(m // 4, n, 2)).astype(np.float32)
+    z[m // 2: m // 2 + m // 4] = t * np.float32(2.0) ** rng.integers(-120, 120, size=(m // 4, n, 1)).astype(np.float32)
+    ifg = np.ascontiguousarray(z).view(np.complex64).reshape(m, n)
+    coh = rng.uniform(0.05, 0.9, size=(m, n)).astype(np.float32)
+    mask = np.ones((m, n), np.uint8)
+    unw, K, tc = ww.unwrap(to_dev(ifg), to_dev(coh), 4.0, to_dev(mask), ws=ws)
+    u, Kn = unw.cpu().numpy(), K.cpu().numpy()
+    psi, _, valid = oracle.prepare(coh, mask, ifg=ifg)
+    v = valid.astype(bool)
+    assert v.all()
+    want = (psi.astype(np.float64) + Kn.astype(np.float64) * 6.283185307179586).astype(np.float32)
+    assert np.array_equal(u.view(np.uint32)[v], want.view(np.uint32)[v])
