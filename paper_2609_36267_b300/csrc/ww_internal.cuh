@@ -170,6 +170,8 @@ struct SolverWs {
   int32_t* inq;        // [t_cap] 1 while a tile is queued
   int32_t* slots;      // [t_cap + ring slack] worklist ring (tile + 1, 0 = empty)
   int32_t* capped;     // [t_cap] tile dropped a candidate at the distance cap
+  int32_t* touched;    // [t_cap] 1 once the search visited the tile in this pass
+  int32_t* tlist;      // [t_cap] tiles the search visited in this pass
   int32_t* tile_prob;  // [t_cap] tile -> problem
   int32_t* border;     // border tiles of every problem
   void* probs;         // ProbDev [p_cap]

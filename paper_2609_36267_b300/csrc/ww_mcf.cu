@@ -113,6 +113,8 @@ struct McfCtr {
   int32_t dbg_set, dbg_dir;
   long long dbg_node, dbg_red;
   int32_t dbg_pass, dbg_pad;
+  int32_t ntouched;    // tiles listed as visited in this pass
+  int32_t ntouched_pad;
 };
 
 // Problems live in slots (stable ids); `order` lists the active slots sorted by
@@ -311,7 +313,8 @@ constexpr int RCOL = TS + 1;  // padded row stride of the arc-weight planes
 template <bool FWD>
 __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int64_t* __restrict__ pot,
                                                            uint64_t* labels, SearchQ* q, int32_t* slots,
-                                                           int32_t* inq, McfCtr* ctr, int32_t* capped_flag) {
+                                                           int32_t* inq, McfCtr* ctr, int32_t* capped_flag,
+                                                           int32_t* touched, int32_t* tlist) {
   __shared__ uint64_t lab[TSH][LROW];
   __shared__ uint32_t rc[4][TS][RCOL];
   __shared__ int64_t spot[TSH][TSH];  // potentials with halo (the ground outside the grid)
@@ -347,6 +350,13 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
     uint64_t* plab = labels + p.node_off;
     const int64_t* ppot = pot + p.node_off;
     if (tid < 4) side[tid] = 0;
+    // first visit of the tile in this pass: list it, so that its labels are
+    // reset after the pass without a sweep over every node
+    if (tid == 0 && atomicExch(&touched[tile], 1) == 0) {
+      const int k = atomicAdd(&ctr->ntouched, 1);
+      if (k < (int)b.t_total) tlist[k] = tile;
+      else err |= kErrInternal;
+    }
     const long long t_start = clock64();
     // labels with halo; directly outside the grid stands G, a root (label 0)
     for (int qd = tid; qd < TSH * TSH; qd += SEARCH_THREADS) {
@@ -573,11 +583,12 @@ __device__ __forceinline__ int32_t* cand_nxt(int32_t* base, const McfCtr* c, int
 }
 
 // A problem joins: imbalances from its residues, its imbalanced nodes appended
-// to the current list, and every node potential set to the current ground
-// potential (all its reduced costs then equal its raw costs, >= 0).
+// to the current list, every node potential set to the current ground
+// potential (all its reduced costs then equal its raw costs, >= 0) and every
+// label unreached.
 // Grid: x over the problem's nodes, y over the listed slots.
 __global__ void k_init_state(Batch b, const int32_t* slots, int32_t* excess, int32_t* cand_base, int64_t* pot,
-                             int32_t* prob_left, McfCtr* ctr) {
+                             uint64_t* labels, int32_t* prob_left, McfCtr* ctr) {
   const int slot = slots[blockIdx.y];
   const ProbDev& p = b.probs[slot];
   const int64_t pg = pot[b.g_index];
@@ -587,6 +598,7 @@ __global__ void k_init_state(Batch b, const int32_t* slots, int32_t* excess, int
     int32_t r = p.res[v];
     excess[p.node_off + v] = r;
     pot[p.node_off + v] = pg;
+    labels[p.node_off + v] = kInf;
     if (r != 0) {
       cand[atomicAdd(&ctr->ncand, 1)] = (int32_t)(p.node_off + v);
       ++cnt;
@@ -623,15 +635,20 @@ __global__ void k_pass_setup(McfCtr* ctr, SearchQ* q) {
   q->head = q->tail = q->pending = 0;
 }
 
-// Grid: x over a problem's nodes, y over the active problems.
+// Labels at the start of a pass: every label is unreached already (set when a
+// problem joins, and reset after each pass on the tiles the search visited and
+// at the listed nodes), so only the roots are set, to distance 0: the excess
+// nodes forward, the deficit nodes reverse.
 template <bool FWD>
-__global__ void k_init_labels(Batch b, const int32_t* excess, uint64_t* labels, const McfCtr* ctr) {
+__global__ void k_set_roots(const int32_t* excess, int32_t* cand_base, int64_t n_total, uint64_t* labels,
+                            const McfCtr* ctr) {
   if (!ctr->go_on) return;
-  const ProbDev& p = b.probs[b.order[blockIdx.y]];
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.N; v += (int64_t)gridDim.x * blockDim.x) {
-    int32_t e = excess[p.node_off + v];
-    bool root = FWD ? e > 0 : e < 0;
-    labels[p.node_off + v] = root ? 0ull : kInf;
+  const int nc = ctr->ncand;
+  const int32_t* cand = cand_cur(cand_base, ctr, n_total);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+    const int32_t v = cand[q];
+    const int32_t e = excess[v];
+    if (FWD ? e > 0 : e < 0) labels[v] = 0ull;
   }
 }
 
@@ -972,17 +989,33 @@ __global__ void k_augment_ground(Batch b, int32_t* excess, const uint64_t* label
   }
 }
 
-// Grid: x over a problem's nodes, y over the active problems.
+// After a pass, on the tiles the search visited (one block per tile, grid-
+// stride over the list): potentials p += D - d forward (p -= D - d reverse)
+// for the nodes labelled below the largest augmented distance D, then every
+// label back to unreached and the tile unlisted.  Nodes outside these tiles
+// hold no label (roots lie on seeded tiles, which the search visits).
 template <bool FWD>
-__global__ void k_potentials(Batch b, const uint64_t* labels, int64_t* pot, const McfCtr* ctr) {
-  if (!ctr->go_on || ctr->naug == 0 || ctr->D == 0) return;  // D = 0: no node lies below it
+__global__ void k_potentials(Batch b, uint64_t* labels, int64_t* pot, int32_t* touched, const int32_t* tlist,
+                             const McfCtr* ctr) {
+  const bool apply = ctr->go_on && ctr->naug != 0 && ctr->D != 0;  // D = 0: no node lies below it
   const uint32_t D = ctr->D;
-  const ProbDev& p = b.probs[b.order[blockIdx.y]];
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.N; v += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t l = labels[p.node_off + v];
-    if (l == kInf) continue;
-    uint32_t d = (uint32_t)(l >> 32);
-    if (d < D) pot[p.node_off + v] += FWD ? (int64_t)(D - d) : -(int64_t)(D - d);
+  const int nt = ctr->ntouched;
+  for (int k = blockIdx.x; k < nt; k += gridDim.x) {
+    const int tile = tlist[k];
+    const ProbDev& p = b.probs[b.tile_prob[tile]];
+    const int64_t lt = tile - p.tile_off;
+    const int64_t i0 = (lt / p.tiles_x) * TS, j0 = (lt % p.tiles_x) * TS;
+    for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
+      const int64_t i = i0 + q / TS, j = j0 + q % TS;
+      if (i >= p.R || j >= p.C) continue;
+      const int64_t v = p.node_off + i * p.C + j;
+      const uint64_t l = labels[v];
+      if (l == kInf) continue;
+      const uint32_t d = (uint32_t)(l >> 32);
+      if (apply && d < D) pot[v] += FWD ? (int64_t)(D - d) : -(int64_t)(D - d);
+      labels[v] = kInf;
+    }
+    if (threadIdx.x == 0) touched[tile] = 0;
   }
 }
 
@@ -993,13 +1026,15 @@ __global__ void k_potential_ground(Batch b, int64_t* pot, const McfCtr* ctr) {
   pot[b.g_index] += FWD ? (int64_t)ctr->D : -(int64_t)ctr->D;
 }
 
-__global__ void k_compact(Batch b, const int32_t* excess, int32_t* cand_base, int32_t* prob_left, McfCtr* ctr) {
+__global__ void k_compact(Batch b, const int32_t* excess, int32_t* cand_base, uint64_t* labels, int32_t* prob_left,
+                          McfCtr* ctr) {
   if (!ctr->go_on) return;
   const int nc = ctr->ncand;
   const int32_t* cand = cand_cur(cand_base, ctr, b.n_total);
   int32_t* next = cand_nxt(cand_base, ctr, b.n_total);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
     int32_t v = cand[q];
+    labels[v] = kInf;  // a root on a tile the search did not reach (an aborted search)
     if (excess[v] != 0) {
       next[atomicAdd(&ctr->ncand_next, 1)] = v;
       atomicAdd(&prob_left[prob_of_node(b, v)], 1);
@@ -1009,6 +1044,7 @@ __global__ void k_compact(Batch b, const int32_t* excess, int32_t* cand_base, in
 
 // End of a pass: swap the candidate lists and decide whether to go on.
 __global__ void k_finish_pass(McfCtr* ctr) {
+  ctr->ntouched = 0;  // the list was reset with the labels
   if (!ctr->go_on) return;
   ctr->ncand = ctr->ncand_next;
   ctr->ncand_next = 0;
@@ -1032,17 +1068,37 @@ __global__ void k_finish_pass(McfCtr* ctr) {
 }
 
 // Total cost of the listed slots; grid: x over a problem's pixels, y over the list.
+// Flows are mostly zero: with both planes 16-byte aligned the flows are read
+// 16 edges at a time and the costs only where an edge carries flow.
+__device__ __forceinline__ long long edge_cost(const ProbDev& p, int64_t P, int64_t e, int a, int c) {
+  long long s = 0;
+  if (a == 1) s += p.costs[e];
+  if (a == -1) s += p.costs[P + e];
+  if (c == 1) s += p.costs[2 * P + e];
+  if (c == -1) s += p.costs[3 * P + e];
+  return s;
+}
+
 __global__ void k_total_cost(Batch b, const int32_t* slots, long long* tc) {
   const int slot = slots[blockIdx.y];
   const ProbDev& p = b.probs[slot];
   const int64_t P = p.m * p.n;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
   long long s = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
-    int a = p.flows[e], c = p.flows[P + e];
-    if (a == 1) s += p.costs[e];
-    if (a == -1) s += p.costs[P + e];
-    if (c == 1) s += p.costs[2 * P + e];
-    if (c == -1) s += p.costs[3 * P + e];
+  if ((reinterpret_cast<uintptr_t>(p.flows) & 15) == 0 && (P & 15) == 0) {
+    const uint4* fa = reinterpret_cast<const uint4*>(p.flows);
+    const uint4* fc = reinterpret_cast<const uint4*>(p.flows + P);
+    for (int64_t k = t0; k < P / 16; k += stride) {
+      const uint4 a = fa[k], c = fc[k];
+      if ((a.x | a.y | a.z | a.w | c.x | c.y | c.z | c.w) == 0) continue;
+      const int8_t* ab = reinterpret_cast<const int8_t*>(&a);
+      const int8_t* cb = reinterpret_cast<const int8_t*>(&c);
+#pragma unroll
+      for (int t = 0; t < 16; ++t)
+        if (ab[t] | cb[t]) s += edge_cost(p, P, 16 * k + t, ab[t], cb[t]);
+    }
+  } else {
+    for (int64_t e = t0; e < P; e += stride) s += edge_cost(p, P, e, p.flows[e], p.flows[P + e]);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd((unsigned long long*)&tc[slot], (unsigned long long)s);
@@ -1091,7 +1147,7 @@ bool trace_enabled() {
 // ---------------- host side ----------------
 
 int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
-  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8) + (n_nodes + 1) * 8 + n_tiles * 4 * 6 + (kMaxSearchGrid + 64) * 4 +
+  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 + (kMaxSearchGrid + 64) * 4 +
          n_probs * (sizeof(ProbDev) + 4 + 8 + 8 + 16 + 12) + (int64_t)sizeof(McfCtr) + 4096;
 }
 
@@ -1107,6 +1163,7 @@ ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n
             cudaMalloc(&sv->pot, (n_nodes + 1) * 8) == cudaSuccess && cudaMalloc(&sv->inq, n_tiles * 4) == cudaSuccess &&
             cudaMalloc(&sv->slots, (n_tiles + kMaxSearchGrid + 64) * 4) == cudaSuccess &&
             cudaMalloc(&sv->capped, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tile_prob, n_tiles * 4) == cudaSuccess &&
+            cudaMalloc(&sv->touched, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tlist, n_tiles * 4) == cudaSuccess &&
             cudaMalloc(&sv->border, nb * 4) == cudaSuccess && cudaMalloc(&sv->probs, n_probs * sizeof(ProbDev)) == cudaSuccess &&
             cudaMalloc(&sv->prob_left, n_probs * 4) == cudaSuccess && cudaMalloc(&sv->g_net, n_probs * 8) == cudaSuccess &&
             cudaMalloc(&sv->tc, n_probs * 8) == cudaSuccess && cudaMalloc(&sv->ctr, sizeof(McfCtr)) == cudaSuccess &&
@@ -1118,10 +1175,11 @@ ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n
             cudaMallocHost(&sv->h_lists, (4 * n_probs + nb) * 4) == cudaSuccess;
   sv->nb_cap = nb;
   if (!ok) return WW_ERR_OOM;
-  // best labels start unreached; worklist flags, ring slots and cap flags start (and end every search) zero
+  // best labels start unreached; worklist flags, ring slots, cap flags and visit
+  // flags start (and end every search or pass) zero
   if (cudaMemset(sv->best, 0xFF, n_nodes * 8) != cudaSuccess || cudaMemset(sv->inq, 0, n_tiles * 4) != cudaSuccess ||
       cudaMemset(sv->slots, 0, (n_tiles + kMaxSearchGrid + 64) * 4) != cudaSuccess ||
-      cudaMemset(sv->capped, 0, n_tiles * 4) != cudaSuccess)
+      cudaMemset(sv->capped, 0, n_tiles * 4) != cudaSuccess || cudaMemset(sv->touched, 0, n_tiles * 4) != cudaSuccess)
     return WW_ERR_CUDA;
   cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(sv->events);
   if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) return WW_ERR_CUDA;
@@ -1138,6 +1196,8 @@ void solver_free(SolverWs* sv) {
   cudaFree(sv->inq);
   cudaFree(sv->slots);
   cudaFree(sv->capped);
+  cudaFree(sv->touched);
+  cudaFree(sv->tlist);
   cudaFree(sv->tile_prob);
   cudaFree(sv->border);
   cudaFree(sv->probs);
@@ -1333,7 +1393,7 @@ ww_status Session::commit() {
     dim3 gi(grid_blocks(biggest, 256, std::max(1, sm_count * 16 / (int)pending.size() + 1)), (unsigned)pending.size());
     k_join<<<gi, 256, 0, s>>>(reinterpret_cast<const ProbDev*>(sv->probs), sv->slot_list, sv->tile_prob,
                               sv->prob_left, sv->g_net, sv->tc);
-    k_init_state<<<gi, 256, 0, s>>>(batch(), sv->slot_list, sv->excess, sv->cand, pot, sv->prob_left,
+    k_init_state<<<gi, 256, 0, s>>>(batch(), sv->slot_list, sv->excess, sv->cand, pot, sv->labels, sv->prob_left,
                                     reinterpret_cast<McfCtr*>(sv->ctr));
     pending.clear();
   }
@@ -1364,18 +1424,17 @@ ww_status Session::enqueue_pass() {
   const McfCtr* hc = reinterpret_cast<const McfCtr*>(sv->host_ctr);
   const int64_t nc_bound = ncand_unknown ? n_total : std::max<int64_t>(1, hc->ncand);
   const int grid_cand = grid_blocks(nc_bound + n_border, 256, sm_count * 16);
-  const dim3 gn(grid_blocks(max_nodes, 256, std::max(1, sm_count * 16 / std::max(1, b.nact) + 1)),
-                (unsigned)std::max(1, b.nact));
   const int grid_tiles = grid_blocks(t_high, 256, sm_count * 8);
   k_pass_setup<<<1, 1, 0, s>>>(ctr, q);
-  k_init_labels<FWD><<<gn, 256, 0, s>>>(b, sv->excess, sv->labels, ctr);
+  k_set_roots<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->cand, 0, sv->labels, ctr);
   k_seed_tiles<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->cand, ctr, sv->prob_left, sv->border,
                                               (int32_t)n_border, q, sv->slots, sv->inq, search_grid);
   if (!capturing) WW_CUDA_TRY(cudaEventRecord(ev[0], s));
   const dim3 ga(grid_blocks(max_garcs, 256, std::max(1, sm_count * 4 / std::max(1, b.nact) + 1)),
                 (unsigned)std::max(1, b.nact));
   for (int band = 0; band < kBands; ++band) {
-    k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped);
+    k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped,
+                                                         sv->touched, sv->tlist);
     k_ground_dist<FWD><<<ga, 256, 0, s>>>(b, sv->labels, pot, ctr);
     k_count_found<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->labels, sv->cand, 0, ctr);
     k_band_decide<<<1, 1, 0, s>>>(ctr, q, band == kBands - 2 ? 1 : 0);
@@ -1390,9 +1449,9 @@ ww_status Session::enqueue_pass() {
                                            ctr);
   k_augment_ground<FWD><<<ga, 256, 0, s>>>(b, sv->excess, sv->labels, pot, sv->best, sv->g_net, ctr);
   k_reset_best<<<grid_cand, 256, 0, s>>>(b, sv->cand_root, sv->best, sv->prob_left, (int)sv->p_cap, ctr);
-  k_potentials<FWD><<<gn, 256, 0, s>>>(b, sv->labels, pot, ctr);
+  k_potentials<FWD><<<sm_count * 8, 256, 0, s>>>(b, sv->labels, pot, sv->touched, sv->tlist, ctr);
   k_potential_ground<FWD><<<1, 1, 0, s>>>(b, pot, ctr);
-  k_compact<<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->cand, sv->prob_left, ctr);
+  k_compact<<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->cand, sv->labels, sv->prob_left, ctr);
   k_finish_pass<<<1, 1, 0, s>>>(ctr);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
