@@ -17,9 +17,11 @@ namespace ww {
 namespace {
 
 // ---------------- residues ----------------
-constexpr int RTX = 32, RTY = 8;
+constexpr int RTX = 32, RTY = 32, RTT = 8;  // node tile RTY x RTX, thread block RTX x RTT
 
-// One RTY x RTX tile of nodes, tile (by, bx).
+// One RTY x RTX tile of nodes, tile (by, bx); each thread takes RTY / RTT rows.
+// The pixel tile (+1 row and column) is loaded with every load of a thread
+// issued before the first store, and the block adds its charge sum to r_G once.
 __device__ __forceinline__ void residues_tile(const void* __restrict__ ifg, int is_complex,
                                               const float* __restrict__ coh, const uint8_t* __restrict__ mask,
                                               int64_t m, int64_t n, int8_t* __restrict__ res,
@@ -27,39 +29,51 @@ __device__ __forceinline__ void residues_tile(const void* __restrict__ ifg, int 
   __shared__ float sp[RTY + 1][RTX + 1];
   const int64_t i0 = by * RTY, j0 = bx * RTX;
   const int tid = threadIdx.y * RTX + threadIdx.x;
-  for (int q = tid; q < (RTY + 1) * (RTX + 1); q += RTX * RTY) {
-    int r = q / (RTX + 1), c = q % (RTX + 1);
-    int64_t i = i0 + r, j = j0 + c;
-    float v = 0.0f;
-    if (i < m && j < n) v = load_pixel(ifg, is_complex, coh, mask, i * n + j).psi;
-    sp[r][c] = v;
+  {
+    constexpr int kQ = (RTY + 1) * (RTX + 1), kU = (kQ + RTX * RTT - 1) / (RTX * RTT);
+    float v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = tid + u * RTX * RTT;
+      const int64_t i = i0 + q / (RTX + 1), j = j0 + q % (RTX + 1);
+      v[u] = (q < kQ && i < m && j < n) ? load_pixel(ifg, is_complex, coh, mask, i * n + j).psi : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = tid + u * RTX * RTT;
+      if (q < kQ) sp[q / (RTX + 1)][q % (RTX + 1)] = v[u];
+    }
   }
   __syncthreads();
-  const int ty = threadIdx.y, tx = threadIdx.x;
-  const int64_t i = i0 + ty, j = j0 + tx;
-  int r = 0;
-  if (i < m - 1 && j < n - 1) {
-    int n_top = wrap_count(__fsub_rn(sp[ty][tx + 1], sp[ty][tx]));
-    int n_right = wrap_count(__fsub_rn(sp[ty + 1][tx + 1], sp[ty][tx + 1]));
-    int n_bottom = wrap_count(__fsub_rn(sp[ty + 1][tx + 1], sp[ty + 1][tx]));
-    int n_left = wrap_count(__fsub_rn(sp[ty + 1][tx], sp[ty][tx]));
-    r = -(n_top + n_right - n_bottom - n_left);
-    res[i * (n - 1) + j] = (int8_t)r;
+  const int tx = threadIdx.x;
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < RTY / RTT; ++k) {
+    const int ty = threadIdx.y + k * RTT;
+    const int64_t i = i0 + ty, j = j0 + tx;
+    if (i < m - 1 && j < n - 1) {
+      int n_top = wrap_count(__fsub_rn(sp[ty][tx + 1], sp[ty][tx]));
+      int n_right = wrap_count(__fsub_rn(sp[ty + 1][tx + 1], sp[ty][tx + 1]));
+      int n_bottom = wrap_count(__fsub_rn(sp[ty + 1][tx + 1], sp[ty + 1][tx]));
+      int n_left = wrap_count(__fsub_rn(sp[ty + 1][tx], sp[ty][tx]));
+      const int r = -(n_top + n_right - n_bottom - n_left);
+      res[i * (n - 1) + j] = (int8_t)r;
+      s += r;
+    }
   }
   // block sum of charges -> ground gets minus the total
-  int s = r;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ int ws[RTY];
-  if (tx == 0) ws[ty] = s;
+  __shared__ int ws[RTT];
+  if (tx == 0) ws[threadIdx.y] = s;
   __syncthreads();
   if (tid == 0) {
     int t = 0;
-    for (int k = 0; k < RTY; ++k) t += ws[k];
+    for (int k = 0; k < RTT; ++k) t += ws[k];
     if (t) atomicAdd(ground, -t);
   }
 }
 
-__global__ void __launch_bounds__(RTX* RTY) k_residues(const void* __restrict__ ifg, int is_complex,
+__global__ void __launch_bounds__(RTX* RTT) k_residues(const void* __restrict__ ifg, int is_complex,
                                                         const float* __restrict__ coh,
                                                         const uint8_t* __restrict__ mask, int64_t m,
                                                         int64_t n, int8_t* __restrict__ res,
@@ -106,15 +120,27 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   __shared__ uint8_t nh[CEY][CTX], nv[CEY][CTX];      // row partial counts
   const int64_t i0 = by * CTY, j0 = bx * CTX;
   const int tid = threadIdx.x;
-  // 1. prepared pixels, tile origin (i0 - CW, j0 - CW)
-  for (int q = tid; q < CPY * CPX; q += 256) {
-    int r = q / CPX, c = q % CPX;
-    int64_t i = i0 - CW + r, j = j0 - CW + c;
-    Pix p{0.0f, 0.0f, false};
-    if (i >= 0 && i < m && j >= 0 && j < n) p = load_pixel(ifg, is_complex, coh, mask, i * n + j);
-    sp[r][c] = p.psi;
-    sc[r][c] = p.coh;
-    sv[r][c] = p.valid ? 1 : 0;
+  // 1. prepared pixels, tile origin (i0 - CW, j0 - CW); every load of a thread
+  // is issued before its first store
+  {
+    constexpr int kU = (CPY * CPX + 255) / 256;
+    Pix px[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = tid + 256 * u;
+      const int64_t i = i0 - CW + q / CPX, j = j0 - CW + q % CPX;
+      px[u] = Pix{0.0f, 0.0f, false};
+      if (q < CPY * CPX && i >= 0 && i < m && j >= 0 && j < n) px[u] = load_pixel(ifg, is_complex, coh, mask, i * n + j);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = tid + 256 * u;
+      if (q >= CPY * CPX) continue;
+      const int r = q / CPX, c = q % CPX;
+      sp[r][c] = px[u].psi;
+      sc[r][c] = px[u].coh;
+      sv[r][c] = px[u].valid ? 1 : 0;
+    }
   }
   __syncthreads();
   // 2. fixed-point wrapped gradients of every edge in the extended tile
@@ -633,7 +659,7 @@ __global__ void k_phase_b(const GridItem* __restrict__ items, int count) {
   }
 }
 
-__global__ void __launch_bounds__(RTX* RTY) k_residues_b(const GridItem* __restrict__ items, int count) {
+__global__ void __launch_bounds__(RTX* RTT) k_residues_b(const GridItem* __restrict__ items, int count) {
   const int64_t b = blockIdx.x;
   const GridItem& it = items[item_of_block<kBlkRes>(items, count, b)];
   const int64_t local = b - it.blk[kBlkRes];
@@ -919,7 +945,7 @@ ww_status launch_residues(const void* ifg, int is_complex, const float* coh, con
                           int64_t m, int64_t n, int8_t* res, int32_t* ground, cudaStream_t s) {
   WW_CUDA_TRY(cudaMemsetAsync(ground, 0, sizeof(int32_t), s));
   dim3 grid((unsigned)((n - 1 + RTX - 1) / RTX), (unsigned)((m - 1 + RTY - 1) / RTY));
-  k_residues<<<grid, dim3(RTX, RTY), 0, s>>>(ifg, is_complex, coh, mask, m, n, res, ground);
+  k_residues<<<grid, dim3(RTX, RTT), 0, s>>>(ifg, is_complex, coh, mask, m, n, res, ground);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
 }
@@ -1068,7 +1094,7 @@ ww_status launch_pre_batch(GridBatch* gb, int count, const ww_params* p, cudaStr
   // phase of the complex items once (their ifg is the float buffer it lands in)
   if (off[kBlkPhase] > 0) k_phase_b<<<(unsigned)off[kBlkPhase], 256, 0, s>>>(gb->d_items, count);
   k_prep_b<<<pb, 256, 0, s>>>(gb->d_items, count);
-  k_residues_b<<<(unsigned)off[kBlkRes], dim3(RTX, RTY), 0, s>>>(gb->d_items, count);
+  k_residues_b<<<(unsigned)off[kBlkRes], dim3(RTX, RTT), 0, s>>>(gb->d_items, count);
   k_costs_b<<<(unsigned)off[kBlkCost], 256, 0, s>>>(gb->d_items, count, p->box_half_width, p->steep_rad);
   k_steep_plan_b<<<pb, 256, 0, s>>>(gb->d_items, count, p->steep_cap_ppm);
   // items within their cap

@@ -168,16 +168,6 @@ __device__ __forceinline__ bool arc_cost(const ProbDev& p, int64_t i, int64_t j,
   return true;
 }
 
-// Local neighbour index inside a problem, -1 for the ground node.
-__device__ __forceinline__ int64_t nb_local(const ProbDev& p, int64_t i, int64_t j, int dir) {
-  switch (dir) {
-    case kDirUp: return i > 0 ? (i - 1) * p.C + j : -1;
-    case kDirDown: return i + 1 < p.R ? (i + 1) * p.C + j : -1;
-    case kDirLeft: return j > 0 ? i * p.C + j - 1 : -1;
-    default: return j + 1 < p.C ? i * p.C + j + 1 : -1;
-  }
-}
-
 // ---- tile worklist shared by all CTAs of one persistent search launch ----
 // Producers reserve ring positions with atomicAdd(tail) and then publish the
 // tile in that slot; consumers take tickets with atomicAdd(head) and wait for
@@ -753,15 +743,26 @@ __global__ void k_clear_capped(Batch b, int32_t* capped_flag, const McfCtr* ctr)
     capped_flag[t] = 0;
 }
 
+// One step from node (i, j) toward its parent in direction d; false when the
+// parent is the ground node (d points out of the grid).
+__device__ __forceinline__ bool step_parent(const ProbDev& p, int d, int64_t* i, int64_t* j) {
+  switch (d) {
+    case kDirUp: if (*i == 0) return false; --*i; return true;
+    case kDirDown: if (*i + 1 >= p.R) return false; ++*i; return true;
+    case kDirLeft: if (*j == 0) return false; --*j; return true;
+    default: if (*j + 1 >= p.C) return false; ++*j; return true;
+  }
+}
+
 // Walk from local node v along the forest to its tree root (local index), or
-// -1 after more steps than nodes (reported as an internal error).
+// -1 after more steps than nodes (reported as an internal error).  The walk
+// keeps the node's row and column, so a step costs one label load.
 __device__ __forceinline__ int64_t walk_root(const ProbDev& p, const uint64_t* plab, int64_t v) {
+  int64_t i = v / p.C, j = v - (v / p.C) * p.C;
   for (int64_t steps = 0; steps <= p.N; ++steps) {
-    int d = label_dir(plab[v]);
-    if (d == kDirRoot) return v;
-    int64_t u = nb_local(p, v / p.C, v % p.C, d);
-    if (u < 0) return v;  // parent is the ground node: v roots a subtree of it
-    v = u;
+    const int d = label_dir(plab[i * p.C + j]);
+    if (d == kDirRoot) return i * p.C + j;
+    if (!step_parent(p, d, &i, &j)) return i * p.C + j;  // parent is the ground: (i, j) roots a subtree of it
   }
   return -1;
 }
@@ -894,17 +895,15 @@ __device__ __forceinline__ void dir_edge(const ProbDev& p, int64_t i, int64_t j,
 template <bool FWD>
 __device__ __forceinline__ void flip_path(const ProbDev& p, const uint64_t* plab, int64_t v) {
   const int64_t P = p.m * p.n;
+  int64_t i = v / p.C, j = v - (v / p.C) * p.C;
   for (int64_t steps = 0; steps <= p.N; ++steps) {
-    int d = label_dir(plab[v]);
+    const int d = label_dir(plab[i * p.C + j]);
     if (d == kDirRoot) break;
-    int64_t i = v / p.C, j = v % p.C;
     int64_t e;
     int plane, s;
     dir_edge(p, i, j, d, &e, &plane, &s);
     p.flows[plane * P + e] += (int8_t)(FWD ? s : -s);
-    int64_t u = nb_local(p, i, j, d);
-    if (u < 0) break;
-    v = u;
+    if (!step_parent(p, d, &i, &j)) break;
   }
 }
 
