@@ -892,18 +892,23 @@ __device__ __forceinline__ void dir_edge(const ProbDev& p, int64_t i, int64_t j,
 
 // Flip dk along the path from local node v to its tree root (forward: the flow
 // runs root -> v; reverse: v -> root), stopping at the root or the ground.
+// The parent's label is loaded before the flow of the current edge is
+// updated, so that the two memory round trips of a step overlap.
 template <bool FWD>
 __device__ __forceinline__ void flip_path(const ProbDev& p, const uint64_t* plab, int64_t v) {
   const int64_t P = p.m * p.n;
   int64_t i = v / p.C, j = v - (v / p.C) * p.C;
+  uint64_t lab = plab[v];
   for (int64_t steps = 0; steps <= p.N; ++steps) {
-    const int d = label_dir(plab[i * p.C + j]);
+    const int d = label_dir(lab);
     if (d == kDirRoot) break;
     int64_t e;
     int plane, s;
     dir_edge(p, i, j, d, &e, &plane, &s);
+    const bool inside = step_parent(p, d, &i, &j);
+    if (inside) lab = plab[i * p.C + j];
     p.flows[plane * P + e] += (int8_t)(FWD ? s : -s);
-    if (!step_parent(p, d, &i, &j)) break;
+    if (!inside) break;
   }
 }
 

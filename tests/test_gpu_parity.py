@@ -270,3 +270,59 @@ def test_complex_phase_bit_exact_extremes(ws):
     assert v.all()
     want = (psi.astype(np.float64) + Kn.astype(np.float64) * 6.283185307179586).astype(np.float32)
     assert np.array_equal(u.view(np.uint32)[v], want.view(np.uint32)[v])
+
+
+def _tie_phase(K):
+    """A phase that puts fp64(psi + fp64(K 2pi)) exactly on a rounding boundary:
+    halfway between two fp32 values when such a psi is an fp32 number, else
+    halfway between two fp64 values (an odd multiple of half an fp64 ulp of K 2pi)."""
+    t = np.float64(K) * np.float64(2 * np.pi)
+    g = np.float32(t)
+    for q in range(-2, 3):
+        lo = g
+        for _ in range(abs(q)):
+            lo = np.nextafter(lo, np.float32(np.inf) if q > 0 else np.float32(-np.inf))
+        mid = (np.float64(lo) + np.float64(np.nextafter(lo, np.float32(np.inf)))) / 2
+        d = mid - t
+        if np.float64(np.float32(d)) == d and abs(d) < 1e-3:
+            return np.float32(d)
+    e = np.frexp(t)[1]
+    return np.float32((2 * (abs(K) % 7) + 1) * np.ldexp(1.0, int(e) - 54))
+
+
+def test_integrate_rounding_bit_exact():
+    """Integration output fp32(fp64(psi) + fp64(K) 2pi) bit for bit on inputs
+    built to stress its two roundings: exact ties of both roundings with |K| up
+    to ~10^4 (either side of the integer path's |K| < 2^11 bound), wrapped
+    phases, phases beyond +-4 and arbitrary fp32 values; K follows the row
+    recurrence K(j+1) - K(j) = dk_h(j) - wrap(psi(j+1) - psi(j))."""
+    rng = np.random.default_rng(77)
+    m, n = 64, 4096
+    flows = np.zeros((2, m, n), np.int8)
+    psi = np.zeros((m, n), np.float32)
+    for i in range(0, 16):  # ties: tiny phases, so every wrap count is 0 and K is the flow sum
+        f = rng.integers(-127, 128, size=n).astype(np.int8)
+        f[-1] = 0
+        flows[0, i] = f
+        K = np.concatenate([[0], np.cumsum(f[:-1].astype(np.int64))])
+        psi[i, 1:] = [_tie_phase(int(k)) for k in K[1:]]
+    psi[16:32, 1:] = rng.uniform(-np.pi, np.pi, size=(16, n - 1)).astype(np.float32)
+    flows[0, 16:32] = rng.integers(-1, 2, size=(16, n))
+    big = rng.uniform(4.0, 1e4, size=(16, n - 1)) * rng.choice([-1.0, 1.0], size=(16, n - 1))
+    psi[32:48, 1:] = big.astype(np.float32)
+    flows[0, 32:48] = rng.integers(-100, 101, size=(16, n))
+    bits = rng.integers(0, 2**32, size=(16, n - 1), dtype=np.uint64).astype(np.uint32)
+    bits[(bits & 0x7F800000) == 0x7F800000] &= 0xBF7FFFFF
+    psi[48:64, 1:] = bits.view(np.float32)
+    flows[0, 48:64] = rng.integers(-3, 4, size=(16, n))
+    unw, cyc = ww.integrate(to_dev(psi), to_dev(flows))
+    u, K = unw.cpu().numpy(), cyc.cpu().numpy().astype(np.int64)
+    assert (K[:, 0] == 0).all()
+    with np.errstate(over="ignore"):
+        d = psi[:, 1:] - psi[:, :-1]  # fp32 differences (+-inf where they overflow, as on the device)
+    pi32 = np.float32(np.pi)
+    wrap = (d > pi32).astype(np.int64) - (d <= -pi32).astype(np.int64)
+    assert np.array_equal(K[:, 1:] - K[:, :-1], flows[0, :, :-1].astype(np.int64) - wrap)
+    assert np.abs(K[:16]).max() >= 2048  # both sides of the integer path's bound
+    want = (psi.astype(np.float64) + K.astype(np.float64) * 6.283185307179586).astype(np.float32)
+    assert np.array_equal(u.view(np.uint32), want.view(np.uint32))
