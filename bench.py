@@ -43,6 +43,25 @@ WORKLOADS = {
 SEARCH_BYTES_PER_NODE = 34
 SEARCH_TILE_NODES = 32 * 32
 
+# DRAM bytes (read + write) of every k_search launch of one unwrap of the
+# 74-Mpixel earthquake scene, from one ncu capture of the same bench command
+# (profiles/k_search_dram_earthquake_8192x9000.md), and the SHA-256 of the
+# solver source it was taken on: the figure is reported only while that source
+# is unchanged.
+SEARCH_DRAM_BYTES_PER_UNWRAP = 2_279_595_691
+SEARCH_DRAM_SOURCE_SHA256 = "a1fa3180c4111b3319e2472682f2b1a2c86817d62015a26e011d29bd7104418a"
+
+
+def search_traffic_per_launch(workload: str, launches: int):
+    if workload != "earthquake" or SEARCH_DRAM_BYTES_PER_UNWRAP is None:
+        return None
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2609_36267_b300", "csrc", "ww_mcf.cu"), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != SEARCH_DRAM_SOURCE_SHA256:
+            return None
+    return SEARCH_DRAM_BYTES_PER_UNWRAP / max(1, launches)
+
 
 def make_input(workload: str):
     from paper_2609_36267_b300 import synth
@@ -314,7 +333,7 @@ def run_ours(args, rank, world, local):
     roof = {"kernel": "k_search (tiled label-correcting shortest-path search)", "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-            "traffic": None, "bytes_per_launch": search_bytes / launches,
+            "traffic": search_traffic_per_launch(args.workload, launches), "bytes_per_launch": search_bytes / launches,
             "ms_per_launch": st["ms_search_gpu"] / launches, "launches_per_step": launches}
     if rank == 0:
         base = cpu_baseline(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
