@@ -12,6 +12,8 @@ Pinned functions and their pins (see tests/test_oracle_*.py):
   costs/indices   hand-evaluated index formula, probe tables, masks, steep rule
   MCF             exhaustive enumeration (<= 5x5), certificate, max-flow
   integration     rewrap identity, Itoh integration on sub-Nyquist fields
+  components      scipy.ndimage.label (every edge reliable), networkx
+                  components, the reliability rule case by case
   Lee pdf         mpmath hypergeometric closed form, single-look closed form,
                   normalisation, Monte Carlo looks
   Touzi pdf       mpmath hypergeometric, gamma=0 closed form, normalisation,
@@ -246,3 +248,43 @@ def lut_build(L, nh=8192, lambda_panels=8):
     st = lib().wwo_lut_build(float(L), nh, lambda_panels, _p(c), _p(t))
     assert st == 0
     return c, t
+
+
+def components(costs_planes, flows, valid, threshold: int):
+    """Connected-component labels (Sec. II-D), plain breadth-first search.
+
+    A pixel edge is reliable when both of its pixels are valid and moving its
+    ambiguity difference dk by +1 or by -1 would raise the MCF objective by more
+    than `threshold` (>= 0).  With the unit-capacity costs of Sec. II-B that
+    change is +c+ / +c- for an edge without flow, and -c+ or -c- (removing the
+    flow) for an edge that carries flow, so: reliable <=> dk = 0 and
+    min(c+, c-) > threshold.  Planes: h edge (i,j)-(i,j+1) has dk = flows[0],
+    c+ = costs[0], c- = costs[1]; v edge (i,j)-(i+1,j) has dk = flows[1],
+    c+ = costs[2], c- = costs[3].  Labels grow over reliable edges; a pixel's
+    label is 1 + the smallest row-major index in its component, 0 where invalid.
+    """
+    from collections import deque
+
+    c = np.asarray(costs_planes, np.int64)
+    fl = np.asarray(flows, np.int64)
+    ok = np.asarray(valid, bool)
+    m, n = ok.shape
+    rel_h = np.zeros((m, n), bool)
+    rel_v = np.zeros((m, n), bool)
+    rel_h[:, :-1] = ok[:, :-1] & ok[:, 1:] & (fl[0, :, :-1] == 0) & (np.minimum(c[0, :, :-1], c[1, :, :-1]) > threshold)
+    rel_v[:-1, :] = ok[:-1, :] & ok[1:, :] & (fl[1, :-1, :] == 0) & (np.minimum(c[2, :-1, :], c[3, :-1, :]) > threshold)
+    labels = np.zeros((m, n), np.int64)
+    for s in range(m * n):  # row-major: the first pixel reached is its component's smallest index
+        i0, j0 = divmod(s, n)
+        if not ok[i0, j0] or labels[i0, j0]:
+            continue
+        labels[i0, j0] = s + 1
+        q = deque([(i0, j0)])
+        while q:
+            i, j = q.popleft()
+            for a, b, edge in ((i, j + 1, j + 1 < n and rel_h[i, j]), (i, j - 1, j > 0 and rel_h[i, j - 1]),
+                               (i + 1, j, i + 1 < m and rel_v[i, j]), (i - 1, j, i > 0 and rel_v[i - 1, j])):
+                if edge and not labels[a, b]:
+                    labels[a, b] = s + 1
+                    q.append((a, b))
+    return labels.astype(np.int32)
