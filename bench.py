@@ -355,7 +355,46 @@ def run_ours(args, rank, world, local):
                                                  "visit_cycles", "load_cycles", "relax_cycles")},
                 "total_costs_seen": sorted(costs_seen)}
         line["gpu_launches"] = launch_count(st, args.steps)
+        line["components"] = measure_components(ww, torch, x, ifg, coh, mask, unw, ws, max(3, args.steps), peak,
+                                                peak_kind)
         print(json.dumps(line), flush=True)
+
+
+# Connected-component labels (ww_components) of the headline scene, timed on
+# their own after the unwrap: algorithmic bytes per pixel = the cost planes (8),
+# flows (2) and unwrapped phase (4) read once and the labels (4) written once.
+COMPONENTS_BYTES_PER_PIXEL = 18
+COMPONENTS_THRESHOLD = 100
+
+
+def measure_components(ww, torch, x, ifg, coh, mask, unw, ws, steps, peak, peak_kind):
+    lut = ww.Lut.build(x.nlooks)
+    r, g = ww.residues(ifg, coh, mask)
+    c = ww.costs(ifg, coh, lut, ws, mask)
+    fl, _, _, status = ww.solve_mcf(r, g, c, ws)
+    assert status == 0, ww.status_string(status)
+    labels = torch.empty(unw.shape, dtype=torch.int32, device=unw.device)
+    ww.components(c, fl, unw, COMPONENTS_THRESHOLD, out=labels)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        ww.components(c, fl, unw, COMPONENTS_THRESHOLD, out=labels)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    px = labels.numel()
+    flat = labels.view(-1)
+    n_comp = int((flat == torch.arange(1, px + 1, device=flat.device, dtype=torch.int32)).sum())  # roots
+    pos = flat[flat > 0]
+    achieved = px * COMPONENTS_BYTES_PER_PIXEL / (ms * 1e-3) / 1e9
+    return {"threshold": COMPONENTS_THRESHOLD, "ms": ms, "Mpixel_per_s": px / (ms * 1e-3) / 1e6,
+            "components": n_comp, "largest_fraction": float(torch.bincount(pos).max().item() / max(1, pos.numel())),
+            "launches_per_call": 4,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_pixel": COMPONENTS_BYTES_PER_PIXEL, "traffic": None,
+                         "peak_source": peak_kind}}
 
 
 def _dev(x, torch):

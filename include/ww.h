@@ -211,6 +211,26 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
                     ww_workspace* ws, float* unwrapped, int32_t* cycles, int64_t* total_cost,
                     ww_stream stream);
 
+/* ---- Connected-component labels (Sec. II-D) ----
+ * After unwrapping, a pixel edge is reliable when both of its pixels are
+ * valid and moving its ambiguity difference dk by +1 or by -1 would raise the
+ * MCF objective by more than `threshold` (cost units of the int16 planes).
+ * With unit capacities that is: dk = 0 on the edge and min(c+, c-) >
+ * threshold (an edge that carries flow can drop it at a negative change).
+ * Labels grow over reliable edges (4-neighbour components).
+ *   costs: DEVICE int16 [4][m][n] as written by ww_costs; flows: DEVICE int8
+ *   [2][m][n] as written by ww_solve_mcf (plane 0: dk of the edge
+ *   (i,j)-(i,j+1) with costs planes 0/1 for +1/-1; plane 1: dk of
+ *   (i,j)-(i+1,j) with planes 2/3); unwrapped: DEVICE float32 [m][n], NaN
+ *   where invalid (as written by ww_integrate / ww_unwrap).
+ *   labels: DEVICE int32 [m][n], caller-owned: 1 + the smallest row-major
+ *   index of the pixel's component, 0 where invalid; unique whatever the
+ *   schedule.  Also the union-find scratch: nothing is allocated.
+ * Needs 1 <= m, n and m*n < 2^31, threshold >= 0 (else WW_ERR_INVALID_ARG).
+ * Asynchronous on the stream; every device loop is bounded by the pixel count. */
+ww_status ww_components(const int16_t* costs, const int8_t* flows, const float* unwrapped, int64_t m,
+                        int64_t n, int32_t threshold, int32_t* labels, ww_stream stream);
+
 /* ---- Batched form: many uneven interferograms in one solve ----
  * Each item is one unwrap request (device pointers; outputs unwrapped/cycles are
  * m x n).  All items are solved together: their node grids are independent

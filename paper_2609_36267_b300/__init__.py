@@ -116,6 +116,7 @@ def lib():
         L.ww_unwrap.argtypes = [P, i32, P, d, P, i64, i64, ctypes.POINTER(Params), P, P, P,
                                 ctypes.POINTER(i64), P]
         L.ww_certificate.argtypes = [P, P, P, P, P, i64, i64, P, P]
+        L.ww_components.argtypes = [P, P, P, i64, i64, i32, P, P]
         L.ww_batch_create.argtypes = [i64, i64, i64, ctypes.POINTER(P)]
         L.ww_batch_free.argtypes = [P]
         L.ww_batch_bytes.argtypes = [i64, i64, i64]
@@ -135,7 +136,7 @@ def lib():
         L.ww_server_destroy.argtypes = [P]
         for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
                   "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_get_solve_stats", "ww_integrate", "ww_unwrap",
-                  "ww_certificate", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_autotune_batch",
+                  "ww_certificate", "ww_components", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_autotune_batch",
                   "ww_server_create",
                   "ww_server_submit", "ww_server_poll", "ww_server_wait", "ww_server_release", "ww_server_get_stats"):
             getattr(L, f).restype = i32
@@ -331,6 +332,17 @@ def integrate(ifg, flows, coh=None, mask=None):
     _check(lib().ww_integrate(p, c, _ptr(coh), _ptr(mask), _ptr(flows), m, n, _ptr(unw), _ptr(cyc), _stream()),
            "ww_integrate")
     return unw, cyc
+
+
+def components(cost_planes, flows, unwrapped, threshold: int = 0, out=None):
+    """Connected-component labels (ww_components) -> int32 [m, n] on the device:
+    1 + the smallest row-major index of each pixel's component, 0 where invalid."""
+    torch = _torch()
+    _, m, n = cost_planes.shape
+    labels = out if out is not None else torch.empty((m, n), dtype=torch.int32, device=cost_planes.device)
+    _check(lib().ww_components(_ptr(cost_planes), _ptr(flows), _ptr(unwrapped), m, n, int(threshold), _ptr(labels),
+                               _stream()), "ww_components")
+    return labels
 
 
 def unwrap(ifg, coh, nlooks: float, mask=None, ws: Workspace | None = None, params: Params | None = None,

@@ -293,6 +293,14 @@ ww_status ww_integrate(const void* ifg, int32_t is_complex, const float* coh, co
                               (cudaStream_t)stream);
 }
 
+ww_status ww_components(const int16_t* costs, const int8_t* flows, const float* unwrapped, int64_t m, int64_t n,
+                        int32_t threshold, int32_t* labels, ww_stream stream) {
+  if (!costs || !flows || !unwrapped || !labels || m < 1 || n < 1 || m > (1ll << 30) || n > (1ll << 30) ||
+      m * n >= (1ll << 31) || threshold < 0)
+    return WW_ERR_INVALID_ARG;
+  return ww::launch_components(costs, flows, unwrapped, m, n, threshold, labels, (cudaStream_t)stream);
+}
+
 ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, double nlooks, const uint8_t* mask,
                     int64_t m, int64_t n, const ww_params* params, ww_workspace* ws, float* unwrapped,
                     int32_t* cycles, int64_t* total_cost, ww_stream stream) {

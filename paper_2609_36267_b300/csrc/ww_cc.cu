@@ -1,0 +1,129 @@
+// Connected-component labels of an unwrapped field (Sec. II-D): a pixel edge is
+// reliable when both of its pixels are valid and moving its ambiguity
+// difference by +1 or -1 would raise the MCF objective by more than a
+// threshold; components grow over reliable edges.
+//
+// Lock-free union-find on the label array itself (int32 parent pointers):
+//   1. every valid pixel is its own root, an invalid one is -1;
+//   2. one thread per pixel unites it with its right and lower neighbour over
+//      reliable edges: the larger of the two roots is hooked under the smaller
+//      by compare-and-swap (a root's pointer changes only from itself), and
+//      finds halve their paths with plain stores of an ancestor;
+//   3. every pixel's pointer is set to its root by read-only finds;
+//   4. labels = root + 1 (0 where invalid), element by element.
+// Pointers only ever point to smaller indices, so every chain ends at a root
+// within as many steps as its start index and each component's root is its
+// smallest row-major index: the labels are unique, whatever the schedule.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "ww_internal.cuh"
+
+namespace ww {
+namespace {
+
+__device__ __forceinline__ int32_t ld_parent(const int32_t* parent, int32_t x) {
+  return *((volatile const int32_t*)(parent + x));
+}
+
+// Root of x with path halving (each visited node skips to its grandparent).
+__device__ __forceinline__ int32_t find_halving(int32_t* parent, int32_t x) {
+  for (int32_t s = 0, lim = x; s <= lim; ++s) {
+    const int32_t p = ld_parent(parent, x);
+    if (p == x) return x;
+    const int32_t gp = ld_parent(parent, p);
+    if (gp != p) parent[x] = gp;
+    x = gp;
+  }
+  return x;  // not reached: the chain from x has at most x steps
+}
+
+__device__ __forceinline__ int32_t find_readonly(const int32_t* parent, int32_t x) {
+  for (int32_t s = 0, lim = x; s <= lim; ++s) {
+    const int32_t p = ld_parent(parent, x);
+    if (p == x) return x;
+    x = p;
+  }
+  return x;
+}
+
+__device__ __forceinline__ void unite(int32_t* parent, int32_t a, int32_t b) {
+  // every failed swap means b's root was hooked under a smaller index, so the
+  // loop runs at most b + 1 times
+  for (int32_t s = 0, lim = b; s <= lim; ++s) {
+    a = find_halving(parent, a);
+    b = find_halving(parent, b);
+    if (a == b) return;
+    if (a > b) {
+      const int32_t t = a;
+      a = b;
+      b = t;
+    }
+    if (atomicCAS(parent + b, b, a) == b) return;
+  }
+}
+
+// Reliable: both pixels valid, no flow on the edge, min(c+, c-) > threshold.
+__device__ __forceinline__ bool reliable(int8_t dk, int16_t cp, int16_t cm, int32_t threshold) {
+  return dk == 0 && min((int32_t)cp, (int32_t)cm) > threshold;
+}
+
+__global__ void k_cc_init(const float* __restrict__ unw, int64_t P, int32_t* __restrict__ parent) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
+    parent[k] = isnan(__ldg(unw + k)) ? -1 : (int32_t)k;
+}
+
+__global__ void k_cc_union(const int16_t* __restrict__ costs, const int8_t* __restrict__ flows,
+                           const float* __restrict__ unw, int64_t m, int64_t n, int32_t threshold,
+                           int32_t* parent) {
+  const int64_t P = m * n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    if (isnan(__ldg(unw + k))) continue;
+    const int64_t i = k / n, j = k - (k / n) * n;
+    // h edge (i,j)-(i,j+1): dk = flows[0], c+ = costs[0], c- = costs[1]
+    if (j + 1 < n && !isnan(__ldg(unw + k + 1)) &&
+        reliable(__ldg(flows + k), __ldg(costs + k), __ldg(costs + P + k), threshold))
+      unite(parent, (int32_t)k, (int32_t)(k + 1));
+    // v edge (i,j)-(i+1,j): dk = flows[1], c+ = costs[2], c- = costs[3]
+    if (i + 1 < m && !isnan(__ldg(unw + k + n)) &&
+        reliable(__ldg(flows + P + k), __ldg(costs + 2 * P + k), __ldg(costs + 3 * P + k), threshold))
+      unite(parent, (int32_t)k, (int32_t)(k + n));
+  }
+}
+
+// Every pointer to its root: reads follow chains, each thread writes only its
+// own pixel (an ancestor either way for the other threads' chains).
+__global__ void k_cc_compress(int64_t P, int32_t* parent) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = ld_parent(parent, (int32_t)k);
+    if (p < 0 || p == (int32_t)k) continue;
+    parent[k] = find_readonly(parent, p);
+  }
+}
+
+__global__ void k_cc_labels(int64_t P, int32_t* labels) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
+    labels[k] = labels[k] + 1;  // root index + 1; -1 (invalid) becomes 0
+}
+
+}  // namespace
+
+ww_status launch_components(const int16_t* costs, const int8_t* flows, const float* unwrapped, int64_t m, int64_t n,
+                            int32_t threshold, int32_t* labels, cudaStream_t s) {
+  const int64_t P = m * n;
+  if (P == 0) return WW_OK;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = (int)std::min<int64_t>((P + 255) / 256, (int64_t)sms * 16);
+  k_cc_init<<<blocks, 256, 0, s>>>(unwrapped, P, labels);
+  k_cc_union<<<blocks, 256, 0, s>>>(costs, flows, unwrapped, m, n, threshold, labels);
+  k_cc_compress<<<blocks, 256, 0, s>>>(P, labels);
+  k_cc_labels<<<blocks, 256, 0, s>>>(P, labels);
+  WW_CUDA_TRY(cudaGetLastError());
+  return WW_OK;
+}
+
+}  // namespace ww

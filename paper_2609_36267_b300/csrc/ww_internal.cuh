@@ -252,6 +252,9 @@ ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, co
                            cudaStream_t s);
 // psi[k] = CORDIC phase of a complex64 image (NaN where a sample is not finite)
 ww_status launch_phase(const void* ifg, int64_t m, int64_t n, float* psi, cudaStream_t s);
+// Connected-component labels over reliable edges (ww_cc.cu).
+ww_status launch_components(const int16_t* costs, const int8_t* flows, const float* unwrapped, int64_t m, int64_t n,
+                            int32_t threshold, int32_t* labels, cudaStream_t s);
 // candidate-list entries needed for an image of `pixels` pixels at cap_ppm (cap + 2)
 int64_t steep_list_capacity(int64_t pixels, int32_t cap_ppm);
 // Batched launches of the grid steps (ww_grid.cu): one launch per step covers
