@@ -3,10 +3,12 @@
 // difference by +1 or -1 would raise the MCF objective by more than a
 // threshold; components grow over reliable edges.
 //
-// Lock-free union-find on the label array itself (int32 parent pointers):
-//   1. every valid pixel is its own root, an invalid one is -1;
-//   2. one thread per pixel unites it with its right and lower neighbour over
-//      reliable edges: the larger of the two roots is hooked under the smaller
+// Union-find on the label array itself (int32 parent pointers):
+//   1. rows: one warp per row links each valid pixel to the start of its run
+//      of reliable horizontal edges (ballot per 32 pixels, the run carried
+//      across segments); a run start is its own root, an invalid pixel -1;
+//   2. one thread per pixel unites it with its lower neighbour over a reliable
+//      vertical edge: the larger of the two roots is hooked under the smaller
 //      by compare-and-swap (a root's pointer changes only from itself), and
 //      finds halve their paths with plain stores of an ancestor;
 //   3. every pixel's pointer is set to its root by read-only finds;
@@ -70,24 +72,39 @@ __device__ __forceinline__ bool reliable(int8_t dk, int16_t cp, int16_t cm, int3
   return dk == 0 && min((int32_t)cp, (int32_t)cm) > threshold;
 }
 
-__global__ void k_cc_init(const float* __restrict__ unw, int64_t P, int32_t* __restrict__ parent) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
-    parent[k] = isnan(__ldg(unw + k)) ? -1 : (int32_t)k;
+// Phase 1: one warp per row, 32 pixels per step.
+__global__ void k_cc_rows(const int16_t* __restrict__ costs, const int8_t* __restrict__ flows,
+                          const float* __restrict__ unw, int64_t m, int64_t n, int32_t threshold,
+                          int32_t* __restrict__ parent) {
+  const int64_t P = m * n;
+  const unsigned lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += warps) {
+    int32_t carry = -1;  // root of the previous segment's last pixel
+    for (int64_t j0 = 0; j0 < n; j0 += 32) {
+      const int64_t j = j0 + lane, k = i * n + j;
+      const bool valid = j < n && !isnan(__ldg(unw + k));
+      // h edge (i,j-1)-(i,j): dk = flows[0], c+ = costs[0], c- = costs[1] at (i,j-1)
+      const bool link = valid && j > 0 && !isnan(__ldg(unw + k - 1)) &&
+                        reliable(__ldg(flows + k - 1), __ldg(costs + k - 1), __ldg(costs + P + k - 1), threshold);
+      const unsigned starts = __ballot_sync(0xffffffffu, valid && !link);
+      const unsigned upto = starts & (0xffffffffu >> (31 - lane));
+      // a linked pixel with no start at or below its lane continues the previous segment's run
+      const int32_t root = upto ? (int32_t)(i * n + j0 + (31 - __clz(upto))) : carry;
+      if (j < n) parent[k] = valid ? root : -1;
+      carry = __shfl_sync(0xffffffffu, root, 31);
+    }
+  }
 }
 
-__global__ void k_cc_union(const int16_t* __restrict__ costs, const int8_t* __restrict__ flows,
-                           const float* __restrict__ unw, int64_t m, int64_t n, int32_t threshold,
-                           int32_t* parent) {
+// Phase 2: vertical edges, one thread per pixel.
+__global__ void k_cc_cols(const int16_t* __restrict__ costs, const int8_t* __restrict__ flows,
+                          const float* __restrict__ unw, int64_t m, int64_t n, int32_t threshold,
+                          int32_t* parent) {
   const int64_t P = m * n;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-    if (isnan(__ldg(unw + k))) continue;
-    const int64_t i = k / n, j = k - (k / n) * n;
-    // h edge (i,j)-(i,j+1): dk = flows[0], c+ = costs[0], c- = costs[1]
-    if (j + 1 < n && !isnan(__ldg(unw + k + 1)) &&
-        reliable(__ldg(flows + k), __ldg(costs + k), __ldg(costs + P + k), threshold))
-      unite(parent, (int32_t)k, (int32_t)(k + 1));
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P - n; k += (int64_t)gridDim.x * blockDim.x) {
     // v edge (i,j)-(i+1,j): dk = flows[1], c+ = costs[2], c- = costs[3]
-    if (i + 1 < m && !isnan(__ldg(unw + k + n)) &&
+    if (!isnan(__ldg(unw + k)) && !isnan(__ldg(unw + k + n)) &&
         reliable(__ldg(flows + P + k), __ldg(costs + 2 * P + k), __ldg(costs + 3 * P + k), threshold))
       unite(parent, (int32_t)k, (int32_t)(k + n));
   }
@@ -118,8 +135,9 @@ ww_status launch_components(const int16_t* costs, const int8_t* flows, const flo
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = (int)std::min<int64_t>((P + 255) / 256, (int64_t)sms * 16);
-  k_cc_init<<<blocks, 256, 0, s>>>(unwrapped, P, labels);
-  k_cc_union<<<blocks, 256, 0, s>>>(costs, flows, unwrapped, m, n, threshold, labels);
+  const int row_blocks = (int)std::min<int64_t>((m + 7) / 8, (int64_t)sms * 16);
+  k_cc_rows<<<row_blocks, 256, 0, s>>>(costs, flows, unwrapped, m, n, threshold, labels);
+  if (m > 1) k_cc_cols<<<blocks, 256, 0, s>>>(costs, flows, unwrapped, m, n, threshold, labels);
   k_cc_compress<<<blocks, 256, 0, s>>>(P, labels);
   k_cc_labels<<<blocks, 256, 0, s>>>(P, labels);
   WW_CUDA_TRY(cudaGetLastError());
