@@ -14,6 +14,9 @@ Pinned functions and their pins (see tests/test_oracle_*.py):
   integration     rewrap identity, Itoh integration on sub-Nyquist fields
   components      scipy.ndimage.label (every edge reliable), networkx
                   components, the reliability rule case by case
+  bridge          a smooth field cut into regions with whole-cycle offsets is
+                  restored up to the largest region's cycles; offset
+                  invariance; nearest-region attachment; region-only medians
   Lee pdf         mpmath hypergeometric closed form, single-look closed form,
                   normalisation, Monte Carlo looks
   Touzi pdf       mpmath hypergeometric, gamma=0 closed form, normalisation,
@@ -288,3 +291,56 @@ def components(costs_planes, flows, valid, threshold: int):
                     labels[a, b] = s + 1
                     q.append((a, b))
     return labels.astype(np.int32)
+
+
+def bridge(unwrapped, valid, window: int = 65):
+    """Bridging of mask-separated regions (Sec. II-D), plainly.
+
+    Regions are the 4-connected components of the valid pixels.  Taken in order
+    of decreasing size (ties: smaller first pixel first), every region after the
+    first is attached to the nearest region already taken, through the closest
+    pair of pixels (squared Euclidean distance; ties: smaller parent-region
+    rank, then smaller pixel indices).  Across each such edge the offset is
+    round((median_parent - median_child) / 2pi) cycles, each median taken over
+    the unwrapped phase of the endpoint's region inside a window x window box
+    centred on the endpoint (numpy median, round half to even); the child's
+    phase is shifted by 2pi times that offset before its own children are
+    attached, so offsets propagate from parent to child.  Returns (bridged
+    phase float64, cycle offset per pixel int64, region index per pixel, -1
+    where invalid), regions numbered in their processing order."""
+    u = np.array(unwrapped, np.float64)
+    ok = np.asarray(valid, bool)
+    m, n = ok.shape
+    costs = np.ones((4, m, n), np.int16)
+    flows = np.zeros((2, m, n), np.int8)
+    lab = components(costs, flows, ok, 0).astype(np.int64)  # every edge between valid pixels
+    roots = np.unique(lab[lab > 0])
+    sizes = {r: int((lab == r).sum()) for r in roots}
+    order = sorted(roots, key=lambda r: (-sizes[r], r))
+    region = np.full((m, n), -1, np.int64)
+    for rank, r in enumerate(order):
+        region[lab == r] = rank
+    shift = np.zeros((m, n), np.int64)
+    h = window // 2
+    pix = [np.argwhere(region == k) for k in range(len(order))]
+
+    def median_at(i, j, k):
+        box = region[max(0, i - h):i + h + 1, max(0, j - h):j + h + 1] == k
+        vals = (u + 2 * np.pi * shift)[max(0, i - h):i + h + 1, max(0, j - h):j + h + 1][box]
+        return float(np.median(vals))
+
+    for k in range(1, len(order)):
+        best = None
+        for q in range(k):
+            a, b = pix[q], pix[k]
+            d = ((a[:, None, :] - b[None, :, :]) ** 2).sum(axis=2)
+            flat = int(np.argmin(d))  # row-major over (parent pixel, child pixel): smallest indices on ties
+            ia, ib = divmod(flat, d.shape[1])
+            key = (int(d.flat[flat]), q)
+            if best is None or key < best[0]:
+                best = (key, tuple(a[ia]), tuple(b[ib]))
+        _, pa, pb = best
+        off = int(np.rint((median_at(*pa, region[pa]) - median_at(*pb, k)) / (2 * np.pi)))
+        shift[region == k] = off  # the parent's median already includes its own shift
+    out = np.where(ok, u + 2 * np.pi * shift, np.nan)
+    return out, shift, region
