@@ -66,3 +66,20 @@ def test_reference_arm_prints_one_line_under_two_ranks():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_search_traffic_only_for_the_captured_source(monkeypatch):
+    """The roofline's DRAM traffic is reported per pass for the scene it was
+    captured on, and only while the solver source has the captured hash."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.search_traffic_per_launch("lobes", 7) is None
+    got = bench.search_traffic_per_launch("earthquake", 7)
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2609_36267_b300", "csrc", "ww_mcf.cu"), "rb") as f:
+        same = hashlib.sha256(f.read()).hexdigest() == bench.SEARCH_DRAM_SOURCE_SHA256
+    assert got == (bench.SEARCH_DRAM_BYTES_PER_UNWRAP / 7 if same else None)
+    monkeypatch.setattr(bench, "SEARCH_DRAM_SOURCE_SHA256", "0" * 64)
+    assert bench.search_traffic_per_launch("earthquake", 7) is None
