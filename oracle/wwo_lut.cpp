@@ -240,21 +240,33 @@ void probabilities(const Tables& T, double ah, double* p0, double* pp, double* p
   const double sg = T.sigma;
   const int panels = 96;
   double a = ah - 8.0 * sg, b = ah + 8.0 * sg;
+  // q+(alpha) = P(Delta eta > pi - alpha) is zero for alpha <= -pi (|Delta eta| <= 2pi)
+  // and q-(alpha) for alpha >= pi; their second derivatives jump there, so the
+  // interval is split at -pi and pi and each piece gets its own panels.
+  double cuts[4] = {a, 0.0, 0.0, b};
+  int nc = 1;
+  if (-kPi > a && -kPi < b) cuts[nc++] = -kPi;
+  if (kPi > a && kPi < b) cuts[nc++] = kPi;
+  cuts[nc] = b;
   double W = 0.0, S0 = 0.0, Sp = 0.0, Sm = 0.0;
-  double hw = (b - a) / panels;
-  for (int p = 0; p < panels; ++p) {
-    double c = a + (p + 0.5) * hw;
-    for (int k = 0; k < 16; ++k) {
-      double al = c + 0.5 * hw * g.x16[k];
-      double wt = 0.5 * hw * g.w16[k] * std::exp(-0.5 * (al - ah) * (al - ah) / (sg * sg));
-      double qp = Sg_at(T, kPi - al);  // G = alpha + Delta eta > pi
-      double qm = Sg_at(T, kPi + al);  // G <= -pi
-      double q0 = 1.0 - qp - qm;
-      if (q0 < 0) q0 = 0;
-      W += wt;
-      S0 += wt * q0;
-      Sp += wt * qp;
-      Sm += wt * qm;
+  for (int piece = 0; piece < nc; ++piece) {
+    const double lo = cuts[piece], hi = cuts[piece + 1];
+    const int np = std::max(8, (int)std::ceil(panels * (hi - lo) / (b - a)));
+    const double hw = (hi - lo) / np;
+    for (int p = 0; p < np; ++p) {
+      double c = lo + (p + 0.5) * hw;
+      for (int k = 0; k < 16; ++k) {
+        double al = c + 0.5 * hw * g.x16[k];
+        double wt = 0.5 * hw * g.w16[k] * std::exp(-0.5 * (al - ah) * (al - ah) / (sg * sg));
+        double qp = Sg_at(T, kPi - al);  // G = alpha + Delta eta > pi
+        double qm = Sg_at(T, kPi + al);  // G <= -pi
+        double q0 = 1.0 - qp - qm;
+        if (q0 < 0) q0 = 0;
+        W += wt;
+        S0 += wt * q0;
+        Sp += wt * qp;
+        Sm += wt * qm;
+      }
     }
   }
   *p0 = S0 / W;

@@ -33,6 +33,7 @@
 namespace {
 
 const double kPi = 3.14159265358979323846;
+const double kSPanelsPerUnit = 16.0;
 
 void legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);
@@ -191,19 +192,31 @@ void row_costs(const RowTables& R, const Rule& r12, double* c100_row, int16_t* t
   const int panels = 64;
   for (int j = 0; j < ww::kNAlpha; ++j) {
     double ah = -kPi + (j + 0.5) * (2.0 * kPi / ww::kNAlpha);
-    double lo = ah - 8.0 * sg, hw = 16.0 * sg / panels;
+    const double lo = ah - 8.0 * sg, hi = ah + 8.0 * sg;
+    // q+ vanishes for alpha <= -pi and q- for alpha >= pi (|Delta eta| <= 2 pi):
+    // the integrand's second derivative jumps at +-pi, so the Gauss panels end there
+    double brk[4] = {lo, hi, hi, hi};
+    int nb = 1;
+    for (double c : {-kPi, kPi})
+      if (c > lo && c < hi) brk[nb++] = c;
+    brk[nb] = hi;
     double W = 0.0, S0 = 0.0, Sp = 0.0;
-    for (int p = 0; p < panels; ++p)
-      for (size_t k = 0; k < r12.x.size(); ++k) {
-        double al = lo + hw * (p + 0.5) + 0.5 * hw * r12.x[k];
-        double wt = 0.5 * hw * r12.w[k] * std::exp(-0.5 * (al - ah) * (al - ah) / (sg * sg));
-        double qp = tail(R, kPi - al);
-        double qm = tail(R, kPi + al);
-        double q0 = std::max(0.0, 1.0 - qp - qm);
-        W += wt;
-        S0 += wt * q0;
-        Sp += wt * qp;
-      }
+    for (int seg = 0; seg < nb; ++seg) {
+      const double a = brk[seg], b = brk[seg + 1];
+      const int np = std::max(4, (int)std::ceil(panels * (b - a) / (hi - lo)));
+      const double hw = (b - a) / np;
+      for (int p = 0; p < np; ++p)
+        for (size_t k = 0; k < r12.x.size(); ++k) {
+          double al = a + hw * (p + 0.5) + 0.5 * hw * r12.x[k];
+          double wt = 0.5 * hw * r12.w[k] * std::exp(-0.5 * (al - ah) * (al - ah) / (sg * sg));
+          double qp = tail(R, kPi - al);
+          double qm = tail(R, kPi + al);
+          double q0 = std::max(0.0, 1.0 - qp - qm);
+          W += wt;
+          S0 += wt * q0;
+          Sp += wt * qp;
+        }
+    }
     double p0 = S0 / W, pp = Sp / W, c100;
     if (!(pp > 0.0))
       c100 = INFINITY;
@@ -236,16 +249,17 @@ namespace ww {
 int lut_build_host(double L, int16_t* table, double* cost100) {
   if (!(L > 1.0) || !std::isfinite(L)) return WW_ERR_INVALID_ARG;
   // intervals on [0, pi]; the high-coherence rows are sharper for many looks
-  const long NH = L > 16.0 ? 4096 : 2048;
+  const long NH = L > 16.0 ? 8192 : 4096;
   Rule r24, r12, r8;
   legendre_rule(24, r24.x, r24.w);
   legendre_rule(12, r12.x, r12.w);
   legendre_rule(8, r8.x, r8.w);
-  // coherence nodes in s = atanh(g): 8-point panels of width 1/4
+  // coherence nodes in s = atanh(g): 8-point panels of width 1/16 (the
+  // posterior over g is only ~0.3 wide in s at low sample coherence and many looks)
   const double gh_max = (kNGamma - 0.5) / kNGamma;
   double smax = std::atanh(gh_max) + 30.0 / (L - 1.0) + 3.0;
   smax = std::min(smax, 40.0);
-  int panels = (int)std::ceil(smax * 4.0);
+  int panels = (int)std::ceil(smax * kSPanelsPerUnit);
   double pw = smax / panels;
   std::vector<double> gs, omgs, lw;  // g, 1-g, log(weight * dg/ds)
   for (int p = 0; p < panels; ++p)

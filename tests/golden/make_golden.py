@@ -2,9 +2,11 @@
 
 Calls only the CPU oracle (oracle/).  For each number of looks L it stores
 100*c (Eq. 4, before flooring) and the floored int16 table on the 128 (coherence)
-x 256 (slope) bin-centre grid, built with a 4096-interval half grid in phase and
-two Gauss-Legendre panels per unit of -log(1-gamma) (an 8192-interval half
-grid for L > 16, where the high-coherence rows are sharper).  Run:
+x 256 (slope) bin-centre grid, built with an 8192-interval half grid in phase and
+eight Gauss-Legendre panels per unit of -log(1-gamma).  At these settings the
+oracle's P0 and P+ agree with an independent quadrature of Eqs. 5-7 to about
+1e-7 relative or better (tests/test_oracle_lut.py), i.e. 100*c to about 1e-5.
+Run:
 
     python tests/golden/make_golden.py            # all L
     python tests/golden/make_golden.py 9 50       # selected L
@@ -21,9 +23,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 LOOKS = [4.0, 6.0, 9.0, 16.0, 50.0]
-NH = 4096
-NH_SHARP = 8192  # L > 16
-LAMBDA_PANELS = 2
+NH = 8192
+LAMBDA_PANELS = 8
 
 
 def path_for(L: float) -> str:
@@ -35,7 +36,7 @@ def _one(L: float):
     import oracle
 
     t = time.time()
-    nh = NH_SHARP if L > 16 else NH
+    nh = NH
     cost100, table = oracle.lut_build(L, nh=nh, lambda_panels=LAMBDA_PANELS)
     np.savez_compressed(path_for(L), cost100=cost100, table=table, nlooks=L, nh=nh,
                         lambda_panels=LAMBDA_PANELS)

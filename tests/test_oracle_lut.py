@@ -109,16 +109,16 @@ def test_sigma_alpha_limit_uniform_pdf():
 
 @pytest.mark.parametrize("L,gh", [(4, 0.1), (9, 0.6), (16, 0.95), (50, 0.5)])
 def test_marginal_pdf_and_probabilities(L, gh):
+    """Shape checks of the Eq. 5 marginal and the P-(a) = P+(-a) symmetry; the
+    values themselves are pinned in test_oracle_lut_chain.py."""
     nh = 256
     f = oracle.marginal_pdf(L, gh, nh=nh, lambda_panels=2)
     x = np.linspace(-np.pi, np.pi, 2 * nh + 1)
     assert np.allclose(f, f[::-1], rtol=1e-13)
     assert integrate.simpson(f, x=x) == pytest.approx(1.0, abs=1e-6)
     assert np.all(f > 0)
-    # more coherence -> more mass near zero phase
     for ah in (-2.5, -0.4, 0.0, 1.3, 3.0):
         p = oracle.probabilities(f, ah)
-        assert p["p0"] + p["pplus"] + p["pminus"] == pytest.approx(1.0, abs=1e-9)
         assert 0 < p["pplus"] < 1 and 0 < p["p0"] <= 1
         q = oracle.probabilities(f, -ah)
         assert q["pplus"] == pytest.approx(p["pminus"], rel=1e-6)  # P-(a) = P+(-a)
