@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(RTX* RTT) k_residues(const void* __restrict__ 
                                                         const uint8_t* __restrict__ mask, int64_t m,
                                                         int64_t n, int8_t* __restrict__ res,
                                                         int32_t* __restrict__ ground) {
-  residues_tile(ifg, is_complex, coh, mask, m, n, res, ground, blockIdx.x, blockIdx.y);
+  const int64_t gx = (n - 1 + RTX - 1) / RTX, b = blockIdx.x;  // one-dimensional grid of tiles
+  residues_tile(ifg, is_complex, coh, mask, m, n, res, ground, b % gx, b / gx);
 }
 
 // ---------------- costs ----------------
@@ -278,9 +279,13 @@ __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int
                                                const int16_t* __restrict__ table, int w, float steep_rad,
                                                int16_t* __restrict__ costs, SteepCtr* ctr, uint32_t* list,
                                                unsigned long long list_cap) {
-  costs_tile(ifg, is_complex, coh, mask, m, n, table, w, steep_rad, costs, ctr, list, list_cap, blockIdx.x,
-             blockIdx.y);
+  // one-dimensional grid of tiles (gridDim.y would cap the rows at 65535 tiles)
+  const int64_t gx = (n + CTX - 1) / CTX, b = blockIdx.x;
+  costs_tile(ifg, is_complex, coh, mask, m, n, table, w, steep_rad, costs, ctr, list, list_cap, b % gx, b / gx);
 }
+
+// number of k_costs tiles (one block each) of an m x n image
+unsigned cost_tiles(int64_t m, int64_t n) { return (unsigned)(((n + CTX - 1) / CTX) * ((m + CTY - 1) / CTY)); }
 
 // Within the cap (mode 0) with every candidate in the list: zero the listed edges.
 __global__ void k_steep_zero_list(const SteepCtr* ctr, const uint32_t* list, unsigned long long list_cap,
@@ -944,8 +949,8 @@ __global__ void __launch_bounds__(kRowThreads) k_integrate_rows_b(const GridItem
 ww_status launch_residues(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                           int64_t m, int64_t n, int8_t* res, int32_t* ground, cudaStream_t s) {
   WW_CUDA_TRY(cudaMemsetAsync(ground, 0, sizeof(int32_t), s));
-  dim3 grid((unsigned)((n - 1 + RTX - 1) / RTX), (unsigned)((m - 1 + RTY - 1) / RTY));
-  k_residues<<<grid, dim3(RTX, RTT), 0, s>>>(ifg, is_complex, coh, mask, m, n, res, ground);
+  const int64_t tiles = ((n - 1 + RTX - 1) / RTX) * ((m - 1 + RTY - 1) / RTY);
+  k_residues<<<(unsigned)tiles, dim3(RTX, RTT), 0, s>>>(ifg, is_complex, coh, mask, m, n, res, ground);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
 }
@@ -979,15 +984,14 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
                        ww_workspace* ws, int16_t* costs, cudaStream_t s) {
   SteepCtr* ctr = reinterpret_cast<SteepCtr*>(ws->steep_ctr);
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
-  dim3 grid((unsigned)((n + CTX - 1) / CTX), (unsigned)((m + CTY - 1) / CTY));
   // candidate list: within the cap every candidate fits (cap + 1 <= capacity), so the
   // common case zeroes the listed edges instead of scanning every edge again
   const int64_t need = steep_list_capacity(m * n, p->steep_cap_ppm);
   const bool use_list = ws->steep_list && need <= ws->steep_list_cap && 2 * m * n < (1ll << 32);
   uint32_t* list = use_list ? ws->steep_list : nullptr;
   const unsigned long long list_cap = use_list ? (unsigned long long)ws->steep_list_cap : 0ull;
-  k_costs<<<grid, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad,
-                               costs, ctr, list, list_cap);
+  k_costs<<<cost_tiles(m, n), 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, dtable, p->box_half_width,
+                                           p->steep_rad, costs, ctr, list, list_cap);
   WW_CUDA_TRY(cudaGetLastError());
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
   if (use_list) k_steep_zero_list<<<148 * 4, 256, 0, s>>>(ctr, list, list_cap, m * n, costs);
@@ -1202,8 +1206,7 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   const ww_params* p = params ? params : &def;
   if (!ifg || !coh || !lut || !costs || m < 2 || n < 2) return WW_ERR_INVALID_ARG;
   if (m > kNoAllocMaxPixels || n > kNoAllocMaxPixels || m * n > kNoAllocMaxPixels) return WW_ERR_INVALID_ARG;
-  if (p->box_half_width < 0 || p->box_half_width > CW || p->steep_cap_ppm < 0 || p->steep_cap_ppm > 1000000)
-    return WW_ERR_INVALID_ARG;
+  if (!params_valid(p)) return WW_ERR_INVALID_ARG;
   unsigned char* base = nullptr;
   ww_status st = noalloc_scratch(&base);
   if (st != WW_OK) return st;
@@ -1213,13 +1216,15 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   SteepCtr* ctr = reinterpret_cast<SteepCtr*>(base + kNoAllocCtrOff);
   uint32_t* blocksum = reinterpret_cast<uint32_t*>(base + kNoAllocBlocksumOff);
   const int c = is_complex ? 1 : 0;
-  // every call shares the array: copy this call's table, clear what starts at zero
-  WW_CUDA_TRY(cudaMemcpyAsync(dtable, lut_host_table(lut), kNoAllocTableBytes, cudaMemcpyHostToDevice, s));
+  // every call shares the array: copy this call's table, clear what starts at zero.
+  // The table comes from its page-locked copy, so the upload does not wait for the
+  // stream; only if that copy could not be made is the pageable one used.
+  const int16_t* src = lut_pinned_table(lut);
+  WW_CUDA_TRY(cudaMemcpyAsync(dtable, src ? src : lut_host_table(lut), kNoAllocTableBytes, cudaMemcpyHostToDevice, s));
   WW_CUDA_TRY(cudaMemsetAsync(hist, 0, 65536 * sizeof(uint32_t), s));
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
-  dim3 grid((unsigned)((n + CTX - 1) / CTX), (unsigned)((m + CTY - 1) / CTY));
-  k_costs<<<grid, 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad, costs, ctr,
-                               nullptr, 0ull);
+  k_costs<<<cost_tiles(m, n), 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad,
+                                           costs, ctr, nullptr, 0ull);
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
   const int hist_blocks = 148 * 8;
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, hist, 0);

@@ -22,6 +22,11 @@ def test_noalloc_rejects_grids_over_its_limit():
     assert st == ww.WW_ERR_INVALID_ARG
     st = ww.lib().ww_costs_noalloc(dummy, 0, dummy, None, 1, 100, lut.handle, None, dummy, None)
     assert st == ww.WW_ERR_INVALID_ARG
+    # the same parameter checks as ww_costs: a NaN steep threshold would silently
+    # disable the steep-edge cap (Sec. II-B)
+    bad = ww.default_params(steep_rad=float("nan"))
+    st = ww.lib().ww_costs_noalloc(dummy, 0, dummy, None, 100, 100, lut.handle, ctypes.byref(bad), dummy, None)
+    assert st == ww.WW_ERR_INVALID_ARG
 
 
 def _noise(seed, m, n):
@@ -51,3 +56,32 @@ def test_noalloc_matches_workspace_costs_on_consecutive_calls():
         got = ww.costs_noalloc(ifg, coh, lut, mask).cpu().numpy()
         assert np.array_equal(got, ref)
         assert np.count_nonzero(ref) > 0
+
+
+@pytest.mark.gpu
+def test_noalloc_call_after_the_first_is_captured_into_a_graph():
+    """After its first call on a device (which looks up the scratch array's
+    address), the entry point enqueues only an upload from the table's
+    page-locked copy, two memsets and kernel launches, so a later call can be
+    captured into a CUDA graph; each replay gives ww_costs's planes."""
+    import torch
+
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x = _noise(5, 190, 207)
+    tab = ((np.arange(128 * 256, dtype=np.int64).reshape(128, 256) * 13) % 25013).astype(np.int16)
+    lut = ww.Lut.from_table(x.nlooks, tab)
+    ifg, coh, mask = dev(x.phase), dev(x.coh), dev(x.mask)
+    ref = ww.costs(ifg, coh, lut, ww.Workspace(190, 207), mask).cpu().numpy()
+    out = torch.empty((4, 190, 207), dtype=torch.int16, device="cuda")
+    ww.costs_noalloc(ifg, coh, lut, mask, out=out)  # first call on this device: outside the capture
+    torch.cuda.synchronize()
+    out.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=s):
+        ww.costs_noalloc(ifg, coh, lut, mask, out=out)
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
