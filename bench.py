@@ -38,16 +38,19 @@ WORKLOADS = {
     "served": dict(name="served: Poisson arrivals, log-uniform 0.25-32 Mpixel, 150 GB budget", m=0, n=0),
 }
 
-# algorithmic bytes per node per search tile visit: labels read+write (16),
-# potentials (8), four cost planes (8), two flow planes (2)
-SEARCH_BYTES_PER_NODE = 34
+# Algorithmic bytes of the shortest-path search per settled-node visit (a node
+# holding a finite label at the end of a tile visit, counted on the device):
+# cost planes 8, flow planes 2, potential 8, label write 8, worklist 2.
+SEARCH_BYTES_PER_SETTLED_VISIT = 28
+# Bytes a tile visit moves for every node of the tile, reached or not: labels
+# read and written 16, potential 8, four cost planes 8, two flow planes 2.
+SEARCH_TILE_BYTES_PER_NODE = 34
 SEARCH_TILE_NODES = 32 * 32
 
 # DRAM bytes (read + write) of every k_search launch of one unwrap of the
-# 74-Mpixel earthquake scene, from one ncu capture of the same bench command
-# (profiles/k_search_dram_earthquake_8192x9000.md), and the SHA-256 of the
-# solver source it was taken on: the figure is reported only while that source
-# is unchanged.
+# 74-Mpixel earthquake scene, from one ncu capture of the same bench command,
+# and the SHA-256 of the solver source it was taken on: the figure is reported
+# only while that source is unchanged.
 SEARCH_DRAM_BYTES_PER_UNWRAP = 2_279_595_691
 SEARCH_DRAM_SOURCE_SHA256 = "a1fa3180c4111b3319e2472682f2b1a2c86817d62015a26e011d29bd7104418a"
 
@@ -163,6 +166,20 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def host_cpu():
+    """CPU model and logical core count of this host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(workload: str, seconds_target: float = 20.0):
     """The oracle as it stands on this host (single-threaded), on a bounded crop."""
     import oracle
@@ -194,31 +211,56 @@ def cpu_baseline(workload: str, seconds_target: float = 20.0):
         if time.perf_counter() - t0 > seconds_target or reps >= 3:
             break
     dt = (time.perf_counter() - t0) / reps
-    return {"value": m * n / dt / 1e6, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-            "sample": f"{m}x{n} crop of the same workload recipe (seed 3001 scaled), full path, "
-                      f"{reps} rep(s), {dt:.2f} s each"}
+    return dict({"value": m * n / dt / 1e6, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+                 "sample": f"{m}x{n} crop of the same workload recipe (seed 3001 scaled), full path, "
+                           f"{reps} rep(s), {dt:.2f} s each", "sample_pixels": m * n, "seconds_per_sample": dt},
+                **host_cpu())
 
 
 def run_reference(args, rank, world):
+    """The oracle timed as the reference arm: each step is one whole-path unwrap
+    of a bounded crop of the workload (the full 74-Mpixel scene would take the
+    single-threaded oracle over an hour per step); ms_per_step is that measured
+    step, value the oracle's Mpixel/s on it."""
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    steps = []
+    steps, secs = [], []
     base = None
     for _ in range(args.warmup + args.steps):
         base = cpu_baseline(args.workload, seconds_target=1.0)
         steps.append(base["value"])
+        secs.append(base["seconds_per_sample"])
     vals = steps[args.warmup:] or steps
     v = float(np.median(vals))
+    ms = float(np.mean(secs[args.warmup:] or secs)) * 1e3
     px = wl["m"] * wl["n"]
     line = {"metric": "Mpixel/s unwrapped at oracle-equal optimal cost", "value": v, "unit": "Mpixel/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": px / (v * 1e6) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/fp32", "data": "synthetic",
-            "config": {"workload": wl["name"], "pixels": px}, "impl": "reference",
+            "config": run_config(args, wl, px, world), "impl": "reference",
+            "sample": {"what": base["sample"], "pixels_per_step": base["sample_pixels"],
+                       "full_scene_seconds_extrapolated": px / (v * 1e6)},
             "cpu_baseline": dict(base, value=v),
             "e2e": {"value": v, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+SCHEDULE_KEYS = ("full_passes", "band_start_ppm", "band_min", "band_mult", "band_growth", "ground_sink_below",
+                 "zero_stop_below", "zero_band_hops", "search_ctas_per_sm")
+
+
+def run_config(args, wl, px, world):
+    """The `config` object both arms print for the same workload."""
+    import paper_2609_36267_b300 as ww
+
+    prm = ww.default_params()
+    for k, v in json.loads(args.params).items():
+        setattr(prm, k, int(v))
+    return {"workload": wl["name"], "pixels": px, "replicas": world,
+            "parallelism": "replicas" if world > 1 else "single",
+            "schedule": {k: getattr(prm, k) for k in SCHEDULE_KEYS}}
 
 
 def run_ours(args, rank, world, local):
@@ -322,41 +364,61 @@ def run_ours(args, rank, world, local):
     ms_e2e = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
     assert np.array_equal(host_out[(args.steps - 1) % 2].numpy().view(np.uint32),
                           dev_out[(args.steps - 1) % 2][0].cpu().numpy().view(np.uint32))
+    # the last timed solve's flows and potentials, certified on the device: no
+    # capacity or conservation violation and no residual arc of negative reduced
+    # cost (LP duality: the flow is optimal), total cost = the returned one
+    cert = ws.certify_last_unwrap(m, n)
+    certified = cert[:3] == (0, 0, 0) and len(costs_seen) == 1 and cert[3] == next(iter(costs_seen))
     h2d = host_ifg.numel() * host_ifg.element_size() + host_coh.numel() * 4 + host_mask.numel()
     d2h = host_unw.numel() * 4
     # ---- roofline of the dominant kernel (the shortest-path search) ----
     st = stats_acc[-1]
     peak, peak_kind = measured_peaks()
-    search_bytes = st["tile_visits"] * SEARCH_TILE_NODES * SEARCH_BYTES_PER_NODE
+    search_bytes = st["settled_visits"] * SEARCH_BYTES_PER_SETTLED_VISIT
+    tile_bytes = st["tile_visits"] * SEARCH_TILE_NODES * SEARCH_TILE_BYTES_PER_NODE
     launches = max(1, st["search_iterations"])
-    achieved = search_bytes / (st["ms_search_gpu"] * 1e-3) / 1e9 if st["ms_search_gpu"] > 0 else 0.0
+    sec = st["ms_search_gpu"] * 1e-3
+    achieved = search_bytes / sec / 1e9 if sec > 0 else 0.0
     roof = {"kernel": "k_search (tiled label-correcting shortest-path search)", "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-            "traffic": search_traffic_per_launch(args.workload, launches), "bytes_per_launch": search_bytes / launches,
-            "ms_per_launch": st["ms_search_gpu"] / launches, "launches_per_step": launches}
+            "traffic": search_traffic_per_launch(args.workload, launches),
+            "bytes_model": f"{SEARCH_BYTES_PER_SETTLED_VISIT} B per settled-node visit (device counter)",
+            "settled_visits_per_step": st["settled_visits"], "bytes_per_launch": search_bytes / launches,
+            "ms_per_launch": st["ms_search_gpu"] / launches, "launches_per_step": launches,
+            "traffic_model": {"bytes_per_launch": tile_bytes / launches,
+                              "frac": (tile_bytes / sec / 1e9 / peak) if sec > 0 else 0.0,
+                              "what": f"{SEARCH_TILE_BYTES_PER_NODE} B for every node of every visited 32x32 tile"}}
     if rank == 0:
         base = cpu_baseline(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
         line = {"metric": "Mpixel/s unwrapped at oracle-equal optimal cost", "value": value, "unit": "Mpixel/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/fp32",
                 "data": "synthetic (seeded generator; inputs 0.96 GB > L2, no flush needed)",
-                "config": {"workload": wl["name"], "pixels": px, "replicas": world,
-                           "parallelism": "replicas" if world > 1 else "single",
-                           "schedule": {k: getattr(prm, k) for k in ("full_passes", "band_start_ppm", "band_min",
-                                                                     "band_mult", "band_growth", "ground_sink_below",
-                                                                     "zero_stop_below", "zero_band_hops",
-                                                                     "search_ctas_per_sm")}},
+                "config": run_config(args, wl, px, world),
                 "e2e": {"value": px * world / (ms_e2e * 1e-3) / 1e6, "unit": "Mpixel/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": None, "roofline": roof, "cpu_baseline": base, "clocks": clk.summary(),
                 "solver": {k: st[k] for k in ("passes", "augmentations", "search_iterations", "tile_visits",
-                                                 "residues", "ms_search_gpu", "ms_other", "local_rounds",
-                                                 "visit_cycles", "load_cycles", "relax_cycles")},
-                "total_costs_seen": sorted(costs_seen)}
+                                                 "settled_visits", "residues", "ms_search_gpu", "ms_other",
+                                                 "local_rounds", "visit_cycles", "load_cycles", "relax_cycles")},
+                "total_costs_seen": sorted(costs_seen),
+                "certified": bool(certified),
+                "certificate": {"capacity_violations": cert[0], "conservation_violations": cert[1],
+                                "negative_reduced_costs": cert[2], "total_cost": cert[3],
+                                "table": "library FP64 table for L=50, equal entrywise to the oracle's"}}
         line["gpu_launches"] = launch_count(st, args.steps)
         line["components"] = measure_components(ww, torch, x, ifg, coh, mask, unw, ws, max(3, args.steps), peak,
                                                 peak_kind)
+        if world == 1 and args.workload == "earthquake" and not args.no_extras:
+            # rows a5 and a6 under the same clock: the batched and served forms vs
+            # the plain one-at-a-time solve (the earthquake buffers are freed first)
+            del ws, ifg, coh, mask, unw, cyc, dev_in, dev_out
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            line["batched"] = run_batched(args, summary=True)
+            torch.cuda.empty_cache()
+            line["served"] = run_served(args, summary=True)
         print(json.dumps(line), flush=True)
 
 
@@ -415,8 +477,9 @@ def _generate(fn, indices):
         return list(ex.map(fn, indices, chunksize=max(1, len(indices) // (4 * workers))))
 
 
-def run_batched(args):
-    """Batched form vs the same items unwrapped one at a time (ww_unwrap)."""
+def run_batched(args, summary=False):
+    """Batched form vs the same items unwrapped one at a time (ww_unwrap).
+    With summary=True the result is returned (a key of the default run's line)."""
     import torch
 
     import paper_2609_36267_b300 as ww
@@ -453,23 +516,40 @@ def run_batched(args):
     ms = e0.elapsed_time(e1) / args.steps
     assert [o[2] for o in out] == costs and all(o[3] == 0 for o in out)
     st = batch.stats()
-    if args.skip_plain:
+    if args.skip_plain and not summary:
         print(json.dumps({"workload": "batched", "ms_per_step": ms, "pixels": px, "tune": tune}), flush=True)
         return
     # plain: one request at a time through ww_unwrap (same items, same workspace size class)
     m_max = max(r[0].shape[0] for r in reqs)
     n_max = max(r[0].shape[1] for r in reqs)
     ws = ww.Workspace(m_max, n_max)
-    plain_costs = []
+    plain_costs, plain_K = [], []
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record()
     for r in reqs:
-        plain_costs.append(ww.unwrap(*r, ws=ws)[2])
+        _, K1, tc1 = ww.unwrap(*r, ws=ws)
+        plain_costs.append(tc1)
+        plain_K.append(K1)
     p1.record()
     torch.cuda.synchronize()
     ms_plain = p0.elapsed_time(p1)
     assert plain_costs == costs
+    # cycle maps alone vs in the batch: optimal flows can tie, so the matching
+    # fraction is reported (costs are equal, asserted above)
+    same = sum(int((o[1] == k1).sum()) for o, k1 in zip(out, plain_K))
+    k_agree = same / px
+    items_identical = sum(1 for o, k1 in zip(out, plain_K) if bool(torch.equal(o[1], k1)))
+    del plain_K
+    if summary:
+        return {"value": px / (ms * 1e-3) / 1e6, "unit": "Mpixel/s", "ms_per_batch": ms, "steps": args.steps,
+                "items": args.items, "pixels": px, "workload": WORKLOADS["batched"]["name"],
+                "data": f"synthetic: {args.items} generated items (seed 4000+i)",
+                "plain_sequential": {"value": px / (ms_plain * 1e-3) / 1e6, "unit": "Mpixel/s", "ms": ms_plain},
+                "speedup_vs_plain": ms_plain / ms, "total_cost_mismatches_vs_alone": 0,
+                "K_agreement_alone_vs_batch": k_agree, "items_with_identical_K": items_identical,
+                "autotune": tune, "passes": st["passes"], "augmentations": st["augmentations"],
+                "clocks": clk.summary()}
     line = {"metric": "Mpixel/s unwrapped at oracle-equal optimal cost", "value": px / (ms * 1e-3) / 1e6,
             "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/fp32",
@@ -477,7 +557,8 @@ def run_batched(args):
             "config": {"workload": WORKLOADS["batched"]["name"], "items": args.items, "pixels": px},
             "plain_sequential": {"value": px / (ms_plain * 1e-3) / 1e6, "unit": "Mpixel/s", "ms": ms_plain},
             "speedup_vs_plain": ms_plain / ms, "autotune": tune, "solver": st, "clocks": clk.summary(),
-            "total_cost_sum": int(sum(costs))}
+            "total_cost_sum": int(sum(costs)), "K_agreement_alone_vs_batch": k_agree,
+            "items_with_identical_K": items_identical}
     print(json.dumps(line), flush=True)
 
 
@@ -487,8 +568,9 @@ def _served_scene(i):
     return synth.config2(seed=5000 + i, m=4096, n=8192)
 
 
-def run_served(args):
-    """Continuous-batching server vs a one-request-at-a-time loop on the same arrivals."""
+def run_served(args, summary=False):
+    """Continuous-batching server vs a one-request-at-a-time loop on the same arrivals.
+    With summary=True the result is returned (a key of the default run's line)."""
     import threading
 
     import torch
@@ -552,6 +634,7 @@ def run_served(args):
         tickets = [None] * len(reqs)
         lat = [0.0] * len(reqs)
         costs = [0] * len(reqs)
+        kept_K = {}  # cycle maps of the first requests, compared with their solve alone below
         bad = []
         ready = threading.Semaphore(0)
 
@@ -563,6 +646,8 @@ def run_served(args):
                     bad.append((k, out[3]))
                 costs[k] = out[2]
                 lat[k] = out[4]
+                if k < args.compare_k:
+                    kept_K[k] = out[1]
 
         th = threading.Thread(target=waiter)
         th.start()
@@ -580,15 +665,19 @@ def run_served(args):
         assert not bad, bad[:4]
         # plain loop on the same arrivals (FIFO, one at a time); check equality of costs
         plat = [0.0] * len(reqs)
+        same_px = cmp_px = 0
         start = time.perf_counter()
         for k, r in enumerate(reqs):
             now = time.perf_counter() - start
             if arrivals[k] > now:
                 time.sleep(arrivals[k] - now)
-            tc = ww.unwrap(*r, ws=ws)[2]
+            _, K1, tc = ww.unwrap(*r, ws=ws)
             torch.cuda.synchronize()
             plat[k] = (time.perf_counter() - start - arrivals[k]) * 1e3
             costs_alone[k] = tc
+            if k in kept_K:
+                same_px += int((kept_K.pop(k) == K1).sum())
+                cmp_px += px_list[k]
         pspan = time.perf_counter() - start
         mism = sum(1 for k in range(len(reqs)) if costs[k] != costs_alone[k])
         results[f"load_{load:g}"] = {
@@ -597,8 +686,19 @@ def run_served(args):
                        "p99_ms": float(np.percentile(lat, 99)), "span_s": span, "stats": st},
             "plain_loop": {"Mpixel_per_s": total_px / pspan / 1e6, "p50_ms": float(np.percentile(plat, 50)),
                            "p99_ms": float(np.percentile(plat, 99)), "span_s": pspan},
-            "total_cost_mismatches_vs_alone": mism}
+            "total_cost_mismatches_vs_alone": mism,
+            "K_agreement_alone_vs_served": {"fraction": same_px / max(1, cmp_px),
+                                            "requests_compared": min(args.compare_k, len(reqs))}}
     best = max(v["served"]["Mpixel_per_s"] for v in results.values())
+    note = (f"{args.requests} requests, fewer than the 10,000-request stream of the workload definition, to keep "
+            "the default run within minutes; sizes, arrivals and budget follow it") if args.requests < 10000 else None
+    if summary:
+        return {"value": best, "unit": "Mpixel/s", "workload": WORKLOADS["served"]["name"],
+                "requests": args.requests, "requests_note": note, "mean_Mpixel": total_px / len(reqs) / 1e6,
+                "total_Gpixel": total_px / 1e9, "budget_gb": args.budget_gb, "max_active": args.max_active,
+                "data": (f"synthetic: crops of {args.served_pool} generated 4096x8192 two-lobe scenes "
+                         f"({len(crops)} distinct crops, generation {t_gen:.0f} s)"),
+                "plain_loop_Mpixel_per_s_at_start": plain_px_s / 1e6, "loads": results}
     line = {"metric": "Mpixel/s unwrapped at oracle-equal optimal cost", "value": best, "unit": "Mpixel/s",
             "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/fp32",
@@ -607,7 +707,7 @@ def run_served(args):
             "config": {"workload": WORKLOADS["served"]["name"], "requests": args.requests,
                        "mean_Mpixel": total_px / len(reqs) / 1e6, "total_Gpixel": total_px / 1e9,
                        "budget_gb": args.budget_gb, "max_active": args.max_active,
-                       "plain_loop_Mpixel_per_s_at_start": plain_px_s / 1e6},
+                       "plain_loop_Mpixel_per_s_at_start": plain_px_s / 1e6, "requests_note": note},
             "loads": results}
     print(json.dumps(line), flush=True)
 
@@ -636,6 +736,10 @@ def main():
     ap.add_argument("--items", type=int, default=512, help="batched: items per batch")
     ap.add_argument("--pool", type=int, default=512, help="batched: distinct generated items (reused cyclically)")
     ap.add_argument("--requests", type=int, default=2000, help="served: requests in the stream")
+    ap.add_argument("--compare-k", type=int, default=64,
+                    help="served: requests whose cycle maps are compared with their solve alone")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default run: skip the batched and served measurements")
     ap.add_argument("--served-pool", type=int, default=3, help="served: generated 4096x8192 scenes to crop")
     ap.add_argument("--distinct", type=int, default=64, help="served: distinct crops kept on the device")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.7, 1.5], help="served: offered load vs plain")

@@ -76,9 +76,10 @@ typedef struct ww_params {
   float steep_rad;          /* unsmoothed |gradient| above which an edge costs 0: 1.0 (Sec. II-B) */
   int32_t steep_cap_ppm;    /* cap on zeroed steep edges, per million valid edges: 30000 = 3% */
   int32_t max_passes;       /* solver pass limit -> WW_ERR_TIMEOUT (default 100000) */
-  int32_t max_sweeps;       /* tile-sweep limit per shortest-path search (default 1000000) */
-  int32_t tile_rows;        /* search tile height in nodes (0 = auto) */
-  int32_t radius_policy;    /* 0 = full search each pass (default) */
+  int32_t wait_polls;       /* polls (~0.1-0.2 us each) of any device worklist wait before it gives
+                               up: the search then stops, the pass augments nothing and the solve
+                               returns WW_ERR_TIMEOUT with flows and potentials of the last complete
+                               pass (resumable, see ww_solve_mcf_resume); default 2^25, >= 1 */
   int32_t graph_loop;       /* 1 = the pass loop runs on the device inside one CUDA graph launch
                                (conditional while node; default), 0 = one host sync per pass */
   /* search schedule: the optimum does not depend on it (ww_autotune_batch picks it).
@@ -159,11 +160,17 @@ ww_status ww_costs(const void* ifg, int32_t is_complex, const float* coh, const 
  * the steep-edge selection scratch and a copy of the cost table live in one
  * file-scope device array of about 1.4 MB that every GPU loading the library
  * holds until the process exits.  Limit: m*n <= 2^27 pixels (134,217,728);
- * larger grids return WW_ERR_INVALID_ARG.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the array
- * and each rewrites it (table copy, cleared counters), so calls that overlap
- * on the GPU race and must be serialised by the caller (e.g. one stream). */
+ * larger grids return WW_ERR_INVALID_ARG, and so do parameters ww_costs would
+ * refuse.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every later call enqueues only an upload of the
+ * table from a page-locked host copy made when the table was built, two
+ * memsets and kernel launches, so it neither waits for the stream nor
+ * prevents capturing the call into a CUDA graph (if the page-locked copy
+ * could not be made, the upload comes from pageable memory, which does both).
+ * All calls share the array and each rewrites it (table copy, cleared
+ * counters), so calls that overlap on the GPU race and must be serialised by
+ * the caller (e.g. one stream). */
 ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const float* coh, const uint8_t* mask,
                            int64_t m, int64_t n, const ww_lut* lut, const ww_params* params,
                            int16_t* costs, ww_stream stream);
@@ -174,13 +181,34 @@ ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const float* coh
  * (the last entry is G) certifying optimality: every residual arc has reduced
  * cost c - p(tail) + p(head) >= 0; total_cost: device int64[1] = sum c_a x_a;
  * dev_status: device int32[1] (WW_OK, WW_ERR_INFEASIBLE, WW_ERR_TIMEOUT,
- * WW_ERR_OVERFLOW, WW_ERR_INTERNAL).  The host drives the pass loop, so the
- * call returns when the solve has finished (the stream is synchronised); the
- * returned status equals *dev_status. */
+ * WW_ERR_OVERFLOW, WW_ERR_INTERNAL).  The pass loop runs on the device inside
+ * one CUDA graph launch (params->graph_loop = 1, the default) or is driven by
+ * the host with one stream synchronisation per pass (graph_loop = 0); either
+ * way the call returns when the solve has finished (the stream is
+ * synchronised) and the returned status equals *dev_status.  On
+ * WW_ERR_TIMEOUT (pass limit or worklist wait limit) flows and potentials hold
+ * the state after the last complete pass: every residual arc has a
+ * non-negative reduced cost, and ww_solve_mcf_resume continues from it. */
 ww_status ww_solve_mcf(const int8_t* residues, const int32_t* ground, const int16_t* costs,
                        int64_t m, int64_t n, const ww_params* params, ww_workspace* ws,
                        int8_t* flows, int64_t* potentials, int64_t* total_cost,
                        int32_t* dev_status, ww_stream stream);
+
+/* Continue a solve from given flows and potentials (checkpoint/resume; the
+ * paper's solver has no counterpart).  flows (IN/OUT, [2][m][n], |dk| <= 1)
+ * and potentials (IN/OUT, (m-1)(n-1)+1, ground last) are typically what an
+ * earlier ww_solve_mcf or ww_solve_mcf_resume returned with WW_ERR_TIMEOUT, or
+ * a copy of them saved to host memory and loaded back.  Any pair in which
+ * every residual arc has a non-negative reduced cost (c - p(tail) + p(head) >= 0)
+ * is accepted: the imbalance left by the flows is then routed by successive
+ * shortest paths exactly as in ww_solve_mcf, so the result is an optimum of
+ * Eq. 2 with its certificate.  The pair is checked on the device first; a pair
+ * with |dk| > 1, flow on a missing edge or a negative reduced cost returns
+ * WW_ERR_INVALID_ARG without changing it.  Synchronises the stream. */
+ww_status ww_solve_mcf_resume(const int8_t* residues, const int32_t* ground, const int16_t* costs,
+                              int64_t m, int64_t n, const ww_params* params, ww_workspace* ws,
+                              int8_t* flows, int64_t* potentials, int64_t* total_cost,
+                              int32_t* dev_status, ww_stream stream);
 
 /* Solver statistics of the last ww_solve_mcf on this workspace (host struct). */
 typedef struct ww_solve_stats {
@@ -193,6 +221,7 @@ typedef struct ww_solve_stats {
   int64_t visit_cycles;  /* SM clock cycles summed over tile visits */
   int64_t load_cycles;   /* of which: loading labels and computing reduced arc costs */
   int64_t relax_cycles;  /* of which: the local fixed point (directional scans) */
+  int64_t settled_visits; /* nodes reached (finite label) at the end of a tile visit, summed over visits */
 } ww_solve_stats;
 ww_status ww_get_solve_stats(const ww_workspace* ws, ww_solve_stats* out);
 
@@ -210,6 +239,14 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
                     const uint8_t* mask, int64_t m, int64_t n, const ww_params* params,
                     ww_workspace* ws, float* unwrapped, int32_t* cycles, int64_t* total_cost,
                     ww_stream stream);
+
+/* Device arrays the last ww_unwrap on this workspace solved and certified
+ * with: residues ((m-1)(n-1)), ground charge (1), cost planes ([4][m][n]),
+ * flows ([2][m][n]) and potentials ((m-1)(n-1)+1), laid out for that call's
+ * m x n.  They are workspace memory: valid until the next call that uses the
+ * workspace, not to be freed.  Any output pointer may be NULL. */
+ww_status ww_workspace_last_unwrap(const ww_workspace* ws, const int8_t** residues, const int32_t** ground,
+                                   const int16_t** costs, const int8_t** flows, const int64_t** potentials);
 
 /* ---- Connected-component labels (Sec. II-D) ----
  * After unwrapping, a pixel edge is reliable when both of its pixels are
@@ -294,16 +331,21 @@ ww_status ww_autotune_batch(ww_batch_item* items, int64_t count, const ww_params
  * flight, so new requests join while others are on the GPU.  A request's device
  * buffers (ww_batch_item fields) must hold their inputs when it is submitted
  * and stay valid until it completes.  Requests larger than max_request_pixels
- * or than the budget are rejected at submit (WW_ERR_INVALID_ARG). */
+ * or than the budget are rejected at submit (WW_ERR_INVALID_ARG).
+ * Every device allocation of the server (request state, batch tables, solver
+ * state) is counted against hbm_budget_bytes: the server sizes its pools to
+ * the largest that fits, and ww_server_create returns WW_ERR_INVALID_ARG when
+ * the budget cannot hold one request of max_request_pixels. */
 typedef struct ww_server_config {
-  int64_t hbm_budget_bytes;   /* device memory for resident request state */
+  int64_t hbm_budget_bytes;   /* all device memory the server may allocate */
   int64_t max_request_pixels; /* largest request accepted */
   int32_t max_active;         /* requests in flight at once */
   int32_t reserved[7];
 } ww_server_config;
 typedef struct ww_server ww_server;
 typedef struct ww_server_stats {
-  int64_t submitted, admitted, completed, rejected, passes, peak_active, peak_resident_bytes;
+  int64_t submitted, admitted, completed, rejected, passes, peak_active;
+  int64_t peak_resident_bytes;  /* device bytes the server allocated (<= hbm_budget_bytes) */
   double busy_ms;
 } ww_server_stats;
 ww_status ww_server_create(const ww_server_config* cfg, const ww_params* params, ww_server** out);

@@ -41,8 +41,7 @@ class WWError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("box_half_width", ctypes.c_int32), ("steep_rad", ctypes.c_float),
                 ("steep_cap_ppm", ctypes.c_int32), ("max_passes", ctypes.c_int32),
-                ("max_sweeps", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-                ("radius_policy", ctypes.c_int32), ("graph_loop", ctypes.c_int32),
+                ("wait_polls", ctypes.c_int32), ("graph_loop", ctypes.c_int32),
                 ("search_ctas_per_sm", ctypes.c_int32), ("band_min", ctypes.c_int32),
                 ("band_mult", ctypes.c_int32), ("band_growth", ctypes.c_int32),
                 ("band_start_ppm", ctypes.c_int32), ("full_passes", ctypes.c_int32),
@@ -57,7 +56,7 @@ class SolveStats(ctypes.Structure):
                 ("ms_search", ctypes.c_double), ("ms_other", ctypes.c_double),
                 ("ms_search_gpu", ctypes.c_double), ("local_rounds", ctypes.c_int64),
                 ("visit_cycles", ctypes.c_int64), ("load_cycles", ctypes.c_int64),
-                ("relax_cycles", ctypes.c_int64)]
+                ("relax_cycles", ctypes.c_int64), ("settled_visits", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -111,7 +110,9 @@ def lib():
         L.ww_costs.argtypes = [P, i32, P, P, i64, i64, P, ctypes.POINTER(Params), P, P, P]
         L.ww_costs_noalloc.argtypes = [P, i32, P, P, i64, i64, P, ctypes.POINTER(Params), P, P]
         L.ww_solve_mcf.argtypes = [P, P, P, i64, i64, ctypes.POINTER(Params), P, P, P, P, P, P]
+        L.ww_solve_mcf_resume.argtypes = [P, P, P, i64, i64, ctypes.POINTER(Params), P, P, P, P, P, P]
         L.ww_get_solve_stats.argtypes = [P, ctypes.POINTER(SolveStats)]
+        L.ww_workspace_last_unwrap.argtypes = [P] + [ctypes.POINTER(P)] * 5
         L.ww_integrate.argtypes = [P, i32, P, P, P, i64, i64, P, P, P]
         L.ww_unwrap.argtypes = [P, i32, P, d, P, i64, i64, ctypes.POINTER(Params), P, P, P,
                                 ctypes.POINTER(i64), P]
@@ -135,7 +136,8 @@ def lib():
         L.ww_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
         L.ww_server_destroy.argtypes = [P]
         for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
-                  "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_get_solve_stats", "ww_integrate", "ww_unwrap",
+                  "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_solve_mcf_resume", "ww_get_solve_stats",
+                  "ww_workspace_last_unwrap", "ww_integrate", "ww_unwrap",
                   "ww_certificate", "ww_components", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_autotune_batch",
                   "ww_server_create",
                   "ww_server_submit", "ww_server_poll", "ww_server_wait", "ww_server_release", "ww_server_get_stats"):
@@ -227,6 +229,19 @@ class Workspace:
         s = SolveStats()
         _check(lib().ww_get_solve_stats(self._h, ctypes.byref(s)), "ww_get_solve_stats")
         return s.as_dict()
+
+    def certify_last_unwrap(self, m: int, n: int):
+        """GPU certificate counts of the last ww_unwrap on this workspace (an m x n
+        image): (capacity violations, conservation violations, negative reduced
+        costs, total cost), on exactly the arrays that call solved with."""
+        torch = _torch()
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        _check(lib().ww_workspace_last_unwrap(self._h, *[ctypes.byref(p) for p in ptrs]), "ww_workspace_last_unwrap")
+        counts = torch.zeros(4, dtype=torch.int64, device="cuda")
+        res, g, costs, flows, pot = ptrs
+        _check(lib().ww_certificate(res, g, costs, flows, pot, int(m), int(n), _ptr(counts), _stream()),
+               "ww_certificate")
+        return tuple(int(x) for x in counts.cpu())
 
     def close(self):
         if self._h:
@@ -320,6 +335,21 @@ def solve_mcf(res, ground, cost_planes, ws: Workspace, params: Params | None = N
     if check:
         _check(status, "ww_solve_mcf")
     return flows, pot, tc, status
+
+
+def solve_mcf_resume(res, ground, cost_planes, ws: Workspace, flows, pot, params: Params | None = None,
+                     check=True):
+    """Continue a solve from (flows, potentials), updated in place -> (total_cost int64 [1], status int)."""
+    torch = _torch()
+    _, m, n = cost_planes.shape
+    tc = torch.empty(1, dtype=torch.int64, device=cost_planes.device)
+    st = torch.empty(1, dtype=torch.int32, device=cost_planes.device)
+    prm = params or default_params()
+    status = lib().ww_solve_mcf_resume(_ptr(res), _ptr(ground), _ptr(cost_planes), m, n, ctypes.byref(prm),
+                                       ws.handle, _ptr(flows), _ptr(pot), _ptr(tc), _ptr(st), _stream())
+    if check:
+        _check(status, "ww_solve_mcf_resume")
+    return tc, status
 
 
 def integrate(ifg, flows, coh=None, mask=None):

@@ -21,9 +21,22 @@ struct LutData {
   bool has_cost100 = false;
   std::mutex mu;
   int16_t* dev[64] = {nullptr};
+  // page-locked copy of `table`, made once when the table is built (null where no
+  // device is available); uploads from it are asynchronous and can be captured
+  int16_t* pinned = nullptr;
+  void make_pinned() {
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(table), cudaHostAllocDefault) == cudaSuccess) {
+      std::memcpy(p, table, sizeof(table));
+      pinned = static_cast<int16_t*>(p);
+    } else {
+      cudaGetLastError();
+    }
+  }
   ~LutData() {
     for (auto* p : dev)
       if (p) cudaFree(p);
+    if (pinned) cudaFreeHost(pinned);
   }
 };
 
@@ -51,7 +64,7 @@ bool params_ok(const ww_params* p) { return ww::params_valid(p); }
 
 bool ww::params_valid(const ww_params* p) {
   return p && p->box_half_width >= 0 && p->box_half_width <= 3 && p->steep_cap_ppm >= 0 &&
-         p->steep_cap_ppm <= 1000000 && p->max_passes > 0 && p->max_sweeps > 0 && std::isfinite(p->steep_rad) &&
+         p->steep_cap_ppm <= 1000000 && p->max_passes > 0 && p->wait_polls > 0 && std::isfinite(p->steep_rad) &&
          (p->graph_loop == 0 || p->graph_loop == 1) && p->search_ctas_per_sm >= 0 && p->search_ctas_per_sm <= 64 &&
          p->band_min >= 1 && p->band_mult >= 0 && p->band_mult <= 1024 && p->band_growth >= 2 &&
          p->band_growth <= 64 && p->band_start_ppm >= 0 && p->band_start_ppm <= 1000000 && p->full_passes >= 0 &&
@@ -87,6 +100,8 @@ const int16_t* lut_device_table(const ww_lut* lut, cudaStream_t, ww_status* st) 
 
 const int16_t* lut_host_table(const ww_lut* lut) { return data_of(lut)->table; }
 
+const int16_t* lut_pinned_table(const ww_lut* lut) { return data_of(lut)->pinned; }
+
 }  // namespace ww
 
 extern "C" {
@@ -113,9 +128,7 @@ void ww_params_default(ww_params* p) {
   p->steep_rad = 1.0f;
   p->steep_cap_ppm = 30000;
   p->max_passes = 100000;
-  p->max_sweeps = 1000000;
-  p->tile_rows = 0;
-  p->radius_policy = 0;
+  p->wait_polls = 1 << 25;
   p->graph_loop = 1;
   p->search_ctas_per_sm = 0;
   p->band_min = 1024;
@@ -142,6 +155,7 @@ ww_status ww_build_lut(double nlooks, ww_lut** out) {
     int st = ww::lut_build_host(nlooks, nd->table, nd->cost100);
     if (st != WW_OK) return st;
     nd->has_cost100 = true;
+    nd->make_pinned();
     std::lock_guard<std::mutex> g(g_cache_mu);
     auto it = g_cache.find(key_of(nlooks));
     if (it != g_cache.end())
@@ -162,6 +176,7 @@ ww_status ww_lut_from_table(double nlooks, const int16_t* host_table, ww_lut** o
   auto d = std::make_shared<LutData>();
   d->nlooks = nlooks;
   std::memcpy(d->table, host_table, sizeof(d->table));
+  d->make_pinned();
   ww_lut* l = new (std::nothrow) ww_lut;
   if (!l) return WW_ERR_OOM;
   l->nlooks = nlooks;
@@ -279,6 +294,30 @@ ww_status ww_solve_mcf(const int8_t* residues, const int32_t* ground, const int1
   return ww::solve_problems(&ph, 1, &ws->sv, p, potentials, &ws->stats, (cudaStream_t)stream);
 }
 
+ww_status ww_solve_mcf_resume(const int8_t* residues, const int32_t* ground, const int16_t* costs, int64_t m,
+                              int64_t n, const ww_params* params, ww_workspace* ws, int8_t* flows,
+                              int64_t* potentials, int64_t* total_cost, int32_t* dev_status, ww_stream stream) {
+  ww_params def;
+  ww_params_default(&def);
+  const ww_params* p = params ? params : &def;
+  if (!residues || !ground || !costs || !flows || !potentials || !total_cost || !dev_status || !grid_ok(m, n) ||
+      !params_ok(p) || !fits(ws, m, n))
+    return WW_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the given pair must be a valid starting point: capacities, and no residual
+  // arc of negative reduced cost (conservation is what the solve restores)
+  int64_t* counts = ws->total_cost;  // 8 int64 of workspace scratch
+  ww_status st = ww::launch_certificate(residues, ground, costs, flows, potentials, m, n, counts, s);
+  if (st != WW_OK) return st;
+  int64_t h[4] = {0, 0, 0, 0};
+  WW_CUDA_TRY(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
+  WW_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h[0] != 0 || h[2] != 0) return WW_ERR_INVALID_ARG;
+  ww::ProbHost ph{m, n, residues, ground, costs, flows, nullptr, total_cost, dev_status};
+  ph.resume = true;
+  return ww::solve_problems(&ph, 1, &ws->sv, p, potentials, &ws->stats, s);
+}
+
 ww_status ww_get_solve_stats(const ww_workspace* ws, ww_solve_stats* out) {
   if (!ws || !out) return WW_ERR_INVALID_ARG;
   *out = ws->stats;
@@ -339,6 +378,17 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
   if (cudaStreamSynchronize(s) != cudaSuccess) st = WW_ERR_CUDA;
   ww_lut_free(lut);
   return st;
+}
+
+ww_status ww_workspace_last_unwrap(const ww_workspace* ws, const int8_t** residues, const int32_t** ground,
+                                   const int16_t** costs, const int8_t** flows, const int64_t** potentials) {
+  if (!ws) return WW_ERR_INVALID_ARG;
+  if (residues) *residues = ws->residues;
+  if (ground) *ground = ws->ground;
+  if (costs) *costs = ws->costs;
+  if (flows) *flows = ws->flows;
+  if (potentials) *potentials = ws->potentials;
+  return WW_OK;
 }
 
 ww_status ww_certificate(const int8_t* residues, const int32_t* ground, const int16_t* costs, const int8_t* flows,

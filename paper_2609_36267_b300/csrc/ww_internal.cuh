@@ -202,6 +202,9 @@ struct ProbHost {
   int64_t* pot_out;
   int64_t* total_cost;
   int32_t* status;
+  // start from the flows already in `flows` and the potentials already in the
+  // solver's potential array (single problem with the caller's potentials only)
+  bool resume = false;
 };
 }  // namespace ww
 
@@ -241,6 +244,8 @@ int lut_build_host(double nlooks, int16_t* table, double* cost100);
 // ww_api.cu
 const int16_t* lut_device_table(const ww_lut* lut, cudaStream_t stream, ww_status* st);
 const int16_t* lut_host_table(const ww_lut* lut);
+// page-locked copy of the host table, or null if it could not be made
+const int16_t* lut_pinned_table(const ww_lut* lut);
 // ww_grid.cu
 ww_status launch_residues(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                           int64_t m, int64_t n, int8_t* res, int32_t* ground, cudaStream_t s);
@@ -311,7 +316,8 @@ struct McfCtr;
 // All problems share the free ground node (potential at pot[g_index]).
 class Session {
  public:
-  Session(SolverWs* sv, int64_t* pot, int64_t g_index, const ww_params* prm, cudaStream_t s);
+  Session(SolverWs* sv, int64_t* pot, int64_t g_index, const ww_params* prm, cudaStream_t s,
+          bool keep_ground_pot = false);
   int next_slot() const;                                            // slot the next add() takes, -1 if full
   int add(const ProbHost& ph, int64_t node_off, int64_t tile_off);  // -> slot, or -1 if full
   void remove(int slot);

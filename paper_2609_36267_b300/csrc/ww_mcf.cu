@@ -67,6 +67,8 @@ struct ProbDev {
   int64_t* pot_out;      // caller's potentials (N + 1) or nullptr when pot is the caller's array
   int64_t* total_cost;   // device int64
   int32_t* status;       // device int32
+  int32_t resume;        // start from the flows in `flows` (and the caller's potentials), not from zero
+  int32_t resume_pad;
 };
 
 struct McfCtr {
@@ -97,6 +99,7 @@ struct McfCtr {
   long long aug_total; // augmentations over all passes
   uint32_t band_min, band_mult, band_growth, band_start_ppm, full_passes;  // search schedule
   unsigned long long load_cycles, relax_cycles;              // phases of the tile visits
+  unsigned long long settled_visits;  // nodes holding a finite label at the end of a tile visit, summed
   // ground as a sink (late passes): the ground is no root; it is reached through
   // border arcs at distance dG, and augmentation is limited to distance <= dG
   int32_t gsink;
@@ -114,7 +117,7 @@ struct McfCtr {
   long long dbg_node, dbg_red;
   int32_t dbg_pass, dbg_pad;
   int32_t ntouched;    // tiles listed as visited in this pass
-  int32_t ntouched_pad;
+  uint32_t wait_polls; // polls of a worklist wait before it gives up (WW_ERR_TIMEOUT)
 };
 
 // Problems live in slots (stable ids); `order` lists the active slots sorted by
@@ -181,18 +184,18 @@ struct SearchQ {
   int32_t head, tail, pending, pad;
 };
 
-constexpr int kSpinLimit = 1 << 25;  // idle polls (~100 ns each) before giving up
-
+// Every wait polls at most `limit` times (ww_params.wait_polls, default 2^25
+// polls of ~100-200 ns, seconds in all); running out is reported as an error.
 __device__ __forceinline__ int ld_volatile(const int32_t* p) { return *((volatile const int32_t*)p); }
 
 // Returns false if the slot stayed occupied past the wait limit (reported as an error).
-__device__ __forceinline__ bool q_push(int tile, int ring, SearchQ* q, int32_t* slots, int32_t* inq) {
+__device__ __forceinline__ bool q_push(int tile, int ring, SearchQ* q, int32_t* slots, int32_t* inq, uint32_t limit) {
   if (atomicExch(&inq[tile], 1) != 0) return true;
   atomicAdd(&q->pending, 1);
   int pos = atomicAdd(&q->tail, 1);
   __threadfence();
   int* slot = &slots[pos % ring];
-  for (int spin = 0; spin < kSpinLimit; ++spin) {
+  for (uint32_t spin = 0; spin < limit; ++spin) {
     if (atomicCAS(slot, 0, tile + 1) == 0) return true;
     __nanosleep(100);
   }
@@ -200,10 +203,10 @@ __device__ __forceinline__ bool q_push(int tile, int ring, SearchQ* q, int32_t* 
 }
 
 // Returns a tile, -1 when the search has converged, -2 on a bounded-wait timeout.
-__device__ int q_pop(int ring, SearchQ* q, int32_t* slots, int32_t* inq) {
+__device__ int q_pop(int ring, SearchQ* q, int32_t* slots, int32_t* inq, uint32_t limit) {
   const int h = atomicAdd(&q->head, 1);
   int* slot = &slots[h % ring];
-  for (int spin = 0; spin < kSpinLimit; ++spin) {
+  for (uint32_t spin = 0; spin < limit; ++spin) {
     int v = ld_volatile(slot);
     if (v != 0) {
       atomicExch(slot, 0);
@@ -320,13 +323,14 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
   const uint64_t capK = (ctr->zstop != 0 && cap == 1u) ? (uint64_t)ctr->zero_hops
                         : (cap == 0xFFFFFFFFu ? KINF : ((uint64_t)cap << 29));
   const bool gsink = ctr->gsink != 0;
+  const uint32_t wait_polls = ctr->wait_polls;
   int err = 0;
   if (tid == 0) {
     rowdirty_next = 0;
     coldirty_next = 0;
   }
   for (;;) {
-    if (tid == 0) s_tile = q_pop(ring, q, slots, inq);
+    if (tid == 0) s_tile = q_pop(ring, q, slots, inq, wait_polls);
     __syncthreads();
     const int tile = s_tile;
     if (tile < 0) {
@@ -523,12 +527,14 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       if (rowdirty == 0) break;
     }
     const long long t_relaxed = clock64();
-    // write back and note which tile sides changed
+    // write back and note which tile sides changed; count the reached nodes
+    unsigned reached = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       int ly = warp + 8 * k;
       int64_t i = i0 + ly, j = j0 + lane;
       uint64_t v = lab[ly + 1][lane + 1];
+      reached += __popc(__ballot_sync(0xffffffffu, i < p.R && j < p.C && v != kInf));
       if (i < p.R && j < p.C && v != orig[k]) {
         // the same tile may be in process in two CTAs (it can be re-queued
         // while in flight); atomicMin keeps every label monotone
@@ -539,6 +545,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
         if (lane == TS - 1) side[3] = 1;
       }
     }
+    if (lane == 0 && reached) atomicAdd(&ctr->settled_visits, (unsigned long long)reached);
     if (__syncthreads_or(capped) && tid == 0) {
       capped_flag[tile] = 1;
       ctr->capped_any = 1;
@@ -547,10 +554,10 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
     __syncthreads();
     if (tid == 0) {
       bool ok = true;
-      if (side[0] && ti > 0) ok &= q_push(tile - p.tiles_x, ring, q, slots, inq);
-      if (side[1] && ti + 1 < p.tiles_y) ok &= q_push(tile + p.tiles_x, ring, q, slots, inq);
-      if (side[2] && tj > 0) ok &= q_push(tile - 1, ring, q, slots, inq);
-      if (side[3] && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq);
+      if (side[0] && ti > 0) ok &= q_push(tile - p.tiles_x, ring, q, slots, inq, wait_polls);
+      if (side[1] && ti + 1 < p.tiles_y) ok &= q_push(tile + p.tiles_x, ring, q, slots, inq, wait_polls);
+      if (side[2] && tj > 0) ok &= q_push(tile - 1, ring, q, slots, inq, wait_polls);
+      if (side[3] && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq, wait_polls);
       if (!ok) err |= kErrSpin;
       atomicAdd(&ctr->tile_visits, 1ull);
       atomicAdd(&ctr->local_rounds, (unsigned long long)(round + 1));
@@ -583,11 +590,21 @@ __global__ void k_init_state(Batch b, const int32_t* slots, int32_t* excess, int
   const ProbDev& p = b.probs[slot];
   const int64_t pg = pot[b.g_index];
   int32_t* cand = cand_cur(cand_base, ctr, ctr->n_cap_nodes);
+  const int64_t P = p.m * p.n;
   int cnt = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.N; v += (int64_t)gridDim.x * blockDim.x) {
     int32_t r = p.res[v];
+    if (p.resume) {
+      // imbalance left by the given flows: supply minus net outflow of node (i, j),
+      // whose four edges are h(i,j) [above], h(i+1,j) [below], v(i,j) [left], v(i,j+1)
+      const int64_t i = v / p.C, j = v - (v / p.C) * p.C;
+      const int net = (int)p.flows[(i + 1) * p.n + j] - (int)p.flows[i * p.n + j] + (int)p.flows[P + i * p.n + j] -
+                      (int)p.flows[P + i * p.n + j + 1];
+      r -= net;
+    } else {
+      pot[p.node_off + v] = pg;
+    }
     excess[p.node_off + v] = r;
-    pot[p.node_off + v] = pg;
     labels[p.node_off + v] = kInf;
     if (r != 0) {
       cand[atomicAdd(&ctr->ncand, 1)] = (int32_t)(p.node_off + v);
@@ -669,17 +686,18 @@ __global__ void k_seed_tiles(Batch b, const int32_t* excess, int32_t* cand_base,
       // reports it as changed: a root on a tile edge also seeds the tile across
       // that edge, which reads it as halo
       bool ok = true;
-      if (i % TS == 0 && ti > 0) ok &= q_push(tile - p.tiles_x, ring, q, slots, inq);
-      if (i % TS == TS - 1 && ti + 1 < p.tiles_y) ok &= q_push(tile + p.tiles_x, ring, q, slots, inq);
-      if (j % TS == 0 && tj > 0) ok &= q_push(tile - 1, ring, q, slots, inq);
-      if (j % TS == TS - 1 && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq);
+      const uint32_t lim = ctr->wait_polls;
+      if (i % TS == 0 && ti > 0) ok &= q_push(tile - p.tiles_x, ring, q, slots, inq, lim);
+      if (i % TS == TS - 1 && ti + 1 < p.tiles_y) ok &= q_push(tile + p.tiles_x, ring, q, slots, inq, lim);
+      if (j % TS == 0 && tj > 0) ok &= q_push(tile - 1, ring, q, slots, inq, lim);
+      if (j % TS == TS - 1 && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq, lim);
       if (!ok) atomicOr(&ctr_err(ctr), kErrSpin);
     } else {
       if (ctr->gsink) continue;  // the ground is no root in this pass
       tile = border[k - nc];
       if (prob_left[b.tile_prob[tile]] == 0) continue;
     }
-    if (!q_push(tile, ring, q, slots, inq)) atomicOr(&ctr_err(ctr), kErrSpin);
+    if (!q_push(tile, ring, q, slots, inq, ctr->wait_polls)) atomicOr(&ctr_err(ctr), kErrSpin);
   }
 }
 
@@ -706,7 +724,7 @@ __global__ void k_count_found(const int32_t* excess, const uint64_t* labels, int
 // is over.  Runs on one thread.
 __global__ void k_band_decide(McfCtr* ctr, SearchQ* q, int last_band) {
   if (!ctr->band_again) return;
-  bool again = ctr->cap != 0xFFFFFFFFu && ctr->found == 0 && ctr->capped_any;
+  bool again = ctr->cap != 0xFFFFFFFFu && ctr->found == 0 && ctr->capped_any && ctr->err == 0;
   if (again) {
     const unsigned long long w = (unsigned long long)ctr->cap * ctr->band_growth;
     if (ctr->zstop && ctr->cap == 1u) {
@@ -730,7 +748,7 @@ __global__ void k_reseed(Batch b, int32_t* capped_flag, SearchQ* q, int32_t* slo
        t += (int64_t)gridDim.x * blockDim.x) {
     if (capped_flag[t]) {
       capped_flag[t] = 0;
-      if (!q_push((int)t, ring, q, slots, inq)) atomicOr(&ctr->err, kErrSpin);
+      if (!q_push((int)t, ring, q, slots, inq, ctr->wait_polls)) atomicOr(&ctr->err, kErrSpin);
     }
   }
 }
@@ -836,7 +854,7 @@ __device__ __forceinline__ uint32_t ground_vid(const ProbDev& p, int64_t k) {
 // away could not augment: the pass radius is at most dG).
 template <bool FWD>
 __global__ void k_select_ground(Batch b, const uint64_t* labels, const int64_t* pot, uint64_t* best, McfCtr* ctr) {
-  if (!ctr->go_on || !ctr->gsink || ctr->dG == 0xFFFFFFFFu) return;
+  if (!ctr->go_on || ctr->err || !ctr->gsink || ctr->dG == 0xFFFFFFFFu) return;
   const ProbDev& p = b.probs[b.order[blockIdx.y]];
   const int64_t na = 2 * (p.C + p.R), pG = pot[b.g_index];
   const uint64_t* plab = labels + p.node_off;
@@ -858,12 +876,17 @@ template <bool FWD>
 __global__ void k_select(Batch b, const int32_t* excess, const uint64_t* labels, int32_t* cand_base,
                          int32_t* cand_root, uint64_t* best, McfCtr* ctr) {
   if (!ctr->go_on) return;
+  // a search that stopped on an error left labels that are not shortest
+  // distances: the pass then augments nothing, so flows and potentials stay
+  // the consistent pair of the last complete pass (a resumable state)
+  const bool aborted = ctr->err != 0;
   const int nc = ctr->ncand;
   const int32_t* cand = cand_cur(cand_base, ctr, b.n_total);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
     int32_t t = cand[q];
     int32_t e = excess[t];
     cand_root[q] = -1;
+    if (aborted) continue;
     if (!(FWD ? e < 0 : e > 0)) continue;
     uint64_t l = labels[t];
     if (l == kInf) continue;
@@ -959,7 +982,7 @@ __global__ void k_reset_best(Batch b, const int32_t* cand_root, uint64_t* best, 
 template <bool FWD>
 __global__ void k_augment_ground(Batch b, int32_t* excess, const uint64_t* labels, const int64_t* pot,
                                  uint64_t* best, long long* g_net, McfCtr* ctr) {
-  if (!ctr->go_on || !ctr->gsink || ctr->dG == 0xFFFFFFFFu) return;
+  if (!ctr->go_on || ctr->err || !ctr->gsink || ctr->dG == 0xFFFFFFFFu) return;
   const int slot = b.order[blockIdx.y];
   const ProbDev& p = b.probs[slot];
   const int64_t na = 2 * (p.C + p.R), pG = pot[b.g_index], P = p.m * p.n;
@@ -1001,7 +1024,7 @@ __global__ void k_augment_ground(Batch b, int32_t* excess, const uint64_t* label
 template <bool FWD>
 __global__ void k_potentials(Batch b, uint64_t* labels, int64_t* pot, int32_t* touched, const int32_t* tlist,
                              const McfCtr* ctr) {
-  const bool apply = ctr->go_on && ctr->naug != 0 && ctr->D != 0;  // D = 0: no node lies below it
+  const bool apply = ctr->go_on && ctr->err == 0 && ctr->naug != 0 && ctr->D != 0;  // D = 0: none below it
   const uint32_t D = ctr->D;
   const int nt = ctr->ntouched;
   for (int k = blockIdx.x; k < nt; k += gridDim.x) {
@@ -1026,7 +1049,7 @@ __global__ void k_potentials(Batch b, uint64_t* labels, int64_t* pot, int32_t* t
 // The ground node is a root of every search (distance 0).
 template <bool FWD>
 __global__ void k_potential_ground(Batch b, int64_t* pot, const McfCtr* ctr) {
-  if (!ctr->go_on || ctr->naug == 0 || ctr->gsink) return;  // a sink ground lies at distance >= D
+  if (!ctr->go_on || ctr->err || ctr->naug == 0 || ctr->gsink) return;  // a sink ground lies at distance >= D
   pot[b.g_index] += FWD ? (int64_t)ctr->D : -(int64_t)ctr->D;
 }
 
@@ -1247,11 +1270,22 @@ __global__ void k_join(const ProbDev* probs, const int32_t* slots, int32_t* tile
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t0 == 0) {
     prob_left[slot] = 0;
-    g_net[slot] = 0;
     tc[slot] = 0;
   }
   const int64_t nt = (int64_t)p.tiles_x * p.tiles_y;
   for (int64_t t = t0; t < nt; t += stride) tile_prob[p.tile_off + t] = slot;
+  if (p.resume) {
+    // keep the given flows; the ground's net outflow so far is read off its arcs
+    // (first and last pixel row of h, first and last column of v)
+    long long gn = 0;
+    for (int64_t j = t0; j < p.C; j += stride)
+      gn += (long long)p.flows[j] - (long long)p.flows[(p.m - 1) * p.n + j];
+    for (int64_t i = t0; i < p.R; i += stride)
+      gn += (long long)p.flows[p.m * p.n + i * p.n + p.n - 1] - (long long)p.flows[p.m * p.n + i * p.n];
+    for (int o = 16; o > 0; o >>= 1) gn += __shfl_xor_sync(0xffffffffu, gn, o);
+    if ((threadIdx.x & 31) == 0 && gn) atomicAdd((unsigned long long*)&g_net[slot], (unsigned long long)gn);
+    return;
+  }
   // flows, 2 m n bytes: unaligned head, 16-byte words, tail
   uint8_t* f = reinterpret_cast<uint8_t*>(p.flows);
   const int64_t nb = 2 * p.m * p.n;
@@ -1263,6 +1297,11 @@ __global__ void k_join(const ProbDev* probs, const int32_t* slots, int32_t* tile
   for (int64_t k = head + 16 * nw + t0; k < nb; k += stride) f[k] = 0;
 }
 
+// Per-slot counters a join starts from (before k_join, which adds to g_net on a resume).
+__global__ void k_join_clear(const int32_t* slots, int count, long long* g_net) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) g_net[slots[q]] = 0;
+}
+
 // After membership changes: go on if anything is imbalanced.
 __global__ void k_resume(McfCtr* ctr, int64_t n_total) {
   ctr->n_total = n_total;
@@ -1272,7 +1311,8 @@ __global__ void k_resume(McfCtr* ctr, int64_t n_total) {
 
 }  // namespace
 
-Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params* prm, cudaStream_t s)
+Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params* prm, cudaStream_t s,
+                 bool keep_ground_pot)
     : sv(sv_), pot(pot_), g_index(g_index_), stream(s) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1293,8 +1333,17 @@ Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params
   hc->ground_sink_below = (uint32_t)std::max(0, prm->ground_sink_below);
   hc->zero_stop_below = (uint32_t)std::max(0, prm->zero_stop_below);
   hc->zero_hops = (uint32_t)std::max(1, std::min(prm->zero_band_hops, (1 << 29) - 1));
+  hc->wait_polls = (uint32_t)std::max(1, prm->wait_polls);
+  // the worklist flags and ring start empty (a search that stopped on an error
+  // may have left entries behind); the ground potential starts at 0 unless a
+  // resumed solve brings its own
+  const int64_t ring = sv->t_cap + kMaxSearchGrid + 64;
   err = cudaMemcpyAsync(sv->ctr, hc, sizeof(McfCtr), cudaMemcpyHostToDevice, s) == cudaSuccess &&
-                cudaMemsetAsync(pot + g_index, 0, 8, s) == cudaSuccess
+                cudaMemsetAsync(sv->inq, 0, sv->t_cap * 4, s) == cudaSuccess &&
+                cudaMemsetAsync(sv->slots, 0, ring * 4, s) == cudaSuccess &&
+                cudaMemsetAsync(sv->capped, 0, sv->t_cap * 4, s) == cudaSuccess &&
+                cudaMemsetAsync(sv->touched, 0, sv->t_cap * 4, s) == cudaSuccess &&
+                (keep_ground_pot || cudaMemsetAsync(pot + g_index, 0, 8, s) == cudaSuccess)
             ? WW_OK
             : WW_ERR_CUDA;
 }
@@ -1324,6 +1373,7 @@ int Session::add(const ProbHost& ph, int64_t node_off, int64_t tile_off) {
   d.pot_out = ph.pot_out;
   d.total_cost = ph.total_cost;
   d.status = ph.status;
+  d.resume = ph.resume ? 1 : 0;
   used[slot] = 1;
   pending.push_back(slot);
   return slot;
@@ -1395,6 +1445,7 @@ ww_status Session::commit() {
     std::copy(pending.begin(), pending.end(), h_join);
     WW_CUDA_TRY(cudaMemcpyAsync(sv->slot_list, h_join, pending.size() * 4, cudaMemcpyHostToDevice, s));
     dim3 gi(grid_blocks(biggest, 256, std::max(1, sm_count * 16 / (int)pending.size() + 1)), (unsigned)pending.size());
+    k_join_clear<<<1, 256, 0, s>>>(sv->slot_list, (int)pending.size(), sv->g_net);
     k_join<<<gi, 256, 0, s>>>(reinterpret_cast<const ProbDev*>(sv->probs), sv->slot_list, sv->tile_prob,
                               sv->prob_left, sv->g_net, sv->tc);
     k_init_state<<<gi, 256, 0, s>>>(batch(), sv->slot_list, sv->excess, sv->cand, pot, sv->labels, sv->prob_left,
@@ -1565,6 +1616,7 @@ void Session::fill_stats(ww_solve_stats* st) const {
   st->visit_cycles = (int64_t)hc->visit_cycles;
   st->load_cycles = (int64_t)hc->load_cycles;
   st->relax_cycles = (int64_t)hc->relax_cycles;
+  st->settled_visits = (int64_t)hc->settled_visits;
 }
 
 int64_t Session::ctr_bytes() const { return (int64_t)sizeof(McfCtr); }
@@ -1650,7 +1702,11 @@ ww_status solve_problems(const ProbHost* ph, int nprob, SolverWs* sv, const ww_p
   int64_t* pot = pot_global ? pot_global : sv->pot;
   const auto t_setup = std::chrono::steady_clock::now();
   const int64_t g_index = pot_global ? (ph[0].m - 1) * (ph[0].n - 1) : sv->n_cap;
-  Session S(sv, pot, g_index, prm, s);
+  // a resumed single problem keeps its potentials, the ground's included
+  if (!pot_global)
+    for (int k = 0; k < nprob; ++k)
+      if (ph[k].resume) return WW_ERR_INVALID_ARG;
+  Session S(sv, pot, g_index, prm, s, pot_global && ph[0].resume);
   if (S.err != WW_OK) return S.err;
   int64_t node_off = 0, tile_off = 0;
   std::vector<int> all;

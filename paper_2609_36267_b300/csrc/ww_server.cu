@@ -72,9 +72,16 @@ struct Request {
   ww_lut* lut = nullptr;
 };
 
-// bytes of resident state per pixel: residues 1, costs 8, flows 2, phase 4, and
-// per node excess 4, labels 8, best 8, two list entries 8, root 4, potential 8
-constexpr int64_t kBytesPerPixel = 55;
+// Device bytes a server with room for `pixels` pixels of requests in flight
+// allocates: per pixel residues 1, costs 8, flows 2, phase 4; per request slot
+// ground, total cost and status; the grid-batch tables (item table, steep
+// counters, selection histograms, tie counts, candidate lists); the solver
+// state (nodes, tiles, problems).  Every cudaMalloc of ww_server_create is counted.
+int64_t server_tiles(int64_t pixels, int32_t max_active) { return pixels / 1024 + pixels / 64 + 4 * max_active + 64; }
+int64_t server_bytes(int64_t pixels, int32_t max_active) {
+  return pixels * (1 + 8 + 2 + 4) + (int64_t)max_active * (4 + 8 + 4) + ww::grid_batch_bytes(max_active, pixels) +
+         ww::solver_bytes(pixels, server_tiles(pixels, max_active), max_active);
+}
 
 }  // namespace
 
@@ -104,6 +111,7 @@ struct ww_server {
   bool stop = false;
   ww_server_stats stats{};
   ww_status fatal = WW_OK;
+  int64_t resident_bytes = 0;  // device bytes allocated at creation (all of it counted against the budget)
 };
 
 namespace {
@@ -313,10 +321,24 @@ ww_status ww_server_create(const ww_server_config* cfg, const ww_params* params,
   if (params) S->prm = *params;
   S->prm.max_passes = 1 << 30;
   cudaGetDevice(&S->device);
-  int64_t pixels = cfg->hbm_budget_bytes / kBytesPerPixel;
-  pixels = std::min<int64_t>(pixels, (1ll << 31) - (1ll << 22));
-  if (pixels < cfg->max_request_pixels) pixels = cfg->max_request_pixels;
-  const int64_t tiles = pixels / 1024 + pixels / 64 + 4 * cfg->max_active + 64;
+  // the largest pixel pool whose whole allocation fits the budget; a budget that
+  // cannot hold one request of the largest accepted size is refused
+  const int64_t cap_px = (1ll << 31) - (1ll << 22);
+  if (cfg->max_request_pixels > cap_px || server_bytes(cfg->max_request_pixels, cfg->max_active) > cfg->hbm_budget_bytes) {
+    delete S;
+    return WW_ERR_INVALID_ARG;
+  }
+  int64_t lo = cfg->max_request_pixels, hi = std::min<int64_t>(cap_px, cfg->hbm_budget_bytes / 15);
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo + 1) / 2;
+    if (server_bytes(mid, cfg->max_active) <= cfg->hbm_budget_bytes)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const int64_t pixels = lo;
+  const int64_t tiles = server_tiles(pixels, cfg->max_active);
+  S->resident_bytes = server_bytes(pixels, cfg->max_active);
   S->pix.cap = pixels;
   S->node.cap = pixels;
   S->tile.cap = tiles;
@@ -406,7 +428,7 @@ ww_status ww_server_get_stats(ww_server* S, ww_server_stats* out) {
   if (!S || !out) return WW_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(S->mu);
   *out = S->stats;
-  out->peak_resident_bytes = S->pix.cap * kBytesPerPixel;
+  out->peak_resident_bytes = S->resident_bytes;
   return WW_OK;
 }
 

@@ -46,6 +46,10 @@ def test_batch_items_reach_oracle_optimum_alone_and_in_mix():
         unw1, K1, tc1 = ww.unwrap(ifg, coh, L, mask, ws=ws)
         assert tc1 == tc
         Kn = K.cpu().numpy()
+        # optimal flows can tie (Sec. II-C), so the cycle maps alone and in the mix
+        # need not match pixel for pixel: the fraction that does is reported
+        agree = float(np.mean(K1.cpu().numpy() == Kn))
+        print(f"batched item {x.shape}: cost {tc}, K agreement alone vs in the mix {agree:.4f}")
         u = unw.cpu().numpy()
         v = ~np.isnan(u)
         assert np.array_equal(v, ref["valid"].astype(bool))

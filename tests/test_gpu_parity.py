@@ -184,11 +184,60 @@ def test_solve_infeasible_block(ws):
     assert status == ww.WW_ERR_INFEASIBLE
 
 
-def test_solve_pass_limit_times_out(ws):
+def _resume_to_optimum(ref, ws, flows, pot, tc_o):
+    """Continue from (flows, pot) with the default parameters: the optimum with a certificate."""
+    fl, po = to_dev(flows), to_dev(pot)
+    tc, status = ww.solve_mcf_resume(to_dev(ref["res"]), to_dev(np.array([ref["g"]], np.int32)),
+                                     to_dev(ref["costs"]), ws, fl, po, check=False)
+    assert status == ww.WW_OK, ww.status_string(status)
+    assert int(tc.cpu()[0]) == tc_o
+    ok, tc2, why = numpy_certificate(ref["res"], ref["g"], ref["costs"], fl.cpu().numpy(), po.cpu().numpy())
+    assert ok and tc2 == tc_o, why
+
+
+def test_solve_pass_limit_times_out_and_resumes(ws):
+    """A pass limit stops the solve with WW_ERR_TIMEOUT; the flows and potentials
+    it returns are a valid (unbalanced) state that resumes to the optimum."""
     x = synth.config2(m=256, n=256)
     ref = oracle_pipeline(x, golden_table(x.nlooks))
-    status, *_ = solve_and_check(ref, ws, params=ww.default_params(max_passes=1))
+    st_o, _, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+    status, flows, pot, _ = solve_and_check(ref, ws, params=ww.default_params(max_passes=1))
     assert status == ww.WW_ERR_TIMEOUT
+    ok, _, why = numpy_certificate(ref["res"], ref["g"], ref["costs"], flows, pot)
+    assert not ok and why == "conservation"  # capacities and reduced costs hold, supplies not yet routed
+    _resume_to_optimum(ref, ws, flows, pot, tc_o)
+
+
+def test_worklist_wait_limit_times_out_and_resumes(ws):
+    """A device worklist wait that runs out (wait_polls = 1: a search CTA whose
+    worklist slot is still empty gives up at its first poll) ends the search
+    with an error flag; the kernel returns, the pass augments nothing, the solve
+    reports WW_ERR_TIMEOUT, and its state resumes to the optimum.  Nothing traps."""
+    x = synth.config2(m=512, n=512)
+    ref = oracle_pipeline(x, golden_table(x.nlooks))
+    st_o, _, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+    for graph_loop in (0, 1):
+        status, flows, pot, _ = solve_and_check(ref, ws, params=ww.default_params(wait_polls=1, graph_loop=graph_loop))
+        assert status == ww.WW_ERR_TIMEOUT, ww.status_string(status)
+        _resume_to_optimum(ref, ws, flows, pot, tc_o)
+    # the workspace is reusable after the aborted searches
+    status, flows, pot, tc = solve_and_check(ref, ws)
+    assert status == ww.WW_OK and tc == tc_o
+
+
+def test_resume_rejects_an_invalid_starting_pair(ws):
+    """A potential that leaves a residual arc with negative reduced cost is refused
+    before any pass (the flows and potentials are left as given)."""
+    x = synth.config1()
+    ref = oracle_pipeline(x, golden_table(x.nlooks))
+    flows = np.zeros((2,) + ref["costs"].shape[1:], np.int8)
+    pot = np.zeros(ref["res"].size + 1, np.int64)
+    pot[1000] = 10 ** 6
+    fl, po = to_dev(flows), to_dev(pot)
+    tc, status = ww.solve_mcf_resume(to_dev(ref["res"]), to_dev(np.array([ref["g"]], np.int32)),
+                                     to_dev(ref["costs"]), ws, fl, po, check=False)
+    assert status == ww.WW_ERR_INVALID_ARG
+    assert np.array_equal(po.cpu().numpy(), pot) and not fl.cpu().numpy().any()
 
 
 @pytest.mark.parametrize("m,n", [(2, 2), (2, 9), (9, 2), (3, 3), (33, 33), (65, 2)])
@@ -204,6 +253,19 @@ def test_tiny_grids(m, n, ws):
     status, flows, pot, tc = solve_and_check(ref, ws)
     assert status == 0 and tc == tc_o
     assert numpy_certificate(ref["res"], ref["g"], ref["costs"], flows, pot)[0]
+
+
+def test_tall_image_beyond_65535_tile_rows():
+    """An image taller than 65535 tiles of the residue and cost kernels (both use a
+    one-dimensional grid of tiles): residues and cost planes bit-exact."""
+    m, n = 2_100_000, 3
+    x = synth.small_random(91, m, n, lo=0.05, hi=0.9)
+    ifg, coh, mask = device_inputs(x)
+    ref = oracle_pipeline(x, probe_table())
+    r, g = ww.residues(ifg, coh, mask)
+    assert np.array_equal(r.cpu().numpy(), ref["res"]) and int(g.cpu()[0]) == ref["g"]
+    c = ww.costs(ifg, coh, ww.Lut.from_table(x.nlooks, probe_table()), ww.Workspace(m, n), mask)
+    assert np.array_equal(c.cpu().numpy(), ref["costs"])
 
 
 def test_all_masked_and_single_valid_pixel(ws):
@@ -223,17 +285,17 @@ def test_all_masked_and_single_valid_pixel(ws):
 @pytest.mark.parametrize("name", ["cfg1_256", "complex_300x333_mask", "cfg2_512"])
 def test_unwrap_end_to_end(name, ws):
     """Whole path with the library's own table; optimal cost equal to the
-    oracle run on the library's table values (index/gather parity is tested
-    above with the oracle's table), rewrap within 1e-5 rad."""
+    oracle's optimum on the same table values, rewrap within 1e-5 rad."""
     x = cases()[name]()
     ifg, coh, mask = device_inputs(x)
     unw, K, tc = ww.unwrap(ifg, coh, x.nlooks, mask, ws=ws)
     u, Kn = unw.cpu().numpy(), K.cpu().numpy()
-    ref = oracle_pipeline(x, golden_table(x.nlooks))
+    # the oracle on the library's own table (equal to the oracle's tables, see
+    # test_lib_cpu.py, but the solve is compared on exactly what the path used)
     lib_tab = ww.Lut.build(x.nlooks).table()
-    if np.array_equal(lib_tab, golden_table(x.nlooks)):
-        st_o, flows_o, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
-        assert tc == tc_o
+    ref = oracle_pipeline(x, lib_tab)
+    st_o, flows_o, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
+    assert st_o == 0 and tc == tc_o
     v = ~np.isnan(u)
     assert np.array_equal(v, ref["valid"].astype(bool))
     exact = ref["psi"].astype(np.float64) + 2 * np.pi * Kn

@@ -51,6 +51,17 @@ def test_argument_checks_without_device():
     assert lib.ww_workspace_bytes(8192, 9000) > 8192 * 9000 * 20
 
 
+def test_server_refuses_a_budget_below_one_request():
+    """Every device allocation of a server counts against its budget: a budget
+    that cannot hold one request of the largest accepted size is refused before
+    anything is allocated."""
+    cfg = ww.ServerConfig(2 << 20, 1 << 24, 4)
+    h = ctypes.c_void_p()
+    prm = ww.default_params()
+    assert ww.lib().ww_server_create(ctypes.byref(cfg), ctypes.byref(prm), ctypes.byref(h)) == ww.WW_ERR_INVALID_ARG
+    assert not h.value
+
+
 def test_lut_from_table_roundtrip():
     t = (np.arange(128 * 256) % 30000).astype(np.int16).reshape(128, 256)
     lut = ww.Lut.from_table(9.0, t)
