@@ -410,6 +410,7 @@ def run_ours(args, rank, world, local):
         line["gpu_launches"] = launch_count(st, args.steps)
         line["components"] = measure_components(ww, torch, x, ifg, coh, mask, unw, ws, max(3, args.steps), peak,
                                                 peak_kind)
+        line["bridge"] = measure_bridge(ww, torch, unw, 3)
         if world == 1 and args.workload == "earthquake" and not args.no_extras:
             # rows a5 and a6 under the same clock: the batched and served forms vs
             # the plain one-at-a-time solve (the earthquake buffers are freed first)
@@ -457,6 +458,38 @@ def measure_components(ww, torch, x, ifg, coh, mask, unw, ws, steps, peak, peak_
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "bytes_per_pixel": COMPONENTS_BYTES_PER_PIXEL, "traffic": None,
                          "peak_source": peak_kind}}
+
+
+# Bridging (ww_bridge) of the headline scene's unwrapped phase after a river of
+# invalid pixels (a 64-pixel band across the middle, plus a second one along a
+# column) splits it into regions; the regions are given random whole-cycle
+# offsets first, which the bridging removes.  Timed on its own, whole call
+# (labels, sizes, boundary pairs, window medians, offsets, apply).
+def measure_bridge(ww, torch, unw_src, steps):
+    m, n = unw_src.shape
+    base = unw_src.clone()
+    base[m // 2 - 32: m // 2 + 32, :] = float("nan")
+    base[:, n // 3 - 16: n // 3 + 16] = float("nan")
+    region, _, nr = ww.bridge(base.clone())
+    off = torch.randint(-20, 21, (nr,), device=base.device, dtype=torch.int32)
+    shifted = torch.where(region >= 0, base + (2 * np.pi) * off[region.clamp(min=0).long()].float(), base)
+    work = shifted.clone()
+    ww.bridge(work)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        work.copy_(shifted)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, shift, nr = ww.bridge(work)
+        ms.append((time.perf_counter() - t) * 1e3)
+    # the largest region keeps its level; every other region returns to it
+    back = (work - base)[region >= 0] / (2 * np.pi)
+    restored = float((back - back.round()).abs().max().item()) < 1e-3 and \
+        int(torch.unique((back - back[0]).round()).numel()) == 1
+    return {"ms": float(np.median(ms)), "Mpixel_per_s": m * n / (np.median(ms) * 1e-3) / 1e6, "regions": nr,
+            "offsets_removed": bool(restored), "what": "river bands (64 rows, 32 columns) masked, random "
+            "whole-cycle offsets per region, host wall time of the whole call (it synchronises)"}
 
 
 def _dev(x, torch):

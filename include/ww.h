@@ -268,6 +268,32 @@ ww_status ww_workspace_last_unwrap(const ww_workspace* ws, const int8_t** residu
 ww_status ww_components(const int16_t* costs, const int8_t* flows, const float* unwrapped, int64_t m,
                         int64_t n, int32_t threshold, int32_t* labels, ww_stream stream);
 
+/* ---- Bridging of mask-separated regions (Sec. II-D) ----
+ * A mask that separates the valid pixels into several 4-connected regions
+ * leaves their relative 2pi levels undetermined.  The regions are taken in
+ * order of decreasing size (ties: smaller first row-major pixel); each region
+ * after the first attaches to the nearest region already taken through the
+ * closest pair of pixels (squared Euclidean distance; ties: the earlier parent
+ * region, then the smaller parent pixel index, then the smaller child pixel
+ * index).  Across each such edge the offset is
+ * rint((median_parent - median_child) / 2pi) cycles (half to even), each
+ * median taken in FP64 over the unwrapped phase of the endpoint's own region
+ * inside a window x window box centred on the endpoint (the middle value, or
+ * the mean of the two middle values), with the parent's offset already
+ * applied, so offsets propagate from parent to child.  The paper uses 65-pixel
+ * windows.
+ *   unwrapped: DEVICE float32 [m][n], IN/OUT, NaN where invalid (as ww_unwrap
+ *     writes it); valid pixels become (float)((double)phi + 2pi * offset).
+ *   cycles: DEVICE int32 [m][n] or NULL, IN/OUT: offset added to each valid pixel.
+ *   region: DEVICE int32 [m][n] or NULL, OUT: the pixel's region rank (0 =
+ *     largest), -1 where invalid.  shift: DEVICE int32 [m][n] or NULL, OUT: the
+ *     offset applied (0 where invalid).  n_regions: HOST int32 or NULL.
+ * window: odd, 1..127.  Needs m*n < 2^31.  Allocates its scratch (about 16
+ * bytes per pixel) with cudaMalloc and frees it before returning; synchronises
+ * the stream (the size order of the regions is sorted on the host). */
+ww_status ww_bridge(float* unwrapped, int32_t* cycles, int64_t m, int64_t n, int32_t window, int32_t* region,
+                    int32_t* shift, int32_t* n_regions, ww_stream stream);
+
 /* ---- Batched form: many uneven interferograms in one solve ----
  * Each item is one unwrap request (device pointers; outputs unwrapped/cycles are
  * m x n).  All items are solved together: their node grids are independent

@@ -118,6 +118,7 @@ def lib():
                                 ctypes.POINTER(i64), P]
         L.ww_certificate.argtypes = [P, P, P, P, P, i64, i64, P, P]
         L.ww_components.argtypes = [P, P, P, i64, i64, i32, P, P]
+        L.ww_bridge.argtypes = [P, P, i64, i64, i32, P, P, ctypes.POINTER(i32), P]
         L.ww_batch_create.argtypes = [i64, i64, i64, ctypes.POINTER(P)]
         L.ww_batch_free.argtypes = [P]
         L.ww_batch_bytes.argtypes = [i64, i64, i64]
@@ -138,7 +139,7 @@ def lib():
         for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
                   "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_solve_mcf_resume", "ww_get_solve_stats",
                   "ww_workspace_last_unwrap", "ww_integrate", "ww_unwrap",
-                  "ww_certificate", "ww_components", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_autotune_batch",
+                  "ww_certificate", "ww_components", "ww_bridge", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_autotune_batch",
                   "ww_server_create",
                   "ww_server_submit", "ww_server_poll", "ww_server_wait", "ww_server_release", "ww_server_get_stats"):
             getattr(L, f).restype = i32
@@ -373,6 +374,19 @@ def components(cost_planes, flows, unwrapped, threshold: int = 0, out=None):
     _check(lib().ww_components(_ptr(cost_planes), _ptr(flows), _ptr(unwrapped), m, n, int(threshold), _ptr(labels),
                                _stream()), "ww_components")
     return labels
+
+
+def bridge(unwrapped, cycles=None, window: int = 65):
+    """Bridging of mask-separated regions (ww_bridge), in place on `unwrapped`
+    (and `cycles` if given) -> (region int32 [m,n], shift int32 [m,n], regions)."""
+    torch = _torch()
+    m, n = unwrapped.shape
+    region = torch.empty((m, n), dtype=torch.int32, device=unwrapped.device)
+    shift = torch.empty((m, n), dtype=torch.int32, device=unwrapped.device)
+    nr = ctypes.c_int32()
+    _check(lib().ww_bridge(_ptr(unwrapped), _ptr(cycles), m, n, int(window), _ptr(region), _ptr(shift),
+                           ctypes.byref(nr), _stream()), "ww_bridge")
+    return region, shift, nr.value
 
 
 def unwrap(ifg, coh, nlooks: float, mask=None, ws: Workspace | None = None, params: Params | None = None,

@@ -72,6 +72,15 @@ __device__ __forceinline__ bool reliable(int8_t dk, int16_t cp, int16_t cm, int3
   return dk == 0 && min((int32_t)cp, (int32_t)cm) > threshold;
 }
 
+// Without cost planes (costs == nullptr, the regions of the bridging step) every
+// edge between two valid pixels counts as reliable.
+__device__ __forceinline__ bool reliable_at(const int16_t* costs, const int8_t* flows, int64_t P, int64_t e,
+                                            int plane, int32_t threshold) {
+  if (!costs) return true;
+  return reliable(__ldg(flows + plane * P + e), __ldg(costs + 2 * plane * P + e), __ldg(costs + (2 * plane + 1) * P + e),
+                  threshold);
+}
+
 // Phase 1: one warp per row, 32 pixels per step.
 __global__ void k_cc_rows(const int16_t* __restrict__ costs, const int8_t* __restrict__ flows,
                           const float* __restrict__ unw, int64_t m, int64_t n, int32_t threshold,
@@ -85,8 +94,7 @@ __global__ void k_cc_rows(const int16_t* __restrict__ costs, const int8_t* __res
       const int64_t j = j0 + lane, k = i * n + j;
       const bool valid = j < n && !isnan(__ldg(unw + k));
       // h edge (i,j-1)-(i,j): dk = flows[0], c+ = costs[0], c- = costs[1] at (i,j-1)
-      const bool link = valid && j > 0 && !isnan(__ldg(unw + k - 1)) &&
-                        reliable(__ldg(flows + k - 1), __ldg(costs + k - 1), __ldg(costs + P + k - 1), threshold);
+      const bool link = valid && j > 0 && !isnan(__ldg(unw + k - 1)) && reliable_at(costs, flows, P, k - 1, 0, threshold);
       const unsigned starts = __ballot_sync(0xffffffffu, valid && !link);
       const unsigned upto = starts & (0xffffffffu >> (31 - lane));
       // a linked pixel with no start at or below its lane continues the previous segment's run
@@ -104,8 +112,7 @@ __global__ void k_cc_cols(const int16_t* __restrict__ costs, const int8_t* __res
   const int64_t P = m * n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P - n; k += (int64_t)gridDim.x * blockDim.x) {
     // v edge (i,j)-(i+1,j): dk = flows[1], c+ = costs[2], c- = costs[3]
-    if (!isnan(__ldg(unw + k)) && !isnan(__ldg(unw + k + n)) &&
-        reliable(__ldg(flows + P + k), __ldg(costs + 2 * P + k), __ldg(costs + 3 * P + k), threshold))
+    if (!isnan(__ldg(unw + k)) && !isnan(__ldg(unw + k + n)) && reliable_at(costs, flows, P, k, 1, threshold))
       unite(parent, (int32_t)k, (int32_t)(k + n));
   }
 }

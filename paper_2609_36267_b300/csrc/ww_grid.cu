@@ -348,53 +348,76 @@ __global__ void k_steep_hist(const void* ifg, int is_complex, const float* coh, 
   }
 }
 
-// One block of 1024 threads: thread t owns the 64 bins [65535-64t-63, 65535-64t];
-// a block scan from the top finds the bin where the running count reaches the cap.
+// One block of 1024 threads (32 warps) over the 65,536 bins, walked from the top
+// bin down.  Warp w owns the contiguous range of 2048 bins
+// [65535 - 2048 w - 2047, 65535 - 2048 w]; its lanes read 32 consecutive bins
+// per step (coalesced).  The warp totals are scanned from the top to find the
+// warp whose range reaches the cap; that warp then walks its range 32 bins at
+// a time with a warp scan to find the bin.  Every bin is cleared afterwards
+// (coalesced) for the next level or call.
 constexpr int kFindThreads = 1024;
+constexpr int kFindWarps = kFindThreads / 32, kFindSpan = 65536 / kFindWarps;  // 2048 bins per warp
 
 __global__ void __launch_bounds__(kFindThreads) k_steep_find(SteepCtr* ctr, uint32_t* hist, int level) {
   if (ctr->mode != 1) return;
-  __shared__ unsigned long long part[kFindThreads];
-  const int t = threadIdx.x;
-  const int hi = 65535 - 64 * t;
+  __shared__ unsigned long long wsum[kFindWarps];
+  __shared__ int s_warp;
+  __shared__ unsigned long long s_before;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int top = 65535 - kFindSpan * w;  // highest bin of this warp's range
   unsigned long long s = 0;
-  for (int k = 0; k < 64; ++k) s += hist[hi - k];
-  part[t] = s;
+  for (int c = 0; c < kFindSpan; c += 32) s += hist[top - c - lane];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) wsum[w] = s;
   __syncthreads();
-  // inclusive scan of part[] (from the top bins down) by doubling
-  for (int off = 1; off < kFindThreads; off <<= 1) {
-    unsigned long long v = t >= off ? part[t - off] : 0ull;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
   const unsigned long long cap = ctr->pad;
   const unsigned long long base = level == 0 ? 0ull : ctr->above;
-  unsigned long long before = (t ? part[t - 1] : 0ull) + base;
-  unsigned long long after = part[t] + base;
-  // the first thread whose range reaches the cap walks its bins
-  bool mine = after >= cap && before < cap;
-  if (t == 0 && cap == 0) mine = true;  // nothing to take: cut above every bin
-  if (mine) {
-    unsigned long long acc = before;
-    for (int k = 0; k < 64; ++k) {
-      int b = hi - k;
-      unsigned long long h = hist[b];
-      if (acc + h >= cap) {
-        if (level == 0) {
-          ctr->hi_bin = (unsigned long long)b;
-          ctr->above = acc;
-        } else {
-          ctr->threshold = ((unsigned long long)ctr->hi_bin << 16) | (unsigned long long)b;
-          ctr->take_at_thr = cap - acc;
+  if (t == 0) {
+    // the first warp range (from the top) where the running count reaches the cap;
+    // cap == 0 takes nothing: the cut lies above every bin (walk of warp 0 finds bin 65535)
+    unsigned long long acc = base;
+    int hit = -1;
+    for (int k = 0; k < kFindWarps; ++k) {
+      if (acc + wsum[k] >= cap) {
+        hit = k;
+        break;
+      }
+      acc += wsum[k];
+    }
+    s_warp = hit;
+    s_before = acc;
+  }
+  __syncthreads();
+  if (w == s_warp) {
+    unsigned long long acc = s_before;
+    for (int c = 0; c < kFindSpan; c += 32) {
+      const int b = top - c - lane;
+      const unsigned long long h = hist[b];
+      unsigned long long inc = h;  // inclusive scan over the lanes (descending bins)
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+      }
+      const unsigned reach = __ballot_sync(0xffffffffu, acc + inc >= cap);
+      if (reach) {
+        const int first = __ffs(reach) - 1;
+        if (lane == first) {
+          const unsigned long long before_bin = acc + inc - h;
+          if (level == 0) {
+            ctr->hi_bin = (unsigned long long)b;
+            ctr->above = before_bin;
+          } else {
+            ctr->threshold = ((unsigned long long)ctr->hi_bin << 16) | (unsigned long long)b;
+            ctr->take_at_thr = cap - before_bin;
+          }
         }
         break;
       }
-      acc += h;
+      acc += __shfl_sync(0xffffffffu, inc, 31);
     }
   }
   __syncthreads();
-  for (int k = 0; k < 64; ++k) hist[hi - k] = 0;  // ready for the next level / call
+  for (int b = t; b < 65536; b += kFindThreads) hist[b] = 0;  // ready for the next level / call
 }
 
 // mode 0: zero all candidates; mode 1: zero |d| > threshold, and the first
