@@ -101,6 +101,19 @@ typedef struct ww_params {
                                roots, and augments there if it reaches an imbalanced node
                                (zero-cost paths, no potential change); default 64; 0 = never */
   int32_t zero_band_hops;   /* hop radius of that first band (default 512) */
+  /* cost-model variants (Sec. II-B leaves both choices open); every step stays
+   * bit-reproducible (integer or singly rounded fp32 operations only) */
+  int32_t slope_estimator;  /* 0 = fixed-point mean of the wrapped gradients in the window
+                               (default); 1 = argument of the sum of their unit phasors
+                               exp(i d), each from a fixed-point CORDIC rotation of
+                               round(d 2^29) (length 2^30), summed as integers, the argument
+                               by the CORDIC atan2 of the two sums each rounded once to fp32 */
+  int32_t cost_lookup;      /* 0 = nearest bin of the int16 table (default); 1 = bilinear
+                               interpolation, between bin centres, of the table's FP64
+                               100 ln(P0/P+) kept in fp32 (x = (a + PI_F) fp32(256/2pi) - 1/2,
+                               y = g 128 - 1/2, outermost pair and weights clamped,
+                               v0 = r00 + fx (r01 - r00), v1 likewise, v = v0 + fy (v1 - v0)),
+                               then floor, saturated to [0, 32767] */
 } ww_params;
 void ww_params_default(ww_params* p);
 
@@ -121,6 +134,11 @@ typedef struct ww_lut ww_lut;
 ww_status ww_build_lut(double nlooks, ww_lut** out);
 /* Wrap a caller-supplied host table (128*256 int16, row = coherence bin). */
 ww_status ww_lut_from_table(double nlooks, const int16_t* host_table, ww_lut** out);
+/* The same with the fp32 table of 100 ln(P0/P+) (128*256) that the
+ * interpolated lookup (ww_params.cost_lookup = 1) reads. */
+ww_status ww_lut_from_tables(double nlooks, const int16_t* host_table, const float* ratio100, ww_lut** out);
+/* Copy out that fp32 table (built tables and ww_lut_from_tables only). */
+ww_status ww_lut_ratio_table(const ww_lut* lut, float* ratio100);
 /* Copy out the host table (128*256) and, for built tables, 100*c in FP64
  * before flooring (cost100 may be NULL). */
 ww_status ww_lut_table(const ww_lut* lut, int16_t* host_table, double* cost100);
@@ -161,7 +179,7 @@ ww_status ww_costs(const void* ifg, int32_t is_complex, const float* coh, const 
  * file-scope device array of about 1.4 MB that every GPU loading the library
  * holds until the process exits.  Limit: m*n <= 2^27 pixels (134,217,728);
  * larger grids return WW_ERR_INVALID_ARG, and so do parameters ww_costs would
- * refuse.  The first call on a device looks up the array's device address
+ * refuse and the cost-model variants (slope_estimator, cost_lookup other than 0).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every later call enqueues only an upload of the
  * table from a page-locked host copy made when the table was built, two
@@ -293,6 +311,43 @@ ww_status ww_components(const int16_t* costs, const int8_t* flows, const float* 
  * the stream (the size order of the regions is sorted on the host). */
 ww_status ww_bridge(float* unwrapped, int32_t* cycles, int64_t m, int64_t n, int32_t window, int32_t* region,
                     int32_t* shift, int32_t* n_regions, ww_stream stream);
+
+/* ---- Preprocessing: multilook and Eq. (3) sample coherence ----
+ * From two co-registered SLC images slc1, slc2 (DEVICE interleaved complex64
+ * [M][N]) over looks_y x looks_x looks: the multilooked interferogram
+ * ifg = sum z1 conj(z2) (DEVICE complex64 [M/looks_y][N/looks_x], trailing
+ * rows and columns that do not fill a window dropped) and the sample coherence
+ * of Eq. 3, coh = |sum z1 conj(z2)| / sqrt(sum |z1|^2 sum |z2|^2) (DEVICE float32,
+ * clamped to 1, 0 where a power sum is 0).  The looks are summed row-major in
+ * fp32, every product and sum rounded once in the order
+ *   t = (re1 re2 + im1 im2, im1 re2 - re1 im2), S12 += t, S11 += re1^2 + im1^2, ...
+ * so the result is the same on every device.  Asynchronous. */
+ww_status ww_multilook(const void* slc1, const void* slc2, int64_t M, int64_t N, int32_t looks_y, int32_t looks_x,
+                       void* ifg, float* coh, ww_stream stream);
+
+/* ---- Preprocessing: adaptive power-spectrum (Goldstein) filter (Sec. II-D) ----
+ * ifg: DEVICE complex64 [m][n]; out: DEVICE complex64 [m][n] (not ifg).
+ * Patches of 32 x 32 pixels start at every multiple of `step` (1..32) inside the
+ * image (pixels beyond it count as 0).  Per patch: Z = DFT(patch); S = the
+ * smooth x smooth (odd) circular box mean of |Z| divided by its maximum;
+ * Z' = Z S^alpha (alpha >= 0); inverse DFT; the patches are added with the
+ * separable weight w(t) = 1 - |(2t+1)/32 - 1| and the sum divided by the
+ * summed weights.  fp32 arithmetic (agrees with an FP64 evaluation to about
+ * 1e-5 of the local amplitude).  Allocates patch scratch (8 KB per patch) with
+ * cudaMalloc and synchronises the stream before freeing it. */
+ww_status ww_goldstein(const void* ifg, int64_t m, int64_t n, float alpha, int32_t step, int32_t smooth, void* out,
+                       ww_stream stream);
+
+/* ---- Cycle transfer after preprocessing (Sec. II-D) ----
+ * The unwrapped phase of a filtered interferogram fixes the integer cycles of
+ * the original wrapped phase: K = rint((phi_f - psi) / 2pi) in FP64 (half to
+ * even), phi = (float)((double)psi + (double)K * 2pi).  ifg/is_complex/coh/mask
+ * give psi and validity as in ww_integrate; phi_f NaN also counts as invalid.
+ * unwrapped: DEVICE float32 [m][n] (NaN where invalid); cycles: DEVICE int32
+ * [m][n] (0 where invalid).  Asynchronous. */
+ww_status ww_transfer_cycles(const float* unwrapped_filtered, const void* ifg, int32_t is_complex, const float* coh,
+                             const uint8_t* mask, int64_t m, int64_t n, float* unwrapped, int32_t* cycles,
+                             ww_stream stream);
 
 /* ---- Batched form: many uneven interferograms in one solve ----
  * Each item is one unwrap request (device pointers; outputs unwrapped/cycles are

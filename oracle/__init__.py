@@ -23,6 +23,13 @@ Pinned functions and their pins (see tests/test_oracle_*.py):
                   Monte Carlo looks
   sigma_alpha     pi/sqrt(3) for a uniform pdf (the limit stated in Sec. II-B)
   P0/P+/costs     P0+P+ +P- = 1, costs >= 0, the orderings stated in Sec. II-B
+  cost variants   phasor slope vs numpy's angle of the phasor sum, constant
+                  gradients; bilinear lookup exact on linear tables, centres, edges
+  multilook/Eq. 3 numpy fp64 sums within fp32 rounding, gamma = 1 for
+                  proportional images, scale and phase invariance
+  Goldstein       alpha = 0 keeps a single patch-interior field, a pure fringe
+                  pattern is kept, noise is reduced (numpy FFT restatement)
+  cycle transfer  rewrap identity, K = 0 when the filtered field equals psi
 Parity unpinned: the absolute LUT values (the paper prints no table), and
 sigma_alpha's formula away from gamma -> 0 (the paper gives only the limit).
 """
@@ -92,7 +99,11 @@ def lib():
         L.wwo_sigma_from_pdf.argtypes = [P, i32]
         L.wwo_sigma_from_pdf.restype = d
         L.wwo_probabilities.argtypes = [P, i32, d, P, P, P, P]
-        L.wwo_lut_build.argtypes = [d, i32, i32, P, P]
+        L.wwo_lut_build.argtypes = [d, i32, i32, P, P, P]
+        L.wwo_multilook.argtypes = [P, P, i64, i64, i32, i32, P, P]
+        L.wwo_alpha_hat2.argtypes = [P, P, i64, i64, i32, i32, P]
+        L.wwo_costs2.argtypes = [P, P, P, i64, i64, P, P, i32, i32, i32, f, i32, P]
+        L.wwo_costs2.restype = i64
         L.wwo_lut_build.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -136,25 +147,33 @@ def residues(psi: np.ndarray):
     return r, int(g[0])
 
 
-def alpha_hat(psi, valid, half_width=2):
+def alpha_hat(psi, valid, half_width=2, mode=0):
+    """Slope estimate planes [2][m][n]; mode 0 = fixed-point mean of the wrapped
+    gradients, mode 1 = argument of the sum of their unit phasors (CORDIC)."""
     psi = np.ascontiguousarray(psi, np.float32)
     valid = np.ascontiguousarray(valid, np.uint8)
     m, n = psi.shape
     out = np.empty((2, m, n), np.float32)
-    lib().wwo_alpha_hat(_p(psi), _p(valid), m, n, half_width, _p(out))
+    lib().wwo_alpha_hat2(_p(psi), _p(valid), m, n, half_width, int(mode), _p(out))
     return out
 
 
-def costs(psi, coh, valid, table, half_width=2, steep_rad=1.0, steep_cap_ppm=30000):
+def costs(psi, coh, valid, table, half_width=2, steep_rad=1.0, steep_cap_ppm=30000, slope_mode=0, lookup=0,
+          ratio=None):
+    """Cost planes [4][m][n] and the number of steep edges zeroed.  slope_mode:
+    0 fixed-point mean, 1 phasor sum; lookup: 0 nearest bin of `table`, 1
+    bilinear interpolation of `ratio` (float32 [128,256], 100 ln(P0/P+))."""
     psi = np.ascontiguousarray(psi, np.float32)
     coh = np.ascontiguousarray(coh, np.float32)
     valid = np.ascontiguousarray(valid, np.uint8)
     table = np.ascontiguousarray(table, np.int16)
     assert table.size == 128 * 256
+    rt = np.ascontiguousarray(ratio if ratio is not None else np.zeros((128, 256)), np.float32)
+    assert rt.size == 128 * 256 and (lookup == 0 or ratio is not None)
     m, n = psi.shape
     out = np.empty((4, m, n), np.int16)
-    nsteep = lib().wwo_costs(_p(psi), _p(coh), _p(valid), m, n, _p(table), half_width,
-                             float(steep_rad), int(steep_cap_ppm), _p(out))
+    nsteep = lib().wwo_costs2(_p(psi), _p(coh), _p(valid), m, n, _p(table), _p(rt), half_width, int(slope_mode),
+                              int(lookup), float(steep_rad), int(steep_cap_ppm), _p(out))
     return out, int(nsteep)
 
 
@@ -245,12 +264,14 @@ def probabilities(f, alpha_hat_value):
 
 
 def lut_build(L, nh=8192, lambda_panels=8):
-    """-> (cost100 float64 [128,256], table int16 [128,256]); slow (tens of seconds at the default)."""
+    """-> (cost100 float64 [128,256], table int16 [128,256], ratio100 float32 [128,256]);
+    slow (minutes at the default)."""
     c = np.empty((128, 256), np.float64)
     t = np.empty((128, 256), np.int16)
-    st = lib().wwo_lut_build(float(L), nh, lambda_panels, _p(c), _p(t))
+    r = np.empty((128, 256), np.float32)
+    st = lib().wwo_lut_build(float(L), nh, lambda_panels, _p(c), _p(t), _p(r))
     assert st == 0
-    return c, t
+    return c, t, r
 
 
 def components(costs_planes, flows, valid, threshold: int):
@@ -344,3 +365,74 @@ def bridge(unwrapped, valid, window: int = 65):
         shift[region == k] = off  # the parent's median already includes its own shift
     out = np.where(ok, u + 2 * np.pi * shift, np.nan)
     return out, shift, region
+
+
+def multilook(slc1, slc2, looks_y: int, looks_x: int):
+    """Multilooked interferogram and Eq. (3) sample coherence from two SLC images
+    (complex64 [M, N]) over ly x lx looks: S12 = sum z1 conj(z2), gamma =
+    |S12| / sqrt(S11 S22) (clamped to 1; 0 when a power is 0), fp32 in a fixed
+    order (row-major over the looks, every product and sum rounded once).
+    -> (ifg complex64 [M//ly, N//lx], coh float32)."""
+    z1 = np.ascontiguousarray(slc1, np.complex64)
+    z2 = np.ascontiguousarray(slc2, np.complex64)
+    M, N = z1.shape
+    m, n = M // looks_y, N // looks_x
+    ifg = np.empty((m, n), np.complex64)
+    coh = np.empty((m, n), np.float32)
+    lib().wwo_multilook(_p(z1), _p(z2), M, N, int(looks_y), int(looks_x), _p(ifg), _p(coh))
+    return ifg, coh
+
+
+def goldstein(ifg, alpha=0.5, patch=32, step=16, smooth=3):
+    """Adaptive power-spectrum (Goldstein) filter of a wrapped interferogram in
+    overlapping Fourier-domain patches (Sec. II-D), plainly, in float64.
+
+    Patches of patch x patch pixels start at every multiple of `step` in both
+    directions that lies inside the image (pixels beyond the image count as 0).
+    Per patch: Z = FFT2(patch); S = the smooth x smooth circular box mean of |Z|,
+    divided by its maximum; Z' = Z S^alpha; z' = IFFT2(Z').  The patches are
+    added with the separable triangular weight w(t) = 1 - |(2t + 1)/patch - 1|
+    (t = 0 .. patch-1 along each axis) and the sum is divided by the summed
+    weights.  -> complex128 [m, n]."""
+    z = np.asarray(ifg, np.complex128)
+    m, n = z.shape
+    t = np.arange(patch)
+    w1 = 1.0 - np.abs((2 * t + 1) / patch - 1.0)
+    w = np.outer(w1, w1)
+    acc = np.zeros((m, n), np.complex128)
+    wsum = np.zeros((m, n), np.float64)
+    h = smooth // 2
+    for y0 in range(0, m, step):
+        for x0 in range(0, n, step):
+            blk = np.zeros((patch, patch), np.complex128)
+            ys, xs = min(patch, m - y0), min(patch, n - x0)
+            blk[:ys, :xs] = z[y0:y0 + ys, x0:x0 + xs]
+            Z = np.fft.fft2(blk)
+            a = np.abs(Z)
+            S = np.zeros_like(a)
+            for dy in range(-h, h + 1):
+                for dx in range(-h, h + 1):
+                    S += np.roll(np.roll(a, dy, axis=0), dx, axis=1)
+            S /= smooth * smooth
+            mx = S.max()
+            H = (S / mx) ** alpha if mx > 0 else np.zeros_like(S)
+            out = np.fft.ifft2(Z * H)
+            acc[y0:y0 + ys, x0:x0 + xs] += (w * out)[:ys, :xs]
+            wsum[y0:y0 + ys, x0:x0 + xs] += w[:ys, :xs]
+    return acc / wsum
+
+
+def transfer_cycles(unwrapped_filtered, psi, valid):
+    """The integer solution of a preprocessed (filtered) phase moved to the
+    original wrapped phase psi (Sec. II-D): K = rint((phi_f - psi) / 2pi) in
+    float64 (half to even), phi = fp32(psi + 2pi K) with the integration's
+    single rounding; NaN where invalid or where phi_f is NaN.
+    -> (unwrapped float32, cycles int32)."""
+    pf = np.asarray(unwrapped_filtered, np.float32).astype(np.float64)
+    ps = np.asarray(psi, np.float32)
+    ok = np.asarray(valid, bool) & ~np.isnan(pf)
+    two_pi = 6.283185307179586
+    K = np.where(ok, np.rint((pf - ps.astype(np.float64)) / two_pi), 0.0).astype(np.int64)
+    out = (ps.astype(np.float64) + K.astype(np.float64) * two_pi).astype(np.float32)
+    out[~ok] = np.nan
+    return out, K.astype(np.int32)

@@ -45,6 +45,21 @@ void wwo_alpha_hat(const float* psi, const uint8_t* valid, int64_t m, int64_t n,
 int64_t wwo_costs(const float* psi, const float* coh, const uint8_t* valid, int64_t m, int64_t n,
                   const int16_t* table, int32_t half_width, float steep_rad, int32_t steep_cap_ppm,
                   int16_t* costs);
+/* Cost-model variants: slope_mode 0 = fixed-point mean of wrapped gradients,
+ * 1 = argument of the sum of unit phasors (CORDIC); lookup 0 = nearest bin of
+ * the int16 table, 1 = bilinear interpolation of the float table ratio
+ * (100 ln(P0/P+) at the bin centres, 128 x 256) then floor, saturated. */
+int64_t wwo_costs2(const float* psi, const float* coh, const uint8_t* valid, int64_t m, int64_t n,
+                   const int16_t* table, const float* ratio, int32_t half_width, int32_t slope_mode,
+                   int32_t lookup, float steep_rad, int32_t steep_cap_ppm, int16_t* costs);
+void wwo_alpha_hat2(const float* psi, const uint8_t* valid, int64_t m, int64_t n, int32_t half_width,
+                    int32_t mode, float* alpha);
+
+/* ---- preprocessing: multilook + Eq. (3) sample coherence ----
+ * slc1, slc2: interleaved complex64 [M][N]; outputs [M/ly][N/lx]: ifg
+ * (interleaved complex64, sum z1 conj(z2)) and coh (float32).  fp32, fixed order. */
+void wwo_multilook(const float* slc1, const float* slc2, int64_t M, int64_t N, int32_t ly, int32_t lx,
+                   float* ifg, float* coh);
 
 /* ---- integration ---- */
 void wwo_integrate(const float* psi, const uint8_t* valid, const int8_t* flows, int64_t m, int64_t n,
@@ -75,8 +90,9 @@ double wwo_sigma_from_pdf(const double* f, int32_t nh);
 /* P0, P+ for one (alpha-hat, gamma-hat) from a tabulated pdf. */
 void wwo_probabilities(const double* f, int32_t nh, double alpha_hat, double* p0, double* pplus,
                        double* pminus, double* sigma);
-/* The whole 128 x 256 table: 100*c in FP64 (cost100) and floor'd int16. */
-int wwo_lut_build(double L, int32_t nh, int32_t lambda_panels, double* cost100, int16_t* table);
+/* The whole 128 x 256 table: 100*c in FP64 (cost100), floor'd int16, and
+ * (ratio100, may be NULL) 100 ln(P0/P+) in fp32 for interpolated lookup. */
+int wwo_lut_build(double L, int32_t nh, int32_t lambda_panels, double* cost100, int16_t* table, float* ratio100);
 
 #ifdef __cplusplus
 }

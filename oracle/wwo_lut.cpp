@@ -367,7 +367,7 @@ void wwo_probabilities(const double* f, int32_t nh, double alpha_hat, double* p0
   *sigma = T.sigma;
 }
 
-int wwo_lut_build(double L, int32_t nh, int32_t lambda_panels, double* cost100, int16_t* table) {
+int wwo_lut_build(double L, int32_t nh, int32_t lambda_panels, double* cost100, int16_t* table, float* ratio100) {
   if (!(L > 1.0) || nh < 16) return -1;
   std::vector<double> lam, wl, F;
   lambda_nodes(L, lambda_panels, lam, wl);
@@ -392,6 +392,12 @@ int wwo_lut_build(double L, int32_t nh, int32_t lambda_panels, double* cost100, 
       cost100[k * 256 + j] = c100;
       double fl = std::floor(c100);
       table[k * 256 + j] = (int16_t)(fl >= 32767.0 ? 32767 : (int)fl);
+      if (ratio100) {
+        // 100 ln(P0/P+) before the max and the floor, for interpolated lookup;
+        // P+ = 0 saturates, P0 = 0 gives the lower bound
+        double r = !(pp > 0.0) ? 32767.0 : (!(p0 > 0.0) ? -10000.0 : -100.0 * std::log(pp / p0));
+        ratio100[k * 256 + j] = (float)std::min(32767.0, std::max(-10000.0, r));
+      }
     }
   }
   return 0;

@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("band_mult", ctypes.c_int32), ("band_growth", ctypes.c_int32),
                 ("band_start_ppm", ctypes.c_int32), ("full_passes", ctypes.c_int32),
                 ("ground_sink_below", ctypes.c_int32), ("zero_stop_below", ctypes.c_int32),
-                ("zero_band_hops", ctypes.c_int32)]
+                ("zero_band_hops", ctypes.c_int32),
+                ("slope_estimator", ctypes.c_int32), ("cost_lookup", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
@@ -118,6 +119,11 @@ def lib():
                                 ctypes.POINTER(i64), P]
         L.ww_certificate.argtypes = [P, P, P, P, P, i64, i64, P, P]
         L.ww_components.argtypes = [P, P, P, i64, i64, i32, P, P]
+        L.ww_lut_from_tables.argtypes = [d, P, P, ctypes.POINTER(P)]
+        L.ww_multilook.argtypes = [P, P, i64, i64, i32, i32, P, P, P]
+        L.ww_goldstein.argtypes = [P, i64, i64, ctypes.c_float, i32, i32, P, P]
+        L.ww_transfer_cycles.argtypes = [P, P, i32, P, P, i64, i64, P, P, P]
+        L.ww_lut_ratio_table.argtypes = [P, P]
         L.ww_bridge.argtypes = [P, P, i64, i64, i32, P, P, ctypes.POINTER(i32), P]
         L.ww_batch_create.argtypes = [i64, i64, i64, ctypes.POINTER(P)]
         L.ww_batch_free.argtypes = [P]
@@ -139,7 +145,8 @@ def lib():
         for f in ("ww_build_lut", "ww_lut_from_table", "ww_lut_table", "ww_workspace_create", "ww_residues",
                   "ww_costs", "ww_costs_noalloc", "ww_solve_mcf", "ww_solve_mcf_resume", "ww_get_solve_stats",
                   "ww_workspace_last_unwrap", "ww_integrate", "ww_unwrap",
-                  "ww_certificate", "ww_components", "ww_bridge", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_autotune_batch",
+                  "ww_certificate", "ww_components", "ww_bridge", "ww_lut_from_tables", "ww_lut_ratio_table", "ww_multilook", "ww_goldstein",
+                  "ww_transfer_cycles", "ww_batch_create", "ww_unwrap_batch", "ww_batch_stats", "ww_autotune_batch",
                   "ww_server_create",
                   "ww_server_submit", "ww_server_poll", "ww_server_wait", "ww_server_release", "ww_server_get_stats"):
             getattr(L, f).restype = i32
@@ -185,6 +192,22 @@ class Lut:
         _check(lib().ww_lut_from_table(float(nlooks), t.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)),
                "ww_lut_from_table")
         return cls(h.value, nlooks)
+
+    @classmethod
+    def from_tables(cls, nlooks: float, table: np.ndarray, ratio100: np.ndarray) -> "Lut":
+        """An int16 table plus the fp32 100 ln(P0/P+) table of the interpolated lookup."""
+        t = np.ascontiguousarray(table, np.int16)
+        r = np.ascontiguousarray(ratio100, np.float32)
+        assert t.size == N_GAMMA * N_ALPHA and r.size == N_GAMMA * N_ALPHA
+        h = ctypes.c_void_p()
+        _check(lib().ww_lut_from_tables(float(nlooks), t.ctypes.data_as(ctypes.c_void_p),
+                                        r.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)), "ww_lut_from_tables")
+        return cls(h.value, nlooks)
+
+    def ratio100(self) -> np.ndarray:
+        r = np.empty((N_GAMMA, N_ALPHA), np.float32)
+        _check(lib().ww_lut_ratio_table(self._h, r.ctypes.data_as(ctypes.c_void_p)), "ww_lut_ratio_table")
+        return r
 
     def table(self) -> np.ndarray:
         t = np.empty((N_GAMMA, N_ALPHA), np.int16)
@@ -374,6 +397,40 @@ def components(cost_planes, flows, unwrapped, threshold: int = 0, out=None):
     _check(lib().ww_components(_ptr(cost_planes), _ptr(flows), _ptr(unwrapped), m, n, int(threshold), _ptr(labels),
                                _stream()), "ww_components")
     return labels
+
+
+def multilook(slc1, slc2, looks_y: int, looks_x: int):
+    """Multilooked interferogram and Eq. (3) coherence -> (ifg complex64, coh float32)."""
+    torch = _torch()
+    M, N = slc1.shape
+    m, n = M // looks_y, N // looks_x
+    ifg = torch.empty((m, n), dtype=torch.complex64, device=slc1.device)
+    coh = torch.empty((m, n), dtype=torch.float32, device=slc1.device)
+    _check(lib().ww_multilook(_ptr(slc1), _ptr(slc2), M, N, int(looks_y), int(looks_x), _ptr(ifg), _ptr(coh),
+                              _stream()), "ww_multilook")
+    return ifg, coh
+
+
+def goldstein(ifg, alpha: float = 0.5, step: int = 16, smooth: int = 3):
+    """Adaptive power-spectrum filter of a complex64 interferogram -> complex64."""
+    torch = _torch()
+    m, n = ifg.shape
+    out = torch.empty_like(ifg)
+    _check(lib().ww_goldstein(_ptr(ifg), m, n, float(alpha), int(step), int(smooth), _ptr(out), _stream()),
+           "ww_goldstein")
+    return out
+
+
+def transfer_cycles(unwrapped_filtered, ifg, coh=None, mask=None):
+    """Cycles of a filtered unwrap moved to the original phase -> (unwrapped, cycles)."""
+    torch = _torch()
+    m, n = ifg.shape
+    unw = torch.empty((m, n), dtype=torch.float32, device=ifg.device)
+    cyc = torch.empty((m, n), dtype=torch.int32, device=ifg.device)
+    p, c = _ifg(ifg)
+    _check(lib().ww_transfer_cycles(_ptr(unwrapped_filtered), p, c, _ptr(coh), _ptr(mask), m, n, _ptr(unw),
+                                    _ptr(cyc), _stream()), "ww_transfer_cycles")
+    return unw, cyc
 
 
 def bridge(unwrapped, cycles=None, window: int = 65):

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libww.so")
-SOURCES = ["ww_api.cu", "ww_grid.cu", "ww_mcf.cu", "ww_server.cu", "ww_tune.cu", "ww_cc.cu", "ww_bridge.cu", "ww_lut.cpp"]
+SOURCES = ["ww_api.cu", "ww_grid.cu", "ww_mcf.cu", "ww_server.cu", "ww_tune.cu", "ww_cc.cu", "ww_bridge.cu", "ww_pre.cu", "ww_lut.cpp"]
 HEADERS = ["ww_internal.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

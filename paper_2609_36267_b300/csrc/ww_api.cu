@@ -18,9 +18,12 @@ struct LutData {
   double nlooks = 0.0;
   int16_t table[ww::kNGamma * ww::kNAlpha];
   double cost100[ww::kNGamma * ww::kNAlpha];
+  float ratio100[ww::kNGamma * ww::kNAlpha];  // 100 ln(P0/P+) for the interpolated lookup
   bool has_cost100 = false;
+  bool has_ratio = false;
   std::mutex mu;
   int16_t* dev[64] = {nullptr};
+  float* dev_ratio[64] = {nullptr};
   // page-locked copy of `table`, made once when the table is built (null where no
   // device is available); uploads from it are asynchronous and can be captured
   int16_t* pinned = nullptr;
@@ -35,6 +38,8 @@ struct LutData {
   }
   ~LutData() {
     for (auto* p : dev)
+      if (p) cudaFree(p);
+    for (auto* p : dev_ratio)
       if (p) cudaFree(p);
     if (pinned) cudaFreeHost(pinned);
   }
@@ -63,7 +68,8 @@ bool params_ok(const ww_params* p) { return ww::params_valid(p); }
 }  // namespace
 
 bool ww::params_valid(const ww_params* p) {
-  return p && p->box_half_width >= 0 && p->box_half_width <= 3 && p->steep_cap_ppm >= 0 &&
+  return p && (p->slope_estimator == 0 || p->slope_estimator == 1) && (p->cost_lookup == 0 || p->cost_lookup == 1) &&
+         p->box_half_width >= 0 && p->box_half_width <= 3 && p->steep_cap_ppm >= 0 &&
          p->steep_cap_ppm <= 1000000 && p->max_passes > 0 && p->wait_polls > 0 && std::isfinite(p->steep_rad) &&
          (p->graph_loop == 0 || p->graph_loop == 1) && p->search_ctas_per_sm >= 0 && p->search_ctas_per_sm <= 64 &&
          p->band_min >= 1 && p->band_mult >= 0 && p->band_mult <= 1024 && p->band_growth >= 2 &&
@@ -96,6 +102,35 @@ const int16_t* lut_device_table(const ww_lut* lut, cudaStream_t, ww_status* st) 
   }
   *st = WW_OK;
   return d->dev[dev];
+}
+
+const float* lut_device_ratio(const ww_lut* lut, ww_status* st) {
+  auto& d = data_of(lut);
+  if (!d->has_ratio) {
+    *st = WW_ERR_INVALID_ARG;
+    return nullptr;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *st = WW_ERR_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(d->mu);
+  if (!d->dev_ratio[dev]) {
+    float* p = nullptr;
+    if (cudaMalloc(&p, sizeof(d->ratio100)) != cudaSuccess) {
+      *st = WW_ERR_OOM;
+      return nullptr;
+    }
+    if (cudaMemcpy(p, d->ratio100, sizeof(d->ratio100), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(p);
+      *st = WW_ERR_CUDA;
+      return nullptr;
+    }
+    d->dev_ratio[dev] = p;
+  }
+  *st = WW_OK;
+  return d->dev_ratio[dev];
 }
 
 const int16_t* lut_host_table(const ww_lut* lut) { return data_of(lut)->table; }
@@ -152,9 +187,10 @@ ww_status ww_build_lut(double nlooks, ww_lut** out) {
   if (!d) {
     auto nd = std::make_shared<LutData>();
     nd->nlooks = nlooks;
-    int st = ww::lut_build_host(nlooks, nd->table, nd->cost100);
+    int st = ww::lut_build_host(nlooks, nd->table, nd->cost100, nd->ratio100);
     if (st != WW_OK) return st;
     nd->has_cost100 = true;
+    nd->has_ratio = true;
     nd->make_pinned();
     std::lock_guard<std::mutex> g(g_cache_mu);
     auto it = g_cache.find(key_of(nlooks));
@@ -182,6 +218,24 @@ ww_status ww_lut_from_table(double nlooks, const int16_t* host_table, ww_lut** o
   l->nlooks = nlooks;
   l->shared = new std::shared_ptr<LutData>(d);
   *out = l;
+  return WW_OK;
+}
+
+ww_status ww_lut_from_tables(double nlooks, const int16_t* host_table, const float* ratio100, ww_lut** out) {
+  if (!ratio100) return WW_ERR_INVALID_ARG;
+  ww_status st = ww_lut_from_table(nlooks, host_table, out);
+  if (st != WW_OK) return st;
+  auto& d = data_of(*out);
+  std::memcpy(d->ratio100, ratio100, sizeof(d->ratio100));
+  d->has_ratio = true;
+  return WW_OK;
+}
+
+ww_status ww_lut_ratio_table(const ww_lut* lut, float* ratio100) {
+  if (!lut || !ratio100) return WW_ERR_INVALID_ARG;
+  auto& d = data_of(lut);
+  if (!d->has_ratio) return WW_ERR_INVALID_ARG;
+  std::memcpy(ratio100, d->ratio100, sizeof(d->ratio100));
   return WW_OK;
 }
 
@@ -278,7 +332,9 @@ ww_status ww_costs(const void* ifg, int32_t is_complex, const float* coh, const 
   ww_status st;
   const int16_t* dt = ww::lut_device_table(lut, (cudaStream_t)stream, &st);
   if (!dt) return st;
-  return ww::launch_costs(ifg, is_complex ? 1 : 0, coh, mask, m, n, dt, p, ws, costs, (cudaStream_t)stream);
+  const float* dr = nullptr;
+  if (p->cost_lookup == 1 && !(dr = ww::lut_device_ratio(lut, &st))) return st;
+  return ww::launch_costs(ifg, is_complex ? 1 : 0, coh, mask, m, n, dt, dr, p, ws, costs, (cudaStream_t)stream);
 }
 
 ww_status ww_solve_mcf(const int8_t* residues, const int32_t* ground, const int16_t* costs, int64_t m, int64_t n,
@@ -353,7 +409,9 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
   if (st != WW_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int16_t* dt = ww::lut_device_table(lut, s, &st);
-  if (!dt) {
+  const float* dr = nullptr;
+  if (dt && p->cost_lookup == 1) dr = ww::lut_device_ratio(lut, &st);
+  if (!dt || (p->cost_lookup == 1 && !dr)) {
     ww_lut_free(lut);
     return st;
   }
@@ -366,7 +424,7 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
     c = 0;
   }
   if (st == WW_OK) st = ww::launch_residues(src, c, coh, mask, m, n, ws->residues, ws->ground, s);
-  if (st == WW_OK) st = ww::launch_costs(src, c, coh, mask, m, n, dt, p, ws, ws->costs, s);
+  if (st == WW_OK) st = ww::launch_costs(src, c, coh, mask, m, n, dt, dr, p, ws, ws->costs, s);
   if (st == WW_OK) {
     ww::ProbHost ph{m, n, ws->residues, ws->ground, ws->costs, ws->flows, nullptr, ws->total_cost, ws->dev_status};
     st = ww::solve_problems(&ph, 1, &ws->sv, p, ws->potentials, &ws->stats, s);
@@ -617,6 +675,8 @@ ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* 
     const ww_batch_item& it = items[k];
     const int16_t* dt = ww::lut_device_table(luts[k], s, &st);
     if (!dt) break;
+    const float* dr = nullptr;
+    if (p->cost_lookup == 1 && !(dr = ww::lut_device_ratio(luts[k], &st))) break;
     ++filled;
     ww::ProbHost& ph = probs[k];
     ph.m = it.m;
@@ -646,6 +706,7 @@ ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* 
     g.ground = const_cast<int32_t*>(ph.ground);
     g.costs = const_cast<int16_t*>(ph.costs);
     g.table = dt;
+    g.ratio = dr;
     g.flows = ph.flows;
     g.unw = it.unwrapped;
     g.cyc = it.cycles;

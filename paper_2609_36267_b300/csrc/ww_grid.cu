@@ -103,22 +103,56 @@ __device__ __forceinline__ float edge_d(float a, float b) {
   return __fsub_rn(dp, __fmul_rn(kTwoPiF, (float)wrap_count(dp)));
 }
 
+// Slope estimate from the row partial sums of the fixed-point gradients: the
+// vertical sum over the window's rows, then S / (cnt 2^22) rounded once.
+__device__ __forceinline__ float window_mean(const int32_t (*rs)[CTX], const uint8_t (*ns)[CTX], int R, int c, int w) {
+  int32_t S = 0;
+  int cnt = 0;
+  for (int d = -w; d <= w; ++d) {
+    S += rs[R + d][c];
+    cnt += ns[R + d][c];
+  }
+  return __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
+}
+
+// Phasor slope estimate: integer sums of the window's edge phasors (length 2^30
+// each, at most 49 of them: below 2^36), each sum rounded once to fp32, then the
+// CORDIC atan2; 0 for an empty window.
+__device__ __forceinline__ float window_phasor(const int32_t (*xs)[CEX + 1], const int32_t (*ys)[CEX + 1],
+                                               const uint8_t (*es)[CEX + 1], int R, int C, int w) {
+  long long SX = 0, SY = 0;
+  for (int d = -w; d <= w; ++d)
+    for (int e = -w; e <= w; ++e)
+      if (es[R + d][C + e]) {
+        SX += xs[R + d][C + e];
+        SY += ys[R + d][C + e];
+      }
+  return cordic_phase(__ll2float_rn(SX), __ll2float_rn(SY));
+}
+
 // One CTY x CTX tile of pixels (both edges of each pixel), tile (by, bx).
 // Steep candidates are counted, and their edge keys appended to `list` while
 // it has room (`list` may be null).
+// SLOPE 0: slope estimate = fixed-point mean of the window's wrapped gradients
+// (separable sums); SLOPE 1: argument of the sum of their unit phasors (CORDIC
+// rotation per edge, integer window sums, CORDIC atan2).  LOOKUP 0: nearest bin
+// of the int16 table; LOOKUP 1: bilinear interpolation of `ratio`.
+template <int SLOPE, int LOOKUP>
 __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_complex,
                                            const float* __restrict__ coh, const uint8_t* __restrict__ mask,
-                                           int64_t m, int64_t n, const int16_t* __restrict__ table, int w,
-                                           float steep_rad, int16_t* __restrict__ costs, SteepCtr* ctr,
-                                           uint32_t* __restrict__ list, unsigned long long list_cap,
-                                           int64_t bx, int64_t by) {
+                                           int64_t m, int64_t n, const int16_t* __restrict__ table,
+                                           const float* __restrict__ ratio, int w, float steep_rad,
+                                           int16_t* __restrict__ costs, SteepCtr* ctr, uint32_t* __restrict__ list,
+                                           unsigned long long list_cap, int64_t bx, int64_t by) {
   __shared__ float sp[CPY][CPX];
   __shared__ float sc[CPY][CPX];
   __shared__ uint8_t sv[CPY][CPX];
+  // SLOPE 0: fixed-point gradients; SLOPE 1: cos part of the edge phasors
   __shared__ int32_t qh[CEY][CEX + 1], qv[CEY][CEX + 1];
+  __shared__ int32_t yh[SLOPE ? CEY : 1][CEX + 1], yv[SLOPE ? CEY : 1][CEX + 1];  // sin part (SLOPE 1)
   __shared__ uint8_t eh[CEY][CEX + 1], ev[CEY][CEX + 1];
-  __shared__ int32_t rh[CEY][CTX], rv[CEY][CTX];      // row (horizontal) partial sums
-  __shared__ uint8_t nh[CEY][CTX], nv[CEY][CTX];      // row partial counts
+  __shared__ int32_t rh[SLOPE ? 1 : CEY][CTX], rv[SLOPE ? 1 : CEY][CTX];  // row (horizontal) partial sums
+  __shared__ uint8_t nh[SLOPE ? 1 : CEY][CTX], nv[SLOPE ? 1 : CEY][CTX];  // row partial counts
   const int64_t i0 = by * CTY, j0 = bx * CTX;
   const int tid = threadIdx.x;
   // 1. prepared pixels, tile origin (i0 - CW, j0 - CW); every load of a thread
@@ -148,15 +182,23 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   for (int q = tid; q < CEY * CEX; q += 256) {
     int r = q / CEX, c = q % CEX;
     int64_t i = i0 - CW + r, j = j0 - CW + c;
-    int32_t a = 0, b = 0;
+    int32_t a = 0, b = 0, ya = 0, yb = 0;
     uint8_t ea = 0, eb = 0;
     if (i >= 0 && i < m && j >= 0) {
       if (j + 1 < n && sv[r][c] && sv[r][c + 1]) {
-        a = __float2int_rn(__fmul_rn(edge_d(sp[r][c], sp[r][c + 1]), kQScale));
+        const float d = edge_d(sp[r][c], sp[r][c + 1]);
+        if constexpr (SLOPE == 0)
+          a = __float2int_rn(__fmul_rn(d, kQScale));
+        else
+          cordic_cos_sin(__float2int_rn(__fmul_rn(d, 536870912.0f)), &a, &ya);
         ea = 1;
       }
       if (i + 1 < m && j < n && sv[r][c] && sv[r + 1][c]) {
-        b = __float2int_rn(__fmul_rn(edge_d(sp[r][c], sp[r + 1][c]), kQScale));
+        const float d = edge_d(sp[r][c], sp[r + 1][c]);
+        if constexpr (SLOPE == 0)
+          b = __float2int_rn(__fmul_rn(d, kQScale));
+        else
+          cordic_cos_sin(__float2int_rn(__fmul_rn(d, 536870912.0f)), &b, &yb);
         eb = 1;
       }
     }
@@ -164,10 +206,14 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     eh[r][c] = ea;
     qv[r][c] = b;
     ev[r][c] = eb;
+    if constexpr (SLOPE == 1) {
+      yh[r][c] = ya;
+      yv[r][c] = yb;
+    }
   }
   __syncthreads();
   // 3. horizontal window sums for the output columns, every extended row
-  for (int q = tid; q < CEY * CTX; q += 256) {
+  for (int q = tid; q < (SLOPE ? 0 : CEY * CTX); q += 256) {
     int r = q / CTX, c = q % CTX;
     int32_t sa = 0, sb = 0;
     int ca = 0, cb = 0;
@@ -204,16 +250,20 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     // h edge (i,j)
     int16_t hp = 0, hm = 0;
     if (eh[R][C]) {
-      int32_t S = 0;
-      int cnt = 0;
-      for (int d = -w; d <= w; ++d) {
-        S += rh[R + d][c];
-        cnt += nh[R + d][c];
+      float ah;
+      if constexpr (SLOPE == 0)
+        ah = window_mean(rh, nh, R, c, w);
+      else
+        ah = window_phasor(qh, yh, eh, R, C, w);
+      const float ge = fminf(sc[R][C], sc[R][C + 1]);
+      if (LOOKUP == 0) {
+        const int ig = gamma_index(ge);
+        hp = __ldg(table + ig * kNAlpha + alpha_index(ah));
+        hm = __ldg(table + ig * kNAlpha + alpha_index(-ah));
+      } else {
+        hp = bilinear_cost(ratio, ah, ge);
+        hm = bilinear_cost(ratio, -ah, ge);
       }
-      float ah = __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
-      int ig = gamma_index(fminf(sc[R][C], sc[R][C + 1]));
-      hp = __ldg(table + ig * kNAlpha + alpha_index(ah));
-      hm = __ldg(table + ig * kNAlpha + alpha_index(-ah));
       ++cnt_valid;
       hcand = fabsf(edge_d(sp[R][C], sp[R][C + 1])) > steep_rad;
     }
@@ -221,16 +271,20 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     costs[P + k] = hm;
     int16_t vp = 0, vm = 0;
     if (ev[R][C]) {
-      int32_t S = 0;
-      int cnt = 0;
-      for (int d = -w; d <= w; ++d) {
-        S += rv[R + d][c];
-        cnt += nv[R + d][c];
+      float av;
+      if constexpr (SLOPE == 0)
+        av = window_mean(rv, nv, R, c, w);
+      else
+        av = window_phasor(qv, yv, ev, R, C, w);
+      const float ge = fminf(sc[R][C], sc[R + 1][C]);
+      if (LOOKUP == 0) {
+        const int ig = gamma_index(ge);
+        vp = __ldg(table + ig * kNAlpha + alpha_index(av));
+        vm = __ldg(table + ig * kNAlpha + alpha_index(-av));
+      } else {
+        vp = bilinear_cost(ratio, av, ge);
+        vm = bilinear_cost(ratio, -av, ge);
       }
-      float av = __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
-      int ig = gamma_index(fminf(sc[R][C], sc[R + 1][C]));
-      vp = __ldg(table + ig * kNAlpha + alpha_index(av));
-      vm = __ldg(table + ig * kNAlpha + alpha_index(-av));
       ++cnt_valid;
       vcand = fabsf(edge_d(sp[R][C], sp[R + 1][C])) > steep_rad;
     }
@@ -273,15 +327,25 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   }
 }
 
+template <int SLOPE, int LOOKUP>
 __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int is_complex,
                                                const float* __restrict__ coh,
                                                const uint8_t* __restrict__ mask, int64_t m, int64_t n,
-                                               const int16_t* __restrict__ table, int w, float steep_rad,
-                                               int16_t* __restrict__ costs, SteepCtr* ctr, uint32_t* list,
-                                               unsigned long long list_cap) {
+                                               const int16_t* __restrict__ table, const float* __restrict__ ratio,
+                                               int w, float steep_rad, int16_t* __restrict__ costs, SteepCtr* ctr,
+                                               uint32_t* list, unsigned long long list_cap) {
   // one-dimensional grid of tiles (gridDim.y would cap the rows at 65535 tiles)
   const int64_t gx = (n + CTX - 1) / CTX, b = blockIdx.x;
-  costs_tile(ifg, is_complex, coh, mask, m, n, table, w, steep_rad, costs, ctr, list, list_cap, b % gx, b / gx);
+  costs_tile<SLOPE, LOOKUP>(ifg, is_complex, coh, mask, m, n, table, ratio, w, steep_rad, costs, ctr, list, list_cap,
+                            b % gx, b / gx);
+}
+
+// the k_costs variant for a parameter set
+using CostsKernel = void (*)(const void*, int, const float*, const uint8_t*, int64_t, int64_t, const int16_t*,
+                             const float*, int, float, int16_t*, SteepCtr*, uint32_t*, unsigned long long);
+CostsKernel costs_kernel(const ww_params* p) {
+  if (p->slope_estimator == 0) return p->cost_lookup == 0 ? k_costs<0, 0> : k_costs<0, 1>;
+  return p->cost_lookup == 0 ? k_costs<1, 0> : k_costs<1, 1>;
 }
 
 // number of k_costs tiles (one block each) of an m x n image
@@ -695,13 +759,15 @@ __global__ void __launch_bounds__(RTX* RTT) k_residues_b(const GridItem* __restr
   residues_tile(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, it.res, it.ground, local % gx, local / gx);
 }
 
+template <int SLOPE, int LOOKUP>
 __global__ void __launch_bounds__(256) k_costs_b(const GridItem* __restrict__ items, int count, int w,
                                                  float steep_rad) {
   const int64_t b = blockIdx.x;
   const GridItem& it = items[item_of_block<kBlkCost>(items, count, b)];
   const int64_t local = b - it.blk[kBlkCost];
   const int64_t gx = (it.n + CTX - 1) / CTX;
-  costs_tile(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, it.table, w, steep_rad, it.costs,
+  costs_tile<SLOPE, LOOKUP>(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, it.table, it.ratio, w, steep_rad,
+             it.costs,
              reinterpret_cast<SteepCtr*>(it.steep), it.cand_list, (unsigned long long)it.cand_cap, local % gx,
              local / gx);
 }
@@ -1003,8 +1069,9 @@ int64_t steep_list_capacity(int64_t pixels, int32_t cap_ppm) {
 }
 
 ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
-                       int64_t m, int64_t n, const int16_t* dtable, const ww_params* p,
+                       int64_t m, int64_t n, const int16_t* dtable, const float* dratio, const ww_params* p,
                        ww_workspace* ws, int16_t* costs, cudaStream_t s) {
+  if (p->cost_lookup == 1 && !dratio) return WW_ERR_INVALID_ARG;
   SteepCtr* ctr = reinterpret_cast<SteepCtr*>(ws->steep_ctr);
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
   // candidate list: within the cap every candidate fits (cap + 1 <= capacity), so the
@@ -1013,8 +1080,8 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
   const bool use_list = ws->steep_list && need <= ws->steep_list_cap && 2 * m * n < (1ll << 32);
   uint32_t* list = use_list ? ws->steep_list : nullptr;
   const unsigned long long list_cap = use_list ? (unsigned long long)ws->steep_list_cap : 0ull;
-  k_costs<<<cost_tiles(m, n), 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, dtable, p->box_half_width,
-                                           p->steep_rad, costs, ctr, list, list_cap);
+  costs_kernel(p)<<<cost_tiles(m, n), 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, dtable, dratio,
+                                                   p->box_half_width, p->steep_rad, costs, ctr, list, list_cap);
   WW_CUDA_TRY(cudaGetLastError());
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
   if (use_list) k_steep_zero_list<<<148 * 4, 256, 0, s>>>(ctr, list, list_cap, m * n, costs);
@@ -1122,7 +1189,9 @@ ww_status launch_pre_batch(GridBatch* gb, int count, const ww_params* p, cudaStr
   if (off[kBlkPhase] > 0) k_phase_b<<<(unsigned)off[kBlkPhase], 256, 0, s>>>(gb->d_items, count);
   k_prep_b<<<pb, 256, 0, s>>>(gb->d_items, count);
   k_residues_b<<<(unsigned)off[kBlkRes], dim3(RTX, RTT), 0, s>>>(gb->d_items, count);
-  k_costs_b<<<(unsigned)off[kBlkCost], 256, 0, s>>>(gb->d_items, count, p->box_half_width, p->steep_rad);
+  auto kb = p->slope_estimator == 0 ? (p->cost_lookup == 0 ? k_costs_b<0, 0> : k_costs_b<0, 1>)
+                                     : (p->cost_lookup == 0 ? k_costs_b<1, 0> : k_costs_b<1, 1>);
+  kb<<<(unsigned)off[kBlkCost], 256, 0, s>>>(gb->d_items, count, p->box_half_width, p->steep_rad);
   k_steep_plan_b<<<pb, 256, 0, s>>>(gb->d_items, count, p->steep_cap_ppm);
   // items within their cap
   k_steep_zero_list_b<<<dim3(4, (unsigned)count), 256, 0, s>>>(gb->d_items);
@@ -1229,7 +1298,7 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   const ww_params* p = params ? params : &def;
   if (!ifg || !coh || !lut || !costs || m < 2 || n < 2) return WW_ERR_INVALID_ARG;
   if (m > kNoAllocMaxPixels || n > kNoAllocMaxPixels || m * n > kNoAllocMaxPixels) return WW_ERR_INVALID_ARG;
-  if (!params_valid(p)) return WW_ERR_INVALID_ARG;
+  if (!params_valid(p) || p->slope_estimator != 0 || p->cost_lookup != 0) return WW_ERR_INVALID_ARG;
   unsigned char* base = nullptr;
   ww_status st = noalloc_scratch(&base);
   if (st != WW_OK) return st;
@@ -1246,8 +1315,8 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   WW_CUDA_TRY(cudaMemcpyAsync(dtable, src ? src : lut_host_table(lut), kNoAllocTableBytes, cudaMemcpyHostToDevice, s));
   WW_CUDA_TRY(cudaMemsetAsync(hist, 0, 65536 * sizeof(uint32_t), s));
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
-  k_costs<<<cost_tiles(m, n), 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, p->box_half_width, p->steep_rad,
-                                           costs, ctr, nullptr, 0ull);
+  k_costs<0, 0><<<cost_tiles(m, n), 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, nullptr, p->box_half_width,
+                                                 p->steep_rad, costs, ctr, nullptr, 0ull);
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
   const int hist_blocks = 148 * 8;
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, hist, 0);

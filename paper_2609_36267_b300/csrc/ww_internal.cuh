@@ -102,6 +102,62 @@ __device__ __forceinline__ float cordic_phase(float re, float im) {
   return fminf(fmaxf(psi, -kPiF), kPiF);
 }
 
+// Fixed-point CORDIC rotation: (cos t, sin t) scaled to length 2^30 for the
+// angle t = Z 2^-29 rad, |Z| <= round(pi 2^29).  The start vector is
+// (K^-1 2^30, 0) with K^-1 = prod over the 30 steps of (1 + 2^-2i)^(-1/2), so the
+// rotation gain brings it to length 2^30; angles beyond +-pi/2 are first turned
+// by a quarter turn; step i turns by -+atan(2^-i) toward Z = 0.  |X|, |Y| stay
+// below 2^30 (the length only grows toward 2^30) and |Z| below 2^31.
+constexpr int32_t kInvGainQ30 = 652032874;  // round(2^30 prod (1 + 2^-2i)^(-1/2)), i < 30
+
+__device__ __forceinline__ void cordic_cos_sin(int32_t z, int32_t* c, int32_t* s) {
+  int32_t x = kInvGainQ30, y = 0;
+  if (z > (int32_t)kHalfPiQ) {
+    x = 0;
+    y = kInvGainQ30;
+    z -= (int32_t)kHalfPiQ;
+  } else if (z < -(int32_t)kHalfPiQ) {
+    x = 0;
+    y = -kInvGainQ30;
+    z += (int32_t)kHalfPiQ;
+  }
+#pragma unroll
+  for (int i = 0; i < 30; ++i) {
+    const int32_t xs = x >> i, ys = y >> i;
+    if (z >= 0) {
+      x -= ys;
+      y += xs;
+      z -= kAtanQ[i];
+    } else {
+      x += ys;
+      y -= xs;
+      z += kAtanQ[i];
+    }
+  }
+  *c = x;
+  *s = y;
+}
+
+// Interpolated cost (cost_lookup = 1): bilinear in the table of 100 ln(P0/P+)
+// at the bin centres, fp32 with every operation rounded once, then floor and
+// saturation to [0, 32767].
+__device__ __forceinline__ int16_t bilinear_cost(const float* __restrict__ ratio, float a, float g) {
+  const float x = __fsub_rn(__fmul_rn(__fadd_rn(a, kPiF), kAlphaScale), 0.5f);
+  const float y = __fsub_rn(__fmul_rn(g, 128.0f), 0.5f);
+  const int j0 = min(254, max(0, (int)floorf(x)));
+  const int k0 = min(126, max(0, (int)floorf(y)));
+  const float fx = fminf(1.0f, fmaxf(0.0f, __fsub_rn(x, (float)j0)));
+  const float fy = fminf(1.0f, fmaxf(0.0f, __fsub_rn(y, (float)k0)));
+  const float* r0 = ratio + k0 * kNAlpha + j0;
+  const float a00 = __ldg(r0), a01 = __ldg(r0 + 1), a10 = __ldg(r0 + kNAlpha), a11 = __ldg(r0 + kNAlpha + 1);
+  const float v0 = __fadd_rn(a00, __fmul_rn(fx, __fsub_rn(a01, a00)));
+  const float v1 = __fadd_rn(a10, __fmul_rn(fx, __fsub_rn(a11, a10)));
+  const float v = __fadd_rn(v0, __fmul_rn(fy, __fsub_rn(v1, v0)));
+  if (!(v > 0.0f)) return 0;
+  if (v >= 32767.0f) return 32767;
+  return (int16_t)floorf(v);
+}
+
 // Wrap count of a phase difference (fp32): +1 above pi, -1 at or below -pi.
 __device__ __forceinline__ int wrap_count(float dpsi) {
   return (dpsi > kPiF ? 1 : 0) - (dpsi <= -kPiF ? 1 : 0);
@@ -240,9 +296,12 @@ struct ww_workspace {
 
 namespace ww {
 // ww_lut.cpp
-int lut_build_host(double nlooks, int16_t* table, double* cost100);
+int lut_build_host(double nlooks, int16_t* table, double* cost100, float* ratio100);
 // ww_api.cu
 const int16_t* lut_device_table(const ww_lut* lut, cudaStream_t stream, ww_status* st);
+// device copy of the fp32 table of 100 ln(P0/P+) (interpolated lookup), or null
+// with *st = WW_ERR_INVALID_ARG when the table object carries none
+const float* lut_device_ratio(const ww_lut* lut, ww_status* st);
 const int16_t* lut_host_table(const ww_lut* lut);
 // page-locked copy of the host table, or null if it could not be made
 const int16_t* lut_pinned_table(const ww_lut* lut);
@@ -250,7 +309,7 @@ const int16_t* lut_pinned_table(const ww_lut* lut);
 ww_status launch_residues(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                           int64_t m, int64_t n, int8_t* res, int32_t* ground, cudaStream_t s);
 ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
-                       int64_t m, int64_t n, const int16_t* dtable, const ww_params* p,
+                       int64_t m, int64_t n, const int16_t* dtable, const float* dratio, const ww_params* p,
                        ww_workspace* ws, int16_t* costs, cudaStream_t s);
 ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                            const int8_t* flows, int64_t m, int64_t n, float* unw, int32_t* cyc,
@@ -276,6 +335,7 @@ struct GridItem {
   int32_t* ground;
   int16_t* costs;
   const int16_t* table;
+  const float* ratio;  // 100 ln(P0/P+) table of the interpolated lookup (null otherwise)
   void* steep;  // per-item steep-selection counters (set by launch_pre_batch)
   uint32_t* cand_list;  // steep candidate keys (set by launch_pre_batch; null: no list)
   int64_t cand_cap;

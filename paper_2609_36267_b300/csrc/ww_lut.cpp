@@ -187,7 +187,7 @@ double tail(const RowTables& R, double s) {
   return fin ? std::exp(acc) : std::max(acc, 0.0);
 }
 
-void row_costs(const RowTables& R, const Rule& r12, double* c100_row, int16_t* tab_row) {
+void row_costs(const RowTables& R, const Rule& r12, double* c100_row, int16_t* tab_row, float* ratio_row) {
   const double sg = R.sigma;
   const int panels = 64;
   for (int j = 0; j < ww::kNAlpha; ++j) {
@@ -227,6 +227,10 @@ void row_costs(const RowTables& R, const Rule& r12, double* c100_row, int16_t* t
     c100_row[j] = c100;
     double fl = std::floor(c100);
     tab_row[j] = (int16_t)(fl >= 32767.0 ? 32767 : (int)fl);
+    // 100 ln(P0/P+) before the max and the floor, for the interpolated lookup
+    // (saturated like the table: P+ = 0 -> 32767, P0 = 0 -> the lower bound)
+    const double r = !(pp > 0.0) ? 32767.0 : (!(p0 > 0.0) ? -10000.0 : -100.0 * std::log(pp / p0));
+    ratio_row[j] = (float)std::min(32767.0, std::max(-10000.0, r));
   }
 }
 
@@ -246,7 +250,7 @@ void parallel_for(long count, F fn) {
 
 namespace ww {
 
-int lut_build_host(double L, int16_t* table, double* cost100) {
+int lut_build_host(double L, int16_t* table, double* cost100, float* ratio100) {
   if (!(L > 1.0) || !std::isfinite(L)) return WW_ERR_INVALID_ARG;
   // intervals on [0, pi]; the high-coherence rows are sharper for many looks
   const long NH = L > 16.0 ? 8192 : 4096;
@@ -302,7 +306,7 @@ int lut_build_host(double L, int16_t* table, double* cost100) {
     RowTables R;
     row_tables(f, NH, R);
     std::vector<double> c(kNAlpha);
-    row_costs(R, r12, c.data(), table + kg * kNAlpha);
+    row_costs(R, r12, c.data(), table + kg * kNAlpha, ratio100 + kg * kNAlpha);
     if (cost100)
       for (int j = 0; j < kNAlpha; ++j) cost100[kg * kNAlpha + j] = c[j];
   });

@@ -180,8 +180,9 @@ void worker_loop(ww_server* S) {
       const ww_batch_item& it = r->item;
       ww_status st = ww_build_lut(it.nlooks, &r->lut);
       const int16_t* dt = st == WW_OK ? ww::lut_device_table(r->lut, s, &st) : nullptr;
+      const float* dr = (dt && S->prm.cost_lookup == 1) ? ww::lut_device_ratio(r->lut, &st) : nullptr;
       const int slot0 = S->session->next_slot();
-      if (!dt || slot0 < 0) {
+      if (!dt || (S->prm.cost_lookup == 1 && !dr) || slot0 < 0) {
         release_ranges(S, r);
         fail_request(S, r, st != WW_OK ? st : WW_ERR_INTERNAL);
         continue;
@@ -215,6 +216,7 @@ void worker_loop(ww_server* S) {
       g.ground = S->ground + slot;
       g.costs = cst;
       g.table = dt;
+      g.ratio = dr;
       r->slot = slot;
       joined.push_back(r);
     }

@@ -2,7 +2,8 @@
 
 Calls only the CPU oracle (oracle/).  For each number of looks L it stores
 100*c (Eq. 4, before flooring) and the floored int16 table on the 128 (coherence)
-x 256 (slope) bin-centre grid, built with an 8192-interval half grid in phase and
+x 256 (slope) bin-centre grid, 100*ln(P0/P+) in fp32 for interpolated lookup,
+built with an 8192-interval half grid in phase and
 eight Gauss-Legendre panels per unit of -log(1-gamma).  At these settings the
 oracle's P0 and P+ agree with an independent quadrature of Eqs. 5-7 to about
 1e-7 relative or better (tests/test_oracle_lut.py), i.e. 100*c to about 1e-5.
@@ -37,8 +38,8 @@ def _one(L: float):
 
     t = time.time()
     nh = NH
-    cost100, table = oracle.lut_build(L, nh=nh, lambda_panels=LAMBDA_PANELS)
-    np.savez_compressed(path_for(L), cost100=cost100, table=table, nlooks=L, nh=nh,
+    cost100, table, ratio100 = oracle.lut_build(L, nh=nh, lambda_panels=LAMBDA_PANELS)
+    np.savez_compressed(path_for(L), cost100=cost100, table=table, ratio100=ratio100, nlooks=L, nh=nh,
                         lambda_panels=LAMBDA_PANELS)
     return L, time.time() - t
 

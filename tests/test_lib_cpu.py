@@ -89,5 +89,9 @@ def test_library_lut_matches_oracle(L):
     d = np.abs(c - co)[fin] / (co[fin] + 1.0)
     assert d.max() <= REL_TOL, d.max()
     assert np.array_equal(t, to)
+    # the fp32 100 ln(P0/P+) tables of the interpolated lookup: the same FP64
+    # agreement, then one rounding each
+    r, ro = lut.ratio100(), z["ratio100"]
+    assert np.all(np.abs(r.astype(np.float64) - ro) <= REL_TOL * (np.abs(ro) + 1.0) + np.spacing(np.abs(ro)))
     # the cache hands out the same table
     assert np.array_equal(ww.Lut.build(L).table(), t)
