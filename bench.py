@@ -248,7 +248,7 @@ def run_reference(args, rank, world):
 
 
 SCHEDULE_KEYS = ("full_passes", "band_start_ppm", "band_min", "band_mult", "band_growth", "ground_sink_below",
-                 "zero_stop_below", "zero_band_hops", "search_ctas_per_sm")
+                 "zero_stop_below", "zero_band_hops", "zero_band_hops_min", "search_ctas_per_sm")
 
 
 def run_config(args, wl, px, world):
@@ -408,11 +408,12 @@ def run_ours(args, rank, world, local):
                                 "negative_reduced_costs": cert[2], "total_cost": cert[3],
                                 "table": "library FP64 table for L=50, equal entrywise to the oracle's"}}
         line["gpu_launches"] = launch_count(st, args.steps)
-        line["components"] = measure_components(ww, torch, x, ifg, coh, mask, unw, ws, max(3, args.steps), peak,
-                                                peak_kind)
-        line["bridge"] = measure_bridge(ww, torch, unw, 3)
-        line["cost_variants"] = measure_variants(ww, torch, x, ifg, coh, mask, ws, prm)
-        line["preprocessing"] = measure_preprocessing(ww, torch, ifg, peak, peak_kind)
+        if not args.no_extras:
+            line["components"] = measure_components(ww, torch, x, ifg, coh, mask, unw, ws, max(3, args.steps), peak,
+                                                    peak_kind)
+            line["bridge"] = measure_bridge(ww, torch, unw, 3)
+            line["cost_variants"] = measure_variants(ww, torch, x, ifg, coh, mask, ws, prm)
+            line["preprocessing"] = measure_preprocessing(ww, torch, ifg, peak, peak_kind)
         if world == 1 and args.workload == "earthquake" and not args.no_extras:
             # rows a5 and a6 under the same clock: the batched and served forms vs
             # the plain one-at-a-time solve (the earthquake buffers are freed first)
@@ -609,7 +610,8 @@ def run_batched(args, summary=False):
         prm, tune = ww.autotune_batch(sample, repeats=2)
         tune["params"] = {k: getattr(prm, k) for k in ("graph_loop", "search_ctas_per_sm", "band_min", "band_mult",
                                                         "band_growth", "band_start_ppm", "full_passes",
-                                                        "ground_sink_below", "zero_stop_below", "zero_band_hops")}
+                                                        "ground_sink_below", "zero_stop_below", "zero_band_hops",
+                                                        "zero_band_hops_min")}
         del sample
     costs = None
     for _ in range(args.warmup):
@@ -824,14 +826,14 @@ def run_served(args, summary=False):
 
 def launch_count(st, steps):
     """Kernels of this library launched per timed step (host-driven pass loop), times steps."""
-    # phase (complex input), residues, costs, steep plan/zero_list/hist x2/find x2/ties/scan/zero,
-    # integrate col0/rows
-    grid = 14
-    solver_fixed = 7  # join, init_state, resume, zero_slots, total_cost, copy_pot, write_results
-    # pass_setup, init_labels, seed_tiles, 4 bands x (search, ground_dist, count_found, band_decide)
-    # + 3 reseeds, clear_capped, select, select_ground, augment, augment_ground, reset_best,
+    # phase (complex input, validity folded in), costs with the residues fused, steep
+    # plan/zero_list/hist x2/find x2/ties/scan/zero, integrate col0/rows
+    grid = 13
+    solver_fixed = 8  # join_clear, join, init_state, resume, zero_slots, total_cost, copy_pot, write_results
+    # pass_setup, set_roots, seed_tiles, 7 bands x (search, ground_dist, count_found, band_decide)
+    # + 6 reseeds, clear_capped, select, select_ground, augment, augment_ground, reset_best,
     # potentials, potential_ground, compact, finish_pass
-    per_pass = 32
+    per_pass = 3 + 7 * 4 + 6 + 10
     return int((grid + solver_fixed + st["passes"] * per_pass) * steps)
 
 
@@ -849,7 +851,7 @@ def main():
     ap.add_argument("--compare-k", type=int, default=64,
                     help="served: requests whose cycle maps are compared with their solve alone")
     ap.add_argument("--no-extras", action="store_true",
-                    help="default run: skip the batched and served measurements")
+                    help="headline line only (no components, bridging, variants, preprocessing, batched, served)")
     ap.add_argument("--served-pool", type=int, default=3, help="served: generated 4096x8192 scenes to crop")
     ap.add_argument("--distinct", type=int, default=64, help="served: distinct crops kept on the device")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.7, 1.5], help="served: offered load vs plain")

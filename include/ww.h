@@ -100,7 +100,10 @@ typedef struct ww_params {
                                searches at distance 0 only, within zero_band_hops hops of the
                                roots, and augments there if it reaches an imbalanced node
                                (zero-cost paths, no potential change); default 64; 0 = never */
-  int32_t zero_band_hops;   /* hop radius of that first band (default 512) */
+  int32_t zero_band_hops;   /* largest hop radius of that first band (default 512) */
+  int32_t zero_band_hops_min; /* its first hop radius (default 32): the band is searched with
+                               radius min, then sqrt(min * max), then max hops, widening only
+                               while no imbalanced node is reached (each stage a fixed point) */
   /* cost-model variants (Sec. II-B leaves both choices open); every step stays
    * bit-reproducible (integer or singly rounded fp32 operations only) */
   int32_t slope_estimator;  /* 0 = fixed-point mean of the wrapped gradients in the window
@@ -387,7 +390,8 @@ ww_status ww_batch_stats(const ww_batch* b, ww_solve_stats* out);
  * solver has fixed settings).  Unwraps `items` (a sample of the workload to
  * tune for) with the starting parameters, then walks the knobs one at a time
  * (full_passes, band_start_ppm, band_min, band_mult, band_growth,
- * ground_sink_below, search CTAs per SM, graph loop), keeping a value when it lowers the device time of the whole batched
+ * ground_sink_below, zero_stop_below, zero_band_hops, zero_band_hops_min,
+ * search CTAs per SM, graph loop), keeping a value when it lowers the device time of the whole batched
  * unwrap (CUDA events, best of `repeats` runs).  Every trial must reproduce the
  * first trial's total cost for every item (the optimum is unique in cost even
  * where flows tie); otherwise WW_ERR_INTERNAL.  *best receives the chosen

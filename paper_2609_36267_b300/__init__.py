@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
                 ("band_mult", ctypes.c_int32), ("band_growth", ctypes.c_int32),
                 ("band_start_ppm", ctypes.c_int32), ("full_passes", ctypes.c_int32),
                 ("ground_sink_below", ctypes.c_int32), ("zero_stop_below", ctypes.c_int32),
-                ("zero_band_hops", ctypes.c_int32),
+                ("zero_band_hops", ctypes.c_int32), ("zero_band_hops_min", ctypes.c_int32),
                 ("slope_estimator", ctypes.c_int32), ("cost_lookup", ctypes.c_int32)]
 
 
@@ -253,6 +253,12 @@ class Workspace:
         s = SolveStats()
         _check(lib().ww_get_solve_stats(self._h, ctypes.byref(s)), "ww_get_solve_stats")
         return s.as_dict()
+
+    def last_unwrap_pointers(self):
+        """Device addresses (residues, ground, costs, flows, potentials) of the last ww_unwrap."""
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        _check(lib().ww_workspace_last_unwrap(self._h, *[ctypes.byref(p) for p in ptrs]), "ww_workspace_last_unwrap")
+        return tuple(p.value for p in ptrs)
 
     def certify_last_unwrap(self, m: int, n: int):
         """GPU certificate counts of the last ww_unwrap on this workspace (an m x n

@@ -74,7 +74,7 @@ bool ww::params_valid(const ww_params* p) {
          (p->graph_loop == 0 || p->graph_loop == 1) && p->search_ctas_per_sm >= 0 && p->search_ctas_per_sm <= 64 &&
          p->band_min >= 1 && p->band_mult >= 0 && p->band_mult <= 1024 && p->band_growth >= 2 &&
          p->band_growth <= 64 && p->band_start_ppm >= 0 && p->band_start_ppm <= 1000000 && p->full_passes >= 0 &&
-         p->ground_sink_below >= 0 && p->zero_stop_below >= 0 && p->zero_band_hops >= 1;
+         p->ground_sink_below >= 0 && p->zero_stop_below >= 0 && p->zero_band_hops >= 1 && p->zero_band_hops_min >= 1;
 }
 
 namespace ww {
@@ -174,6 +174,7 @@ void ww_params_default(ww_params* p) {
   p->ground_sink_below = 0;
   p->zero_stop_below = 64;
   p->zero_band_hops = 512;
+  p->zero_band_hops_min = 32;
 }
 
 ww_status ww_build_lut(double nlooks, ww_lut** out) {
@@ -417,19 +418,27 @@ ww_status ww_unwrap(const void* ifg, int32_t is_complex, const float* coh, doubl
   }
   int c = is_complex ? 1 : 0;
   const void* src = ifg;
+  // validity inputs of the later steps: for a complex input the phase pass folds
+  // the mask and the coherence test into the phase (NaN = invalid), so residues
+  // and integration read the phase alone and the costs the phase and coherence
+  const uint8_t* vmask = mask;
+  const float* vcoh = coh;
   if (c) {
-    // the phase of a complex input once, then every step reads it as a float image
-    st = ww::launch_phase(ifg, m, n, ws->psi, s);
+    st = ww::launch_phase(ifg, coh, mask, m, n, ws->psi, s);
     src = ws->psi;
     c = 0;
+    vmask = nullptr;
+    vcoh = nullptr;
   }
-  if (st == WW_OK) st = ww::launch_residues(src, c, coh, mask, m, n, ws->residues, ws->ground, s);
-  if (st == WW_OK) st = ww::launch_costs(src, c, coh, mask, m, n, dt, dr, p, ws, ws->costs, s);
+  // residues are computed inside the cost tiles (same pixels, one pass)
+  if (st == WW_OK) WW_CUDA_TRY(cudaMemsetAsync(ws->ground, 0, sizeof(int32_t), s));
+  if (st == WW_OK)
+    st = ww::launch_costs(src, c, coh, vmask, m, n, dt, dr, p, ws, ws->costs, s, ws->residues, ws->ground);
   if (st == WW_OK) {
     ww::ProbHost ph{m, n, ws->residues, ws->ground, ws->costs, ws->flows, nullptr, ws->total_cost, ws->dev_status};
     st = ww::solve_problems(&ph, 1, &ws->sv, p, ws->potentials, &ws->stats, s);
   }
-  ww_status st2 = ww::launch_integrate(src, c, coh, mask, ws->flows, m, n, unwrapped, cycles, s);
+  ww_status st2 = ww::launch_integrate(src, c, vcoh, vmask, ws->flows, m, n, unwrapped, cycles, s);
   if (st == WW_OK) st = st2;
   if (total_cost && cudaMemcpyAsync(total_cost, ws->total_cost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     st = WW_ERR_CUDA;

@@ -143,7 +143,8 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
                                            int64_t m, int64_t n, const int16_t* __restrict__ table,
                                            const float* __restrict__ ratio, int w, float steep_rad,
                                            int16_t* __restrict__ costs, SteepCtr* ctr, uint32_t* __restrict__ list,
-                                           unsigned long long list_cap, int64_t bx, int64_t by) {
+                                           unsigned long long list_cap, int64_t bx, int64_t by,
+                                           int8_t* __restrict__ res = nullptr, int32_t* __restrict__ ground = nullptr) {
   __shared__ float sp[CPY][CPX];
   __shared__ float sc[CPY][CPX];
   __shared__ uint8_t sv[CPY][CPX];
@@ -233,6 +234,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   // 4. vertical sums, slope estimate, LUT gather, mask rule; steep candidates
   const int64_t P = m * n;
   unsigned cnt_valid = 0;
+  int charge = 0;  // sum of this thread's residues (Eq. 1), when res is given
   const unsigned lane = tid & 31, warp = tid >> 5;
   // block-level counting: one global atomic per block and iteration, not per warp
   __shared__ unsigned s_wtot[2][8];
@@ -290,6 +292,16 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     }
     costs[2 * P + k] = vp;
     costs[3 * P + k] = vm;
+    // residue of the node whose top-left pixel is (i,j), from the same prepared phases
+    if (res && i < m - 1 && j < n - 1) {
+      const int n_top = wrap_count(__fsub_rn(sp[R][C + 1], sp[R][C]));
+      const int n_right = wrap_count(__fsub_rn(sp[R + 1][C + 1], sp[R][C + 1]));
+      const int n_bottom = wrap_count(__fsub_rn(sp[R + 1][C + 1], sp[R + 1][C]));
+      const int n_left = wrap_count(__fsub_rn(sp[R + 1][C], sp[R][C]));
+      const int rr = -(n_top + n_right - n_bottom - n_left);
+      res[i * (n - 1) + j] = (int8_t)rr;
+      charge += rr;
+    }
     }
     // count the candidates (warp ballots, then the block); the block's base in the
     // list plus the earlier warps' counts place each warp's keys
@@ -319,11 +331,21 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   }
   for (int o = 16; o > 0; o >>= 1) cnt_valid += __shfl_xor_sync(0xffffffffu, cnt_valid, o);
   if (lane == 0) s_valid[warp] = cnt_valid;
+  __shared__ int s_charge[8];
+  if (res) {
+    for (int o = 16; o > 0; o >>= 1) charge += __shfl_xor_sync(0xffffffffu, charge, o);
+    if (lane == 0) s_charge[warp] = charge;
+  }
   __syncthreads();
   if (tid == 0) {
     unsigned long long v = 0;
     for (int w2 = 0; w2 < 8; ++w2) v += s_valid[w2];
     if (v) atomicAdd(&ctr->valid_edges, v);
+    if (res) {
+      int t = 0;
+      for (int w2 = 0; w2 < 8; ++w2) t += s_charge[w2];
+      if (t) atomicAdd(ground, -t);  // the ground takes minus the total charge
+    }
   }
 }
 
@@ -333,16 +355,18 @@ __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int
                                                const uint8_t* __restrict__ mask, int64_t m, int64_t n,
                                                const int16_t* __restrict__ table, const float* __restrict__ ratio,
                                                int w, float steep_rad, int16_t* __restrict__ costs, SteepCtr* ctr,
-                                               uint32_t* list, unsigned long long list_cap) {
+                                               uint32_t* list, unsigned long long list_cap, int8_t* res,
+                                               int32_t* ground) {
   // one-dimensional grid of tiles (gridDim.y would cap the rows at 65535 tiles)
   const int64_t gx = (n + CTX - 1) / CTX, b = blockIdx.x;
   costs_tile<SLOPE, LOOKUP>(ifg, is_complex, coh, mask, m, n, table, ratio, w, steep_rad, costs, ctr, list, list_cap,
-                            b % gx, b / gx);
+                            b % gx, b / gx, res, ground);
 }
 
 // the k_costs variant for a parameter set
 using CostsKernel = void (*)(const void*, int, const float*, const uint8_t*, int64_t, int64_t, const int16_t*,
-                             const float*, int, float, int16_t*, SteepCtr*, uint32_t*, unsigned long long);
+                             const float*, int, float, int16_t*, SteepCtr*, uint32_t*, unsigned long long, int8_t*,
+                             int32_t*);
 CostsKernel costs_kernel(const ww_params* p) {
   if (p->slope_estimator == 0) return p->cost_lookup == 0 ? k_costs<0, 0> : k_costs<0, 1>;
   return p->cost_lookup == 0 ? k_costs<1, 0> : k_costs<1, 1>;
@@ -641,17 +665,37 @@ __device__ __forceinline__ void integrate_row(const void* ifg, int is_complex, c
   if (threadIdx.x == 0) carry_s = cycles[row];  // K(i,0) from the column pass
   __syncthreads();
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // validity from the phase alone (NaN = invalid) with 8-byte aligned rows: each
+  // thread's 8 pixels come as two 128-bit phase loads and one 64-bit flow load
+  const bool vec = !is_complex && !coh && !mask && (n & 7) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(ifg) | reinterpret_cast<uintptr_t>(flows) |
+                     reinterpret_cast<uintptr_t>(unw) | reinterpret_cast<uintptr_t>(cycles)) & 15) == 0;
   for (int64_t seg = 0; seg < n; seg += kRowThreads * kRowItems) {
     int64_t j0 = seg + (int64_t)threadIdx.x * kRowItems;
     float psi[kRowItems];
     bool val[kRowItems];
+    int8_t fl[kRowItems];
+    if (vec && j0 + kRowItems <= n) {
+      const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(ifg) + row + j0);
+      const float4 a = __ldg(src), b = __ldg(src + 1);
+      const float raw[kRowItems] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      const uint2 f = __ldg(reinterpret_cast<const uint2*>(flows + row + j0));
 #pragma unroll
-    for (int t = 0; t < kRowItems; ++t) {
-      int64_t j = j0 + t;
-      Pix p{0.0f, 0.0f, false};
-      if (j < n) p = load_pixel(ifg, is_complex, coh, mask, row + j);
-      psi[t] = p.psi;
-      val[t] = p.valid;
+      for (int t = 0; t < kRowItems; ++t) {
+        val[t] = isfinite(raw[t]);
+        psi[t] = val[t] ? raw[t] : 0.0f;
+        fl[t] = (int8_t)(((t < 4 ? f.x : f.y) >> (8 * (t & 3))) & 0xFFu);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < kRowItems; ++t) {
+        int64_t j = j0 + t;
+        Pix p{0.0f, 0.0f, false};
+        if (j < n) p = load_pixel(ifg, is_complex, coh, mask, row + j);
+        psi[t] = p.psi;
+        val[t] = p.valid;
+        fl[t] = j < n ? flows[row + j] : (int8_t)0;
+      }
     }
     first_psi[threadIdx.x] = psi[0];
     __syncthreads();
@@ -671,7 +715,7 @@ __device__ __forceinline__ void integrate_row(const void* ifg, int is_complex, c
       int32_t inc = 0;
       if (j + 1 < n) {
         float b = t + 1 < kRowItems ? psi[t + 1] : next_psi;
-        inc = (int32_t)flows[row + j] - wrap_count(__fsub_rn(b, psi[t]));
+        inc = (int32_t)fl[t] - wrap_count(__fsub_rn(b, psi[t]));
       }
       local[t] = s;  // exclusive prefix within this thread
       s += inc;
@@ -690,20 +734,34 @@ __device__ __forceinline__ void integrate_row(const void* ifg, int is_complex, c
       total += ws[k];
     }
     int32_t base = carry_s + add + (v - s);
+    int32_t Ks[kRowItems];
+    float outs[kRowItems];
 #pragma unroll
     for (int t = 0; t < kRowItems; ++t) {
-      int64_t j = j0 + t;
-      if (j >= n) break;
-      int32_t K = base + local[t];
-      cycles[row + j] = K;
-      float out;
+      const int32_t K = base + local[t];
+      Ks[t] = K;
       if (val[t]) {
         double tt = __dmul_rn((double)K, kTwoPiD);
-        out = __double2float_rn(__dadd_rn((double)psi[t], tt));
+        outs[t] = __double2float_rn(__dadd_rn((double)psi[t], tt));
       } else {
-        out = __int_as_float(0x7fc00000);
+        outs[t] = __int_as_float(0x7fc00000);
       }
-      unw[row + j] = out;
+    }
+    if (vec && j0 + kRowItems <= n) {
+      int4* kc = reinterpret_cast<int4*>(cycles + row + j0);
+      float4* uo = reinterpret_cast<float4*>(unw + row + j0);
+      kc[0] = make_int4(Ks[0], Ks[1], Ks[2], Ks[3]);
+      kc[1] = make_int4(Ks[4], Ks[5], Ks[6], Ks[7]);
+      uo[0] = make_float4(outs[0], outs[1], outs[2], outs[3]);
+      uo[1] = make_float4(outs[4], outs[5], outs[6], outs[7]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < kRowItems; ++t) {
+        const int64_t j = j0 + t;
+        if (j >= n) break;
+        cycles[row + j] = Ks[t];
+        unw[row + j] = outs[t];
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) carry_s += total;
@@ -1048,18 +1106,26 @@ namespace {
 // Wrapped phase of a complex interferogram, once per pixel (fixed-point CORDIC); a
 // non-finite sample gives NaN, which the float-input kernels treat as invalid
 // exactly as the complex-input kernels treat the non-finite sample.
-__global__ void k_phase(const float2* __restrict__ z, int64_t P, float* __restrict__ psi) {
+// With coh/mask given, every validity test of a pixel (mask, finite coherence,
+// finite sample) is folded into the phase as NaN, so the later steps can read
+// the phase alone for validity.
+__global__ void k_phase(const float2* __restrict__ z, const float* __restrict__ coh, const uint8_t* __restrict__ mask,
+                        int64_t P, float* __restrict__ psi) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     const float2 v = __ldg(z + k);
-    psi[k] = (isfinite(v.x) && isfinite(v.y)) ? cordic_phase(v.x, v.y) : __int_as_float(0x7fc00000);
+    bool ok = isfinite(v.x) && isfinite(v.y);
+    if (coh) ok = ok && isfinite(__ldg(coh + k));
+    if (mask) ok = ok && __ldg(mask + k) != 0;
+    psi[k] = ok ? cordic_phase(v.x, v.y) : __int_as_float(0x7fc00000);
   }
 }
 }  // namespace
 
-ww_status launch_phase(const void* ifg, int64_t m, int64_t n, float* psi, cudaStream_t s) {
+ww_status launch_phase(const void* ifg, const float* coh, const uint8_t* mask, int64_t m, int64_t n, float* psi,
+                       cudaStream_t s) {
   const int64_t P = m * n;
   int blocks = (int)std::min<int64_t>((P + 255) / 256, 148 * 16);
-  k_phase<<<blocks, 256, 0, s>>>(reinterpret_cast<const float2*>(ifg), P, psi);
+  k_phase<<<blocks, 256, 0, s>>>(reinterpret_cast<const float2*>(ifg), coh, mask, P, psi);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
 }
@@ -1070,7 +1136,7 @@ int64_t steep_list_capacity(int64_t pixels, int32_t cap_ppm) {
 
 ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                        int64_t m, int64_t n, const int16_t* dtable, const float* dratio, const ww_params* p,
-                       ww_workspace* ws, int16_t* costs, cudaStream_t s) {
+                       ww_workspace* ws, int16_t* costs, cudaStream_t s, int8_t* res, int32_t* ground) {
   if (p->cost_lookup == 1 && !dratio) return WW_ERR_INVALID_ARG;
   SteepCtr* ctr = reinterpret_cast<SteepCtr*>(ws->steep_ctr);
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
@@ -1081,7 +1147,8 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
   uint32_t* list = use_list ? ws->steep_list : nullptr;
   const unsigned long long list_cap = use_list ? (unsigned long long)ws->steep_list_cap : 0ull;
   costs_kernel(p)<<<cost_tiles(m, n), 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, dtable, dratio,
-                                                   p->box_half_width, p->steep_rad, costs, ctr, list, list_cap);
+                                                   p->box_half_width, p->steep_rad, costs, ctr, list, list_cap, res,
+                                                   ground);
   WW_CUDA_TRY(cudaGetLastError());
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
   if (use_list) k_steep_zero_list<<<148 * 4, 256, 0, s>>>(ctr, list, list_cap, m * n, costs);
@@ -1316,7 +1383,7 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   WW_CUDA_TRY(cudaMemsetAsync(hist, 0, 65536 * sizeof(uint32_t), s));
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
   k_costs<0, 0><<<cost_tiles(m, n), 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, nullptr, p->box_half_width,
-                                                 p->steep_rad, costs, ctr, nullptr, 0ull);
+                                                 p->steep_rad, costs, ctr, nullptr, 0ull, nullptr, nullptr);
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
   const int hist_blocks = 148 * 8;
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, hist, 0);

@@ -310,12 +310,17 @@ ww_status launch_residues(const void* ifg, int is_complex, const float* coh, con
                           int64_t m, int64_t n, int8_t* res, int32_t* ground, cudaStream_t s);
 ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                        int64_t m, int64_t n, const int16_t* dtable, const float* dratio, const ww_params* p,
-                       ww_workspace* ws, int16_t* costs, cudaStream_t s);
+                       ww_workspace* ws, int16_t* costs, cudaStream_t s, int8_t* res = nullptr,
+                       int32_t* ground = nullptr);
+// (res, ground given: the residues of Eq. 1 and the ground charge are written by
+// the same tiles; *ground must be zero before the call)
 ww_status launch_integrate(const void* ifg, int is_complex, const float* coh, const uint8_t* mask,
                            const int8_t* flows, int64_t m, int64_t n, float* unw, int32_t* cyc,
                            cudaStream_t s);
-// psi[k] = CORDIC phase of a complex64 image (NaN where a sample is not finite)
-ww_status launch_phase(const void* ifg, int64_t m, int64_t n, float* psi, cudaStream_t s);
+// psi[k] = CORDIC phase of a complex64 image, NaN where a sample is not finite
+// and (when given) where the mask is 0 or the coherence is not finite
+ww_status launch_phase(const void* ifg, const float* coh, const uint8_t* mask, int64_t m, int64_t n, float* psi,
+                       cudaStream_t s);
 // Connected-component labels over reliable edges (ww_cc.cu).
 ww_status launch_components(const int16_t* costs, const int8_t* flows, const float* unwrapped, int64_t m, int64_t n,
                             int32_t threshold, int32_t* labels, cudaStream_t s);

@@ -109,7 +109,9 @@ struct McfCtr {
   // zero-distance first band (late passes): the band keeps only labels of distance
   // 0 and fewer than zero_hops hops; augmenting inside it changes no potential (D = 0)
   int32_t zstop;       // this pass starts with such a band
-  uint32_t zero_hops;
+  uint32_t zero_hops;  // largest hop radius of the zero band
+  uint32_t zhop[3];    // hop radius of each stage of the zero band (widened while nothing is reached)
+  int32_t zstage;      // current stage
   uint32_t zero_stop_below;  // use it while at most this many nodes are imbalanced
   uint32_t cap0;       // the pass's ordinary first cap (after the zero band)
   // first negative reduced cost seen (diagnostics): flag, node, direction, value, pass
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
   const int ring = (int)b.t_total + (int)gridDim.x + 64;
   const int64_t pG = pot[b.g_index];
   const uint32_t cap = ctr->cap;
-  // the zero band keeps keys (0, hops < zero_hops): distance 0 within a hop radius
-  const uint64_t capK = (ctr->zstop != 0 && cap == 1u) ? (uint64_t)ctr->zero_hops
+  // the zero band keeps keys (0, hops < radius): distance 0 within the stage's hop radius
+  const uint64_t capK = (ctr->zstop != 0 && cap == 1u) ? (uint64_t)ctr->zhop[ctr->zstage]
                         : (cap == 0xFFFFFFFFu ? KINF : ((uint64_t)cap << 29));
   const bool gsink = ctr->gsink != 0;
   const uint32_t wait_polls = ctr->wait_polls;
@@ -635,6 +637,7 @@ __global__ void k_pass_setup(McfCtr* ctr, SearchQ* q) {
   }
   ctr->cap0 = cap;
   ctr->zstop = (cap != 0xFFFFFFFFu && (uint32_t)ctr->ncand <= ctr->zero_stop_below) ? 1 : 0;
+  ctr->zstage = 0;
   if (ctr->zstop) cap = 1;  // distance 0 only: the zero band first
   ctr->cap = cap;
   ctr->gsink = (uint32_t)ctr->ncand <= ctr->ground_sink_below ? 1 : 0;
@@ -727,7 +730,9 @@ __global__ void k_band_decide(McfCtr* ctr, SearchQ* q, int last_band) {
   bool again = ctr->cap != 0xFFFFFFFFu && ctr->found == 0 && ctr->capped_any && ctr->err == 0;
   if (again) {
     const unsigned long long w = (unsigned long long)ctr->cap * ctr->band_growth;
-    if (ctr->zstop && ctr->cap == 1u) {
+    if (ctr->zstop && ctr->cap == 1u && ctr->zstage < 2 && ctr->zhop[ctr->zstage + 1] > ctr->zhop[ctr->zstage]) {
+      ctr->zstage += 1;  // the zero band with the next hop radius
+    } else if (ctr->zstop && ctr->cap == 1u) {
       ctr->cap = ctr->cap0;  // after the zero band: the pass's ordinary first band
       ctr->zstop = 0;
     } else {
@@ -1258,7 +1263,9 @@ int search_grid_size(int sm_count, int want_per_sm) {
   return std::min(sm_count * k, kMaxSearchGrid);
 }
 
-constexpr int kBands = 4;  // cap c, 8c, 64c, then unbounded
+// band launches per pass: up to three zero-band stages, then caps c, 8c, 64c and
+// further x8 steps until the second-to-last launch opens the cap completely
+constexpr int kBands = 7;
 
 // Joining problems (grid: x strides, y over the joiners): tile -> problem map,
 // zero flows and per-problem counters.
@@ -1333,6 +1340,14 @@ Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params
   hc->ground_sink_below = (uint32_t)std::max(0, prm->ground_sink_below);
   hc->zero_stop_below = (uint32_t)std::max(0, prm->zero_stop_below);
   hc->zero_hops = (uint32_t)std::max(1, std::min(prm->zero_band_hops, (1 << 29) - 1));
+  // zero-band stages: from zero_band_hops_min to zero_band_hops, geometric
+  {
+    const double lo = std::max(1, std::min(prm->zero_band_hops_min, (int32_t)hc->zero_hops));
+    const double hi = hc->zero_hops;
+    hc->zhop[0] = (uint32_t)lo;
+    hc->zhop[1] = (uint32_t)std::max(lo, std::min(hi, std::round(std::sqrt(lo * hi))));
+    hc->zhop[2] = (uint32_t)hi;
+  }
   hc->wait_polls = (uint32_t)std::max(1, prm->wait_polls);
   // the worklist flags and ring start empty (a search that stopped on an error
   // may have left entries behind); the ground potential starts at 0 unless a

@@ -68,6 +68,7 @@ extern "C" ww_status ww_autotune_batch(ww_batch_item* items, int64_t count, cons
       {&ww_params::ground_sink_below, {0, 64, 1024, 16384}},
       {&ww_params::zero_stop_below, {64, 0, 16, 256}},
       {&ww_params::zero_band_hops, {512, 128, 2048}},
+      {&ww_params::zero_band_hops_min, {32, 8, 128, 512}},
       {&ww_params::search_ctas_per_sm, {0, 4, 2}},
       {&ww_params::graph_loop, {1, 0}},
   };

@@ -144,3 +144,19 @@ def band_certificate(res, costs, flows, pot, a, b):
                    + flows[1, i, : n - 1].astype(np.int64) - flows[1, i, 1:])
             bad += np.count_nonzero(net != res[i])
     return bad
+
+
+def device_array(ptr, shape, dtype):
+    """A host copy of a device array given by its raw address (library workspace memory)."""
+    import ctypes
+
+    import torch
+
+    count = int(np.prod(shape)) * np.dtype(dtype).itemsize
+    out = np.empty(shape, dtype)
+    torch.cuda.synchronize()
+    lib = "/usr/local/cuda/lib64/libcudart.so"
+    cudart = ctypes.CDLL(lib if os.path.exists(lib) else "libcudart.so")
+    cudart.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    assert cudart.cudaMemcpy(out.ctypes.data, ctypes.c_void_p(ptr), count, 2) == 0  # device to host
+    return out

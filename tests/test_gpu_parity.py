@@ -11,7 +11,8 @@ import oracle
 import paper_2609_36267_b300 as ww
 from paper_2609_36267_b300 import synth
 
-from gpu_helpers import (device_inputs, golden_table, numpy_certificate, oracle_pipeline, probe_table, to_dev)
+from gpu_helpers import (device_array, device_inputs, golden_table, numpy_certificate, oracle_pipeline, probe_table,
+                         to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -282,7 +283,7 @@ def test_all_masked_and_single_valid_pixel(ws):
         assert np.isnan(u).sum() == x.mask.size - keep
 
 
-@pytest.mark.parametrize("name", ["cfg1_256", "complex_300x333_mask", "cfg2_512"])
+@pytest.mark.parametrize("name", ["cfg1_256", "complex_300x333_mask", "cfg2_512", "ragged_257x301_mask"])
 def test_unwrap_end_to_end(name, ws):
     """Whole path with the library's own table; optimal cost equal to the
     oracle's optimum on the same table values, rewrap within 1e-5 rad."""
@@ -296,6 +297,13 @@ def test_unwrap_end_to_end(name, ws):
     ref = oracle_pipeline(x, lib_tab)
     st_o, flows_o, _, tc_o = oracle.solve_mcf(ref["res"], ref["g"], ref["costs"])
     assert st_o == 0 and tc == tc_o
+    # the residues and cost planes this call computed (in one fused pass for a
+    # complex input), read back from the workspace: bit-exact
+    m, n = x.shape
+    p_res, p_g, p_costs, _, _ = ws.last_unwrap_pointers()
+    assert np.array_equal(device_array(p_res, (m - 1, n - 1), np.int8), ref["res"])
+    assert int(device_array(p_g, (1,), np.int32)[0]) == ref["g"]
+    assert np.array_equal(device_array(p_costs, (4, m, n), np.int16), ref["costs"])
     v = ~np.isnan(u)
     assert np.array_equal(v, ref["valid"].astype(bool))
     exact = ref["psi"].astype(np.float64) + 2 * np.pi * Kn
