@@ -101,9 +101,10 @@ typedef struct ww_params {
                                roots, and augments there if it reaches an imbalanced node
                                (zero-cost paths, no potential change); default 64; 0 = never */
   int32_t zero_band_hops;   /* largest hop radius of that first band (default 512) */
-  int32_t zero_band_hops_min; /* its first hop radius (default 32): the band is searched with
-                               radius min, then sqrt(min * max), then max hops, widening only
-                               while no imbalanced node is reached (each stage a fixed point) */
+  int32_t zero_band_hops_min; /* its first hop radius (default 512 = one stage): below
+                               zero_band_hops the band is searched with radius min, then
+                               sqrt(min * max), then max hops, widening only while no
+                               imbalanced node is reached (each stage a fixed point) */
   /* cost-model variants (Sec. II-B leaves both choices open); every step stays
    * bit-reproducible (integer or singly rounded fp32 operations only) */
   int32_t slope_estimator;  /* 0 = fixed-point mean of the wrapped gradients in the window

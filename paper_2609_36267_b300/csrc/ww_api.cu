@@ -174,7 +174,7 @@ void ww_params_default(ww_params* p) {
   p->ground_sink_below = 0;
   p->zero_stop_below = 64;
   p->zero_band_hops = 512;
-  p->zero_band_hops_min = 32;
+  p->zero_band_hops_min = 512;
 }
 
 ww_status ww_build_lut(double nlooks, ww_lut** out) {

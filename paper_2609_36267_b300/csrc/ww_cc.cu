@@ -3,16 +3,17 @@
 // difference by +1 or -1 would raise the MCF objective by more than a
 // threshold; components grow over reliable edges.
 //
-// Union-find on the label array itself (int32 parent pointers):
+// Union-find on the label array itself, which holds parent + 1 (0 = invalid
+// pixel), so a root holds its own label and the compressed array is the result:
 //   1. rows: one warp per row links each valid pixel to the start of its run
 //      of reliable horizontal edges (ballot per 32 pixels, the run carried
-//      across segments); a run start is its own root, an invalid pixel -1;
+//      across segments); a run start is its own root;
 //   2. one thread per pixel unites it with its lower neighbour over a reliable
 //      vertical edge: the larger of the two roots is hooked under the smaller
 //      by compare-and-swap (a root's pointer changes only from itself), and
 //      finds halve their paths with plain stores of an ancestor;
-//   3. every pixel's pointer is set to its root by read-only finds;
-//   4. labels = root + 1 (0 where invalid), element by element.
+//   3. every pixel's pointer is set to its root by read-only finds, which
+//      leaves root + 1 (the label) in every valid pixel.
 // Pointers only ever point to smaller indices, so every chain ends at a root
 // within as many steps as its start index and each component's root is its
 // smallest row-major index: the labels are unique, whatever the schedule.
@@ -26,8 +27,9 @@
 namespace ww {
 namespace {
 
+// parent index of x (the array stores parent + 1; -1 for an invalid pixel)
 __device__ __forceinline__ int32_t ld_parent(const int32_t* parent, int32_t x) {
-  return *((volatile const int32_t*)(parent + x));
+  return *((volatile const int32_t*)(parent + x)) - 1;
 }
 
 // Root of x with path halving (each visited node skips to its grandparent).
@@ -36,7 +38,7 @@ __device__ __forceinline__ int32_t find_halving(int32_t* parent, int32_t x) {
     const int32_t p = ld_parent(parent, x);
     if (p == x) return x;
     const int32_t gp = ld_parent(parent, p);
-    if (gp != p) parent[x] = gp;
+    if (gp != p) parent[x] = gp + 1;
     x = gp;
   }
   return x;  // not reached: the chain from x has at most x steps
@@ -63,7 +65,7 @@ __device__ __forceinline__ void unite(int32_t* parent, int32_t a, int32_t b) {
       a = b;
       b = t;
     }
-    if (atomicCAS(parent + b, b, a) == b) return;
+    if (atomicCAS(parent + b, b + 1, a + 1) == b + 1) return;
   }
 }
 
@@ -99,7 +101,7 @@ __global__ void k_cc_rows(const int16_t* __restrict__ costs, const int8_t* __res
       const unsigned upto = starts & (0xffffffffu >> (31 - lane));
       // a linked pixel with no start at or below its lane continues the previous segment's run
       const int32_t root = upto ? (int32_t)(i * n + j0 + (31 - __clz(upto))) : carry;
-      if (j < n) parent[k] = valid ? root : -1;
+      if (j < n) parent[k] = valid ? root + 1 : 0;
       carry = __shfl_sync(0xffffffffu, root, 31);
     }
   }
@@ -123,13 +125,8 @@ __global__ void k_cc_compress(int64_t P, int32_t* parent) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p = ld_parent(parent, (int32_t)k);
     if (p < 0 || p == (int32_t)k) continue;
-    parent[k] = find_readonly(parent, p);
+    parent[k] = find_readonly(parent, p) + 1;
   }
-}
-
-__global__ void k_cc_labels(int64_t P, int32_t* labels) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
-    labels[k] = labels[k] + 1;  // root index + 1; -1 (invalid) becomes 0
 }
 
 }  // namespace
@@ -146,7 +143,6 @@ ww_status launch_components(const int16_t* costs, const int8_t* flows, const flo
   k_cc_rows<<<row_blocks, 256, 0, s>>>(costs, flows, unwrapped, m, n, threshold, labels);
   if (m > 1) k_cc_cols<<<blocks, 256, 0, s>>>(costs, flows, unwrapped, m, n, threshold, labels);
   k_cc_compress<<<blocks, 256, 0, s>>>(P, labels);
-  k_cc_labels<<<blocks, 256, 0, s>>>(P, labels);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
 }

@@ -423,6 +423,7 @@ class Session {
   int64_t n_total = 0, t_high = 0, max_nodes = 1, n_border = 0, max_garcs = 1;
   int parity = 0;
   bool capturing = false;  // enqueue_pass is being captured into a graph body
+  bool staged_zero = false;  // the zero band's hop radius grows in stages
   bool ncand_unknown = false;
 };
 

@@ -1263,9 +1263,10 @@ int search_grid_size(int sm_count, int want_per_sm) {
   return std::min(sm_count * k, kMaxSearchGrid);
 }
 
-// band launches per pass: up to three zero-band stages, then caps c, 8c, 64c and
-// further x8 steps until the second-to-last launch opens the cap completely
-constexpr int kBands = 7;
+// band launches per pass: the zero band (one stage, or up to three when its hop
+// radius is staged), then caps c, 8c, ... until the second-to-last launch opens
+// the cap completely
+constexpr int kBands = 4, kBandsStaged = 6;
 
 // Joining problems (grid: x strides, y over the joiners): tile -> problem map,
 // zero flows and per-problem counters.
@@ -1347,6 +1348,7 @@ Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params
     hc->zhop[0] = (uint32_t)lo;
     hc->zhop[1] = (uint32_t)std::max(lo, std::min(hi, std::round(std::sqrt(lo * hi))));
     hc->zhop[2] = (uint32_t)hi;
+    staged_zero = hc->zhop[0] < hc->zhop[2];
   }
   hc->wait_polls = (uint32_t)std::max(1, prm->wait_polls);
   // the worklist flags and ring start empty (a search that stopped on an error
@@ -1502,13 +1504,14 @@ ww_status Session::enqueue_pass() {
   if (!capturing) WW_CUDA_TRY(cudaEventRecord(ev[0], s));
   const dim3 ga(grid_blocks(max_garcs, 256, std::max(1, sm_count * 4 / std::max(1, b.nact) + 1)),
                 (unsigned)std::max(1, b.nact));
-  for (int band = 0; band < kBands; ++band) {
+  const int bands = staged_zero ? kBandsStaged : kBands;
+  for (int band = 0; band < bands; ++band) {
     k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped,
                                                          sv->touched, sv->tlist);
     k_ground_dist<FWD><<<ga, 256, 0, s>>>(b, sv->labels, pot, ctr);
     k_count_found<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->labels, sv->cand, 0, ctr);
-    k_band_decide<<<1, 1, 0, s>>>(ctr, q, band == kBands - 2 ? 1 : 0);
-    if (band + 1 < kBands)
+    k_band_decide<<<1, 1, 0, s>>>(ctr, q, band == bands - 2 ? 1 : 0);
+    if (band + 1 < bands)
       k_reseed<<<grid_tiles, 256, 0, s>>>(b, sv->capped, q, sv->slots, sv->inq, search_grid, ctr);
   }
   if (!capturing) WW_CUDA_TRY(cudaEventRecord(ev[1], s));
