@@ -401,13 +401,14 @@ def run_ours(args, rank, world, local):
                 "gpu_launches": None, "roofline": roof, "cpu_baseline": base, "clocks": clk.summary(),
                 "solver": {k: st[k] for k in ("passes", "augmentations", "search_iterations", "tile_visits",
                                                  "settled_visits", "residues", "ms_search_gpu", "ms_other",
-                                                 "local_rounds", "visit_cycles", "load_cycles", "relax_cycles")},
+                                                 "local_rounds", "visit_cycles", "load_cycles", "relax_cycles",
+                                                 "narrow_visits", "narrow_redone")},
                 "total_costs_seen": sorted(costs_seen),
                 "certified": bool(certified),
                 "certificate": {"capacity_violations": cert[0], "conservation_violations": cert[1],
                                 "negative_reduced_costs": cert[2], "total_cost": cert[3],
                                 "table": "library FP64 table for L=50, equal entrywise to the oracle's"}}
-        line["gpu_launches"] = launch_count(st, args.steps)
+        line["gpu_launches"] = launch_count(st, args.steps, prm)
         if not args.no_extras:
             line["components"] = measure_components(ww, torch, x, ifg, coh, mask, unw, ws, max(3, args.steps), peak,
                                                     peak_kind)
@@ -858,16 +859,18 @@ def run_served(args, summary=False):
     print(json.dumps(line), flush=True)
 
 
-def launch_count(st, steps):
+def launch_count(st, steps, prm):
     """Kernels of this library launched per timed step (host-driven pass loop), times steps."""
     # phase (complex input, validity folded in), costs with the residues fused, steep
     # plan/zero_list/hist x2/find x2/ties/scan/zero, integrate col0/rows
     grid = 13
     solver_fixed = 8  # join_clear, join, init_state, resume, zero_slots, total_cost, copy_pot, write_results
-    # pass_setup, set_roots, seed_tiles, 7 bands x (search, ground_dist, count_found, band_decide)
-    # + 6 reseeds, clear_capped, select, select_ground, augment, augment_ground, reset_best,
+    # bands per pass: 4, or 6 when the zero band's hop radius grows in stages
+    bands = 6 if prm.zero_band_hops_min < prm.zero_band_hops else 4
+    # pass_setup, set_roots, seed_tiles, bands x (search, ground_dist, count_found, band_decide)
+    # + (bands - 1) reseeds, clear_capped, select, select_ground, augment, augment_ground, reset_best,
     # potentials, potential_ground, compact, finish_pass
-    per_pass = 3 + 7 * 4 + 6 + 10
+    per_pass = 3 + bands * 4 + (bands - 1) + 10
     return int((grid + solver_fixed + st["passes"] * per_pass) * steps)
 
 

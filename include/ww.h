@@ -244,6 +244,8 @@ typedef struct ww_solve_stats {
   int64_t load_cycles;   /* of which: loading labels and computing reduced arc costs */
   int64_t relax_cycles;  /* of which: the local fixed point (directional scans) */
   int64_t settled_visits; /* nodes reached (finite label) at the end of a tile visit, summed over visits */
+  int64_t narrow_visits;  /* tile visits relaxed in 32-bit keys (label spans small enough) */
+  int64_t narrow_redone;  /* of which redone in 64-bit keys (a candidate left the 32-bit range) */
 } ww_solve_stats;
 ww_status ww_get_solve_stats(const ww_workspace* ws, ww_solve_stats* out);
 

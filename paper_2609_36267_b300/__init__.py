@@ -57,7 +57,8 @@ class SolveStats(ctypes.Structure):
                 ("ms_search", ctypes.c_double), ("ms_other", ctypes.c_double),
                 ("ms_search_gpu", ctypes.c_double), ("local_rounds", ctypes.c_int64),
                 ("visit_cycles", ctypes.c_int64), ("load_cycles", ctypes.c_int64),
-                ("relax_cycles", ctypes.c_int64), ("settled_visits", ctypes.c_int64)]
+                ("relax_cycles", ctypes.c_int64), ("settled_visits", ctypes.c_int64),
+                ("narrow_visits", ctypes.c_int64), ("narrow_redone", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

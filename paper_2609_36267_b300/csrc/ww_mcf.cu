@@ -120,6 +120,8 @@ struct McfCtr {
   int32_t dbg_pass, dbg_pad;
   int32_t ntouched;    // tiles listed as visited in this pass
   uint32_t wait_polls; // polls of a worklist wait before it gives up (WW_ERR_TIMEOUT)
+  unsigned long long visits32;  // tile visits relaxed in 32-bit keys
+  unsigned long long redo64;    // of which redone in 64-bit keys (a candidate left the 32-bit range)
 };
 
 // Problems live in slots (stable ids); `order` lists the active slots sorted by
@@ -225,85 +227,266 @@ __device__ int q_pop(int ring, SearchQ* q, int32_t* slots, int32_t* inq, uint32_
 constexpr uint64_t KINF = kInf >> 3;                  // (distance, hops) part of an unreached label
 constexpr uint64_t KDIST_INF = 0xFFFFFFFFull << 29;   // distance field all ones
 
-__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
-  uint64_t s = a + b;  // a, b <= KINF < 2^61: no wrap
-  return s < KINF ? s : KINF;
+// Label keys of the local relaxation in two widths.
+//  64-bit cells: (distance:32 | hops:29 | dir:3); a kept distance that overflows
+//    32 bits is reported.
+//  32-bit cells: (distance - d0:13 | hops - h0:15 | dir:3), relative to the
+//    smallest distance d0 and hop count h0 among the finite labels of the tile
+//    and its halo.  Subtracting the same d0 and h0 from every label keeps the
+//    (distance, hops, dir) order and commutes with adding an arc, so a visit gives
+//    the same labels in either width as long as every key it keeps fits: the
+//    visit's finite labels span fewer than kDistSpan32 distance units and at most
+//    kHopSpan32 hops, and the visit converges within kRounds32 rounds (a value
+//    carried in a round is a label read in that round plus at most one arc per
+//    sweep step of the round, 4 x 32, so no hop field carries); else the visit is
+//    redone in 64 bits.  The arc weights are clamped to kDistSpan32 units; a
+//    finite key plus a clamped weight stays below 2^29 - 1 (the unreached key), so
+//    every candidate is either unreached, at or beyond capK, or kept, as in 64
+//    bits.  capK is the band's cap relative to d0 when that is at most kDistSpan32
+//    units, else the local limit kDistSpan32 << 15: a candidate dropped there may
+//    lie inside the band, and the visit is then redone in 64 bits.
+constexpr uint32_t kDistSpan32 = 8191;         // distance span of a 32-bit visit (exclusive)
+constexpr uint32_t kHopSpan32 = 16383;         // hop span of the labels entering a 32-bit visit
+constexpr int kRounds32 = 64;                  // rounds of a 32-bit visit (16383 + 64 * 129 < 2^15)
+constexpr uint32_t KINF32 = 0x1FFFFFFFu;      // key of an unreached 32-bit cell (0xFFFFFFFF >> 3)
+constexpr uint32_t kLocalCap32 = kDistSpan32 << 15;
+
+// 32-bit weight of an arc of reduced cost w (kNoArc: no arc): +w distance (clamped), +1 hop
+__device__ __forceinline__ uint32_t weight32(uint32_t w) {
+  return w == kNoArc ? KINF32 : ((min(w, kDistSpan32) << 15) + 1u);
 }
 
-__device__ __forceinline__ uint64_t arc_weight(uint32_t w) {
-  return w == kNoArc ? KINF : (((uint64_t)w << 29) + 1ull);  // +w distance, +1 hop
-}
-
-// Segmented directional min-plus scan over four 32-cell lines per warp.
-// Lane = 8*line + seg; seg owns cells 4*seg .. 4*seg+3 of its line (in scan
-// order when forward, mirrored when backward).  For one line with cells k in
-// scan order, labels K_k (distance,hops) and entering-arc weights b_k:
-//   c_k = min(K_k, c_{k-1} + b_k),  c_{-1} = halo,
-// computed as a sequential pass inside each segment, an exclusive scan of the
-// segment aggregates (A, B) across the 8 segments (operator
-// (A1,B1).(A2,B2) = (min(A2, A1+B2), B1+B2)), and a sequential fix-up that
-// offers every cell the candidate from its predecessor (direction code dir).
-// `cell(k)` / `wt(k)` address the lane's k-th cell in scan order.
-template <bool FORWARD, class CellF, class WtF>
-__device__ __forceinline__ unsigned scan_segments(CellF cell, WtF wt, uint64_t halo_key, int dir, int seg,
-                                                  uint64_t capK, bool* capped, int* err) {
-  uint64_t K[4], b[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    K[k] = *cell(k) >> 3;
-    b[k] = arc_weight(wt(k));
+template <class KT>
+struct Keys;
+template <>
+struct Keys<uint64_t> {
+  static constexpr int kRounds = kMaxLocalSweeps;
+  __device__ static __forceinline__ uint64_t inf() { return KINF; }
+  // the arc-weight planes hold reduced costs
+  __device__ static __forceinline__ uint64_t weight(uint32_t w) {
+    return w == kNoArc ? KINF : (((uint64_t)w << 29) + 1ull);  // +w distance, +1 hop
   }
-  uint64_t A = K[0], B = b[0];
-#pragma unroll
-  for (int k = 1; k < 4; ++k) {
-    A = min(K[k], sat_add(A, b[k]));
-    B = sat_add(B, b[k]);
-  }
-  const uint64_t h = halo_key >> 3;
-  const bool first = FORWARD ? seg == 0 : seg == 7;
-  if (first) A = min(A, sat_add(h, B));
-#pragma unroll
-  for (int off = 1; off < 8; off <<= 1) {
-    uint64_t Ap = FORWARD ? __shfl_up_sync(0xffffffffu, A, off, 8) : __shfl_down_sync(0xffffffffu, A, off, 8);
-    uint64_t Bp = FORWARD ? __shfl_up_sync(0xffffffffu, B, off, 8) : __shfl_down_sync(0xffffffffu, B, off, 8);
-    bool has = FORWARD ? seg >= off : seg + off < 8;
-    if (has) {
-      A = min(A, sat_add(Ap, B));
-      B = sat_add(Bp, B);
-    }
-  }
-  uint64_t cin = FORWARD ? __shfl_up_sync(0xffffffffu, A, 1, 8) : __shfl_down_sync(0xffffffffu, A, 1, 8);
-  if (first) cin = h;
-  unsigned changed = 0;
-  uint64_t prev = cin;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    uint64_t cand = sat_add(prev, b[k]);
-    uint64_t cur = K[k];
-    if (cand < KINF) {
-      if (cand >= KDIST_INF) {
-        *err |= kErrOverflow;
-      } else if (cand >= capK) {
-        // beyond this search's distance band: dropped, the tile is re-seeded
-        // if the band is widened
-        if (cand < cur) *capped = true;
-      } else {
-        uint64_t* c = cell(k);
-        uint64_t key = (cand << 3) | (uint64_t)dir;
-        if (key < *c) {
-          *c = key;
-          changed |= 1u << k;
-        }
-        cur = min(cur, cand);
-      }
-    }
-    prev = cur;
-  }
-  return changed;  // bit k: the lane's k-th cell (scan order) improved
-}
+  __device__ static __forceinline__ bool overflow(uint64_t cand) { return cand >= KDIST_INF; }
+};
+template <>
+struct Keys<uint32_t> {
+  static constexpr int kRounds = kRounds32;
+  __device__ static __forceinline__ uint32_t inf() { return KINF32; }
+  // the arc-weight planes hold weight32() values
+  __device__ static __forceinline__ uint32_t weight(uint32_t w) { return w; }
+  __device__ static __forceinline__ bool overflow(uint32_t) { return false; }
+};
 
 constexpr int LROW = TS + 3;  // padded row stride of the label tile (halo 1 each side + 1 pad)
 constexpr int RCOL = TS + 1;  // padded row stride of the arc-weight planes
+
+// One directional sweep of one line of the tile by one lane: the cells k in
+// sweep order with labels K_k and entering-arc weights b_k become
+//   c_k = min(K_k, c_{k-1} + b_k),  c_{-1} = the halo label,
+// a candidate keeping direction code dir, kept only below the cap.  The carried
+// value is min(K_k, c_{k-1} + b_k) whether or not it is kept: a value at or
+// beyond the cap only leads to more such values, none of which is written.
+// ROW: the line is row `line`, else column `line`; FORWARD: increasing index.
+// Cells are read a few at a time; the sweeps of the other directions run at the
+// same time, and a lower value one of them wrote may be overwritten (the
+// writer's line is then swept again).  Returns the mask of cells written (bit =
+// index along the line).
+template <class KT, bool ROW, bool FORWARD>
+__device__ __forceinline__ unsigned sweep_line(KT (*L)[LROW], const uint32_t (*W)[RCOL], int line, KT capK8, int dir,
+                                               int* err) {
+  using KK = Keys<KT>;
+  const int h = FORWARD ? 0 : TS + 1;
+  KT prev = (ROW ? L[line + 1][h] : L[h][line + 1]) >> 3;
+  unsigned ch = 0;
+  bool ov = false;
+  constexpr int CH = sizeof(KT) == 4 ? 8 : 4;  // cells read ahead (registers)
+  for (int c0 = 0; c0 < TS; c0 += CH) {
+    KT cell[CH];
+    uint32_t w[CH];
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int k = FORWARD ? c0 + s : TS - 1 - c0 - s;
+      cell[s] = ROW ? L[line + 1][k + 1] : L[k + 1][line + 1];
+      w[s] = ROW ? W[line][k] : W[k][line];
+    }
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int k = FORWARD ? c0 + s : TS - 1 - c0 - s;
+      // prev <= inf and weight <= inf: no wrap in either width
+      const KT cand = prev + KK::weight(w[s]);
+      prev = min(cell[s] >> 3, cand);
+      // key < capK << 3 exactly when cand < capK (the low three bits hold dir)
+      const KT key = (min(cand, KK::inf()) << 3) | (KT)dir;
+      bool imp = key < min(cell[s], capK8);
+      if (KK::overflow(cand) && imp) {
+        ov = true;  // only without a cap: a capped band keeps distances below 2^31
+        imp = false;
+      }
+      if (imp) {
+        (ROW ? L[line + 1][k + 1] : L[k + 1][line + 1]) = key;
+        ch |= 1u << k;
+      }
+    }
+  }
+  if (ov) *err |= kErrOverflow;
+  return ch;
+}
+
+// Local fixed point of one tile: warps 0..3 sweep rows left to right, rows
+// right to left, columns top to bottom and columns bottom to top at the same
+// time (lane = line).  Every value a sweep carries is a label it read plus arcs,
+// so any interleaving leaves valid labels, and a round in which no sweep writes
+// leaves the fixed point.  A line is swept again only if another sweep wrote one
+// of its cells.  L is the label tile with its halo, rc the four arc-weight
+// planes, s_mask two rounds of change masks.  Returns the rounds run; *guard is
+// set when the fixed point was not reached within Keys<KT>::kRounds rounds.
+template <class KT>
+__device__ __forceinline__ int relax_tile(KT (*L)[LROW], const uint32_t (*rc)[TS][RCOL], KT capK,
+                                          unsigned (*s_mask)[8], bool* guard, int* err) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const KT capK8 = capK << 3;  // capK < 2^61
+  unsigned mine = 0xFFFFFFFFu;  // lines this warp sweeps in the next round
+  int par = 0, round = 0;
+  for (;; ++round) {
+    if (round == Keys<KT>::kRounds) {
+      *guard = true;
+      break;
+    }
+    if (warp < 4) {
+      unsigned ch = 0;
+      if ((mine >> lane) & 1u) {
+        if (warp == 0) ch = sweep_line<KT, true, true>(L, rc[kDirLeft - 1], lane, capK8, kDirLeft, err);
+        else if (warp == 1) ch = sweep_line<KT, true, false>(L, rc[kDirRight - 1], lane, capK8, kDirRight, err);
+        else if (warp == 2) ch = sweep_line<KT, false, true>(L, rc[kDirUp - 1], lane, capK8, kDirUp, err);
+        else ch = sweep_line<KT, false, false>(L, rc[kDirDown - 1], lane, capK8, kDirDown, err);
+      }
+      // lines this warp wrote, and the lines of the other orientation it crossed
+      const unsigned lines = __ballot_sync(0xffffffffu, ch != 0);
+      const unsigned cross = __reduce_or_sync(0xffffffffu, ch);
+      if (lane == 0) {
+        s_mask[par][warp] = lines;
+        s_mask[par][4 + warp] = cross;
+      }
+    }
+    __syncthreads();
+    const unsigned* m = s_mask[par];
+    if ((m[0] | m[1] | m[2] | m[3]) == 0) break;
+    // rows: written by the other row sweep or crossed by a column sweep; columns alike
+    if (warp == 0) mine = m[1] | m[6] | m[7];
+    else if (warp == 1) mine = m[0] | m[6] | m[7];
+    else if (warp == 2) mine = m[3] | m[4] | m[5];
+    else if (warp == 3) mine = m[2] | m[4] | m[5];
+    par ^= 1;
+  }
+  return round + 1;
+}
+
+// After the fixed point: does an arc into one of this thread's cells (rows
+// warp + 8k, column lane) carry a finite candidate at or beyond the cap that
+// would improve the cell?  Then the band dropped it, and the tile is re-seeded
+// if the band is widened.
+template <class KT>
+__device__ __forceinline__ bool tile_capped(const KT (*L)[LROW], const uint32_t (*rc)[TS][RCOL], KT capK) {
+  using KK = Keys<KT>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool capped = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = warp + 8 * k, c = lane;
+    const KT cur = L[r + 1][c + 1] >> 3;
+    // the neighbour each arc-weight plane enters from
+    KT from[4];
+    from[kDirUp - 1] = L[r][c + 1];
+    from[kDirDown - 1] = L[r + 2][c + 1];
+    from[kDirLeft - 1] = L[r + 1][c];
+    from[kDirRight - 1] = L[r + 1][c + 2];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const KT cand = (from[d] >> 3) + KK::weight(rc[d][r][c]);
+      capped |= cand >= capK && cand < KK::inf() && cand < cur;
+    }
+  }
+  return capped;
+}
+
+// Reduced costs of the four arcs of every node of a tile, edge by edge: each
+// edge's flow and two costs are read once and give the arcs of both of its
+// nodes.  rc[dir-1][node] is the arc entering the node from dir (forward search)
+// or leaving it toward dir (reverse search); kNoArc where there is none.
+// NARROW: stored as weight32() values, else as reduced costs.
+template <bool FWD, bool NARROW>
+__device__ __forceinline__ void build_rc(const ProbDev& p, int64_t i0, int64_t j0, const int64_t (*spot)[TSH],
+                                         uint32_t (*rc)[TS][RCOL], int* err) {
+  const int tid = threadIdx.x;
+  const int64_t P = p.m * p.n;
+  auto put = [](uint32_t w) { return NARROW ? weight32(w) : w; };
+  // h edges h(i, j), i = i0 + er (er = 0..TS), j = j0 + lx: node A = (i-1, j) above, B = (i, j) below
+  for (int q = tid; q < (TS + 1) * TS; q += SEARCH_THREADS) {
+    const int er = q / TS, lx = q % TS;
+    const int64_t i = i0 + er, j = j0 + lx;
+    const bool a_in = i - 1 >= 0 && i - 1 < p.R && j < p.C;
+    const bool b_in = i < p.R && j < p.C;
+    uint32_t up_b = kNoArc, down_a = kNoArc;  // rc[Up][B], rc[Down][A]
+    if (a_in || b_in) {
+      const int64_t e = i * p.n + j;
+      const int dk = p.flows[e];
+      const int32_t cp = p.costs[e], cm = p.costs[P + e];
+      const int64_t pa = spot[er][lx + 1], pb = spot[er + 1][lx + 1];
+      // A->B raises dk (available unless dk = +1); B->A lowers it (unless dk = -1)
+      const bool ab_ok = dk <= 0, ba_ok = dk >= 0;
+      const int64_t ab = ab_ok ? (int64_t)(dk == 0 ? cp : -cm) - pa + pb : 0;
+      const int64_t ba = ba_ok ? (int64_t)(dk == 0 ? cm : -cp) - pb + pa : 0;
+      // forward: entering B from above = A->B, entering A from below = B->A; reverse: the opposite arcs
+      const bool ok_ub = FWD ? ab_ok : ba_ok, ok_da = FWD ? ba_ok : ab_ok;
+      const int64_t r_ub = FWD ? ab : ba, r_da = FWD ? ba : ab;
+      if (b_in && ok_ub) {
+        if (r_ub < 0) *err |= kErrInternal;
+        if (r_ub >= (int64_t)kNoArc) *err |= kErrOverflow;
+        else up_b = (uint32_t)max(r_ub, (int64_t)0);
+      }
+      if (a_in && ok_da) {
+        if (r_da < 0) *err |= kErrInternal;
+        if (r_da >= (int64_t)kNoArc) *err |= kErrOverflow;
+        else down_a = (uint32_t)max(r_da, (int64_t)0);
+      }
+    }
+    if (er < TS) rc[kDirUp - 1][er][lx] = put(up_b);
+    if (er > 0) rc[kDirDown - 1][er - 1][lx] = put(down_a);
+  }
+  // v edges v(i, j), i = i0 + ly, j = j0 + ec (ec = 0..TS): node L = (i, j-1) left, Rn = (i, j) right
+  for (int q = tid; q < TS * (TS + 1); q += SEARCH_THREADS) {
+    const int ly = q / (TS + 1), ec = q % (TS + 1);
+    const int64_t i = i0 + ly, j = j0 + ec;
+    const bool l_in = i < p.R && j - 1 >= 0 && j - 1 < p.C;
+    const bool r_in = i < p.R && j < p.C;
+    uint32_t left_r = kNoArc, right_l = kNoArc;  // rc[Left][Rn], rc[Right][L]
+    if (l_in || r_in) {
+      const int64_t e = i * p.n + j;
+      const int dk = p.flows[P + e];
+      const int32_t cp = p.costs[2 * P + e], cm = p.costs[3 * P + e];
+      const int64_t pl = spot[ly + 1][ec], pr = spot[ly + 1][ec + 1];
+      // Rn->L raises dk (available unless dk = +1); L->Rn lowers it (unless dk = -1)
+      const bool rl_ok = dk <= 0, lr_ok = dk >= 0;
+      const int64_t rl = rl_ok ? (int64_t)(dk == 0 ? cp : -cm) - pr + pl : 0;
+      const int64_t lr = lr_ok ? (int64_t)(dk == 0 ? cm : -cp) - pl + pr : 0;
+      // forward: entering Rn from the left = L->Rn, entering L from the right = Rn->L
+      const bool ok_lr = FWD ? lr_ok : rl_ok, ok_rl = FWD ? rl_ok : lr_ok;
+      const int64_t r_lr = FWD ? lr : rl, r_rl = FWD ? rl : lr;
+      if (r_in && ok_lr) {
+        if (r_lr < 0) *err |= kErrInternal;
+        if (r_lr >= (int64_t)kNoArc) *err |= kErrOverflow;
+        else left_r = (uint32_t)max(r_lr, (int64_t)0);
+      }
+      if (l_in && ok_rl) {
+        if (r_rl < 0) *err |= kErrInternal;
+        if (r_rl >= (int64_t)kNoArc) *err |= kErrOverflow;
+        else right_l = (uint32_t)max(r_rl, (int64_t)0);
+      }
+    }
+    if (ec < TS) rc[kDirLeft - 1][ly][ec] = put(left_r);
+    if (ec > 0) rc[kDirRight - 1][ly][ec - 1] = put(right_l);
+  }
+}
 
 template <bool FWD>
 __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int64_t* __restrict__ pot,
@@ -311,11 +494,14 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
                                                            int32_t* inq, McfCtr* ctr, int32_t* capped_flag,
                                                            int32_t* touched, int32_t* tlist) {
   __shared__ uint64_t lab[TSH][LROW];
+  __shared__ uint32_t lab32[TSH][LROW];  // the same labels as 32-bit cells (a 32-bit visit)
   __shared__ uint32_t rc[4][TS][RCOL];
   __shared__ int64_t spot[TSH][TSH];  // potentials with halo (the ground outside the grid)
   __shared__ int side[4];
   __shared__ int s_tile;
-  __shared__ unsigned rowdirty, coldirty, rowdirty_next, coldirty_next;
+  // smallest / largest distance and hop count of the finite labels of the tile and its halo
+  __shared__ uint32_t s_dmin, s_dmax, s_hmin, s_hmax;
+  __shared__ unsigned s_mask[2][8];  // change masks of the relaxation rounds
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;  // 8 warps
   const int ring = (int)b.t_total + (int)gridDim.x + 64;
@@ -327,10 +513,6 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
   const bool gsink = ctr->gsink != 0;
   const uint32_t wait_polls = ctr->wait_polls;
   int err = 0;
-  if (tid == 0) {
-    rowdirty_next = 0;
-    coldirty_next = 0;
-  }
   for (;;) {
     if (tid == 0) s_tile = q_pop(ring, q, slots, inq, wait_polls);
     __syncthreads();
@@ -346,6 +528,12 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
     uint64_t* plab = labels + p.node_off;
     const int64_t* ppot = pot + p.node_off;
     if (tid < 4) side[tid] = 0;
+    if (tid == 0) {
+      s_dmin = 0xFFFFFFFFu;
+      s_hmin = 0xFFFFFFFFu;
+      s_dmax = 0;
+      s_hmax = 0;
+    }
     // first visit of the tile in this pass: list it, so that its labels are
     // reset after the pass without a sweep over every node
     if (tid == 0 && atomicExch(&touched[tile], 1) == 0) {
@@ -354,6 +542,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       else err |= kErrInternal;
     }
     const long long t_start = clock64();
+    uint32_t dmin = 0xFFFFFFFFu, dmax = 0, hmin = 0xFFFFFFFFu, hmax = 0;
     // labels with halo; directly outside the grid stands G, a root (label 0)
     for (int qd = tid; qd < TSH * TSH; qd += SEARCH_THREADS) {
       int r = qd / TSH, c = qd % TSH;
@@ -370,164 +559,87 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       }
       lab[r][c] = v;
       spot[r][c] = pv;
-    }
-    __syncthreads();
-    // reduced costs of the four arcs of every node, edge by edge: each edge's flow
-    // and two costs are read once and give the arcs of both of its nodes.
-    // rc[dir-1][node] is the arc entering the node from dir (forward search) or
-    // leaving it toward dir (reverse search); kNoArc where there is none.
-    {
-      const int64_t P = p.m * p.n;
-      // h edges h(i, j), i = i0 + er (er = 0..TS), j = j0 + lx: node A = (i-1, j) above, B = (i, j) below
-      for (int q = tid; q < (TS + 1) * TS; q += SEARCH_THREADS) {
-        const int er = q / TS, lx = q % TS;
-        const int64_t i = i0 + er, j = j0 + lx;
-        const bool a_in = i - 1 >= 0 && i - 1 < p.R && j < p.C;
-        const bool b_in = i < p.R && j < p.C;
-        uint32_t up_b = kNoArc, down_a = kNoArc;  // rc[Up][B], rc[Down][A]
-        if (a_in || b_in) {
-          const int64_t e = i * p.n + j;
-          const int dk = p.flows[e];
-          const int32_t cp = p.costs[e], cm = p.costs[P + e];
-          const int64_t pa = spot[er][lx + 1], pb = spot[er + 1][lx + 1];
-          // A->B raises dk (available unless dk = +1); B->A lowers it (unless dk = -1)
-          const bool ab_ok = dk <= 0, ba_ok = dk >= 0;
-          const int64_t ab = ab_ok ? (int64_t)(dk == 0 ? cp : -cm) - pa + pb : 0;
-          const int64_t ba = ba_ok ? (int64_t)(dk == 0 ? cm : -cp) - pb + pa : 0;
-          // forward: entering B from above = A->B, entering A from below = B->A; reverse: the opposite arcs
-          const bool ok_ub = FWD ? ab_ok : ba_ok, ok_da = FWD ? ba_ok : ab_ok;
-          const int64_t r_ub = FWD ? ab : ba, r_da = FWD ? ba : ab;
-          if (b_in && ok_ub) {
-            if (r_ub < 0) err |= kErrInternal;
-            if (r_ub >= (int64_t)kNoArc) err |= kErrOverflow;
-            else up_b = (uint32_t)max(r_ub, (int64_t)0);
-          }
-          if (a_in && ok_da) {
-            if (r_da < 0) err |= kErrInternal;
-            if (r_da >= (int64_t)kNoArc) err |= kErrOverflow;
-            else down_a = (uint32_t)max(r_da, (int64_t)0);
-          }
-        }
-        if (er < TS) rc[kDirUp - 1][er][lx] = up_b;
-        if (er > 0) rc[kDirDown - 1][er - 1][lx] = down_a;
-      }
-      // v edges v(i, j), i = i0 + ly, j = j0 + ec (ec = 0..TS): node L = (i, j-1) left, Rn = (i, j) right
-      for (int q = tid; q < TS * (TS + 1); q += SEARCH_THREADS) {
-        const int ly = q / (TS + 1), ec = q % (TS + 1);
-        const int64_t i = i0 + ly, j = j0 + ec;
-        const bool l_in = i < p.R && j - 1 >= 0 && j - 1 < p.C;
-        const bool r_in = i < p.R && j < p.C;
-        uint32_t left_r = kNoArc, right_l = kNoArc;  // rc[Left][Rn], rc[Right][L]
-        if (l_in || r_in) {
-          const int64_t e = i * p.n + j;
-          const int dk = p.flows[P + e];
-          const int32_t cp = p.costs[2 * P + e], cm = p.costs[3 * P + e];
-          const int64_t pl = spot[ly + 1][ec], pr = spot[ly + 1][ec + 1];
-          // Rn->L raises dk (available unless dk = +1); L->Rn lowers it (unless dk = -1)
-          const bool rl_ok = dk <= 0, lr_ok = dk >= 0;
-          const int64_t rl = rl_ok ? (int64_t)(dk == 0 ? cp : -cm) - pr + pl : 0;
-          const int64_t lr = lr_ok ? (int64_t)(dk == 0 ? cm : -cp) - pl + pr : 0;
-          // forward: entering Rn from the left = L->Rn, entering L from the right = Rn->L
-          const bool ok_lr = FWD ? lr_ok : rl_ok, ok_rl = FWD ? rl_ok : lr_ok;
-          const int64_t r_lr = FWD ? lr : rl, r_rl = FWD ? rl : lr;
-          if (r_in && ok_lr) {
-            if (r_lr < 0) err |= kErrInternal;
-            if (r_lr >= (int64_t)kNoArc) err |= kErrOverflow;
-            else left_r = (uint32_t)max(r_lr, (int64_t)0);
-          }
-          if (l_in && ok_rl) {
-            if (r_rl < 0) err |= kErrInternal;
-            if (r_rl >= (int64_t)kNoArc) err |= kErrOverflow;
-            else right_l = (uint32_t)max(r_rl, (int64_t)0);
-          }
-        }
-        if (ec < TS) rc[kDirLeft - 1][ly][ec] = left_r;
-        if (ec > 0) rc[kDirRight - 1][ly][ec - 1] = right_l;
+      if (v != kInf) {
+        const uint32_t d = (uint32_t)(v >> 32), h = (uint32_t)(v >> 3) & 0x1FFFFFFFu;
+        dmin = min(dmin, d);
+        dmax = max(dmax, d);
+        hmin = min(hmin, h);
+        hmax = max(hmax, h);
       }
     }
     __syncthreads();
-    const long long t_loaded = clock64();
+    dmin = __reduce_min_sync(0xffffffffu, dmin);
+    dmax = __reduce_max_sync(0xffffffffu, dmax);
+    hmin = __reduce_min_sync(0xffffffffu, hmin);
+    hmax = __reduce_max_sync(0xffffffffu, hmax);
+    if (lane == 0) {
+      atomicMin(&s_dmin, dmin);
+      atomicMax(&s_dmax, dmax);
+      atomicMin(&s_hmin, hmin);
+      atomicMax(&s_hmax, hmax);
+    }
+    __syncthreads();
+    // key width of this visit (see Keys): 32 bits when the finite labels' spans
+    // fit, with the band's cap exact when it lies within the 32-bit range
+    const uint32_t d0 = s_dmin, h0 = s_hmin;
+    bool narrow = d0 != 0xFFFFFFFFu && s_dmax - d0 < kDistSpan32 && s_hmax - h0 <= kHopSpan32;
+    bool local = false;  // the 32-bit range, not the band, limits this visit
+    uint32_t capK32 = kLocalCap32;
+    if (narrow) {
+      if (ctr->zstop != 0 && cap == 1u) {
+        // zero band: keys (0, hops < radius); every kept label has distance 0
+        const uint32_t zh = ctr->zhop[ctr->zstage];
+        if (d0 != 0 || zh <= h0) narrow = false;
+        else if (zh - h0 <= 32767u) capK32 = zh - h0;
+        else capK32 = 32767u, local = true;
+      } else if (cap != 0xFFFFFFFFu && cap - d0 <= kDistSpan32) {
+        capK32 = (cap - d0) << 15;  // cap > d0: every kept label lies below the cap
+      } else {
+        // distances d0 + kDistSpan32 and beyond are left to a 64-bit visit
+        local = true;
+        if (d0 > 0xFFFFFFFEu - kDistSpan32) narrow = false;
+      }
+    }
     uint64_t orig[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) orig[k] = lab[warp + 8 * k + 1][lane + 1];
-    // local fixed point by directional scans: rows left->right and right->left,
-    // then columns top->bottom and bottom->top; a line is rescanned only if a
-    // scan in the other orientation changed one of its cells (all start dirty)
-    if (tid == 0) {
-      rowdirty = 0xFFFFFFFFu;
-      coldirty = 0xFFFFFFFFu;
+    if (narrow) {
+      build_rc<FWD, true>(p, i0, j0, spot, rc, &err);
+      for (int qd = tid; qd < TSH * TSH; qd += SEARCH_THREADS) {
+        const int r = qd / TSH, c = qd % TSH;
+        const uint64_t v = lab[r][c];
+        uint32_t x = 0xFFFFFFFFu;
+        if (v != kInf) {
+          const uint32_t d = (uint32_t)(v >> 32) - d0, h = ((uint32_t)(v >> 3) & 0x1FFFFFFFu) - h0;
+          x = (((d << 15) | h) << 3) | (uint32_t)(v & 7u);
+        }
+        lab32[r][c] = x;
+      }
+    } else {
+      build_rc<FWD, false>(p, i0, j0, spot, rc, &err);
     }
     __syncthreads();
-    const int grp = lane >> 3, seg = lane & 7;
-    bool capped = false;
-    int round = 0;
-    for (; round < kMaxLocalSweeps; ++round) {
-      // rows 4*warp + grp; this lane holds columns 4*seg..4*seg+3
-      const unsigned rd = rowdirty;
-      const int r = 4 * warp + grp;
-      unsigned chr = 0;
-      if ((rd >> (4 * warp)) & 0xFu) {
-        uint64_t* rowp = &lab[r + 1][0];
-        const uint32_t* wl = &rc[kDirLeft - 1][r][0];
-        const uint32_t* wr = &rc[kDirRight - 1][r][0];
-        unsigned f = scan_segments<true>([&](int k) { return rowp + 1 + 4 * seg + k; },
-                                         [&](int k) { return wl[4 * seg + k]; }, rowp[0], kDirLeft, seg, capK,
-                                         &capped, &err);
-        unsigned bk = scan_segments<false>([&](int k) { return rowp + 1 + 4 * seg + 3 - k; },
-                                           [&](int k) { return wr[4 * seg + 3 - k]; }, rowp[TS + 1], kDirRight, seg,
-                                           capK, &capped, &err);
-        // columns touched: bit k of f is column 4seg+k, bit k of bk is column 4seg+3-k
-        unsigned cols = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if ((f >> k) & 1u) cols |= 1u << (4 * seg + k);
-          if ((bk >> k) & 1u) cols |= 1u << (4 * seg + 3 - k);
-        }
-        chr = cols;
+    const long long t_loaded = clock64();
+    bool capped = false, guard = false;
+    int rounds = 0;
+    if (narrow) {
+      rounds = relax_tile<uint32_t>(lab32, rc, capK32, s_mask, &guard, &err);
+      capped = tile_capped<uint32_t>(lab32, rc, capK32);
+      if (__syncthreads_or((local && capped) || guard)) {
+        // a candidate left the 32-bit range: the 64-bit visit from the loaded labels
+        narrow = false;
+        guard = false;
+        if (tid == 0) atomicAdd(&ctr->redo64, 1ull);
+        build_rc<FWD, false>(p, i0, j0, spot, rc, &err);
+        __syncthreads();
       }
-      __syncthreads();
-      if (tid == 0) rowdirty = 0;
-      // reduce the changed-column masks of the block
-      unsigned cm = __reduce_or_sync(0xffffffffu, chr);
-      if (lane == 0 && cm) atomicOr(&coldirty_next, cm);
-      __syncthreads();
-      if (tid == 0) {
-        coldirty |= coldirty_next;
-        coldirty_next = 0;
-      }
-      __syncthreads();
-      const unsigned cd = coldirty;
-      const int c = 4 * warp + grp;
-      unsigned chc = 0;
-      if ((cd >> (4 * warp)) & 0xFu) {
-        const uint32_t* wu = &rc[kDirUp - 1][0][c];
-        const uint32_t* wd = &rc[kDirDown - 1][0][c];
-        unsigned f = scan_segments<true>([&](int k) { return &lab[4 * seg + k + 1][c + 1]; },
-                                         [&](int k) { return wu[(4 * seg + k) * RCOL]; }, lab[0][c + 1], kDirUp,
-                                         seg, capK, &capped, &err);
-        unsigned bk = scan_segments<false>([&](int k) { return &lab[4 * seg + 3 - k + 1][c + 1]; },
-                                           [&](int k) { return wd[(4 * seg + 3 - k) * RCOL]; }, lab[TS + 1][c + 1],
-                                           kDirDown, seg, capK, &capped, &err);
-        unsigned rows = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if ((f >> k) & 1u) rows |= 1u << (4 * seg + k);
-          if ((bk >> k) & 1u) rows |= 1u << (4 * seg + 3 - k);
-        }
-        chc = rows;
-      }
-      __syncthreads();
-      if (tid == 0) coldirty = 0;
-      unsigned rm = __reduce_or_sync(0xffffffffu, chc);
-      if (lane == 0 && rm) atomicOr(&rowdirty_next, rm);
-      __syncthreads();
-      if (tid == 0) {
-        rowdirty = rowdirty_next;
-        rowdirty_next = 0;
-      }
-      __syncthreads();
-      if (rowdirty == 0) break;
     }
+    if (!narrow) {
+      rounds += relax_tile<uint64_t>(lab, rc, capK, s_mask, &guard, &err);
+      capped = tile_capped<uint64_t>(lab, rc, capK);
+      if (guard) err |= kErrInternal;  // no fixed point within the round limit
+    }
+    __syncthreads();
     const long long t_relaxed = clock64();
     // write back and note which tile sides changed; count the reached nodes
     unsigned reached = 0;
@@ -536,6 +648,12 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       int ly = warp + 8 * k;
       int64_t i = i0 + ly, j = j0 + lane;
       uint64_t v = lab[ly + 1][lane + 1];
+      if (narrow) {
+        const uint32_t x = lab32[ly + 1][lane + 1];
+        v = x == 0xFFFFFFFFu ? kInf
+                             : (((uint64_t)((x >> 18) + d0) << 32) | ((uint64_t)(((x >> 3) & 0x7FFFu) + h0) << 3) |
+                                (uint64_t)(x & 7u));
+      }
       reached += __popc(__ballot_sync(0xffffffffu, i < p.R && j < p.C && v != kInf));
       if (i < p.R && j < p.C && v != orig[k]) {
         // the same tile may be in process in two CTAs (it can be re-queued
@@ -547,6 +665,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
         if (lane == TS - 1) side[3] = 1;
       }
     }
+    if (narrow && tid == 0) atomicAdd(&ctr->visits32, 1ull);
     if (lane == 0 && reached) atomicAdd(&ctr->settled_visits, (unsigned long long)reached);
     if (__syncthreads_or(capped) && tid == 0) {
       capped_flag[tile] = 1;
@@ -562,7 +681,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       if (side[3] && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq, wait_polls);
       if (!ok) err |= kErrSpin;
       atomicAdd(&ctr->tile_visits, 1ull);
-      atomicAdd(&ctr->local_rounds, (unsigned long long)(round + 1));
+      atomicAdd(&ctr->local_rounds, (unsigned long long)rounds);
       atomicAdd(&ctr->visit_cycles, (unsigned long long)(clock64() - t_start));
       atomicAdd(&ctr->load_cycles, (unsigned long long)(t_loaded - t_start));
       atomicAdd(&ctr->relax_cycles, (unsigned long long)(t_relaxed - t_loaded));
@@ -1255,6 +1374,11 @@ int search_grid_size(int sm_count, int want_per_sm) {
   static int per_sm = 0;
   if (per_sm == 0) {
     int a = 1, b = 1;
+    // five tiles per SM: ask for the largest shared-memory share of the unified L1
+    cudaFuncSetAttribute(k_search<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_search<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_search<true>, SEARCH_THREADS, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<false>, SEARCH_THREADS, 0);
     per_sm = std::max(1, std::min(a, b));
@@ -1542,10 +1666,11 @@ ww_status Session::pass(ww_solve_stats* st) {
   fill_stats(st);
   if (trace_enabled()) {
     std::fprintf(stderr,
-                 "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu, status %d, go_on %d, "
-                 "ground sink %d (dG %u)\n",
-                 hc->passes, hc->cap, ms, hc->naug, hc->D, hc->ncand, (unsigned long long)hc->tile_visits, hc->status,
-                 hc->go_on, hc->gsink, hc->dG);
+                 "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu (32-bit %llu, redone "
+                 "%llu), status %d, go_on %d, ground sink %d (dG %u)\n",
+                 hc->passes, hc->cap, ms, hc->naug, hc->D, hc->ncand, (unsigned long long)hc->tile_visits,
+                 (unsigned long long)hc->visits32, (unsigned long long)hc->redo64, hc->status, hc->go_on, hc->gsink,
+                 hc->dG);
     if (hc->err)
       std::fprintf(stderr, "[ww]   error flags %d; first negative reduced cost: node %lld dir %d value %lld (pass %d)\n",
                    hc->err, hc->dbg_node, hc->dbg_dir, hc->dbg_red, hc->dbg_pass);
@@ -1635,6 +1760,8 @@ void Session::fill_stats(ww_solve_stats* st) const {
   st->load_cycles = (int64_t)hc->load_cycles;
   st->relax_cycles = (int64_t)hc->relax_cycles;
   st->settled_visits = (int64_t)hc->settled_visits;
+  st->narrow_visits = (int64_t)hc->visits32;
+  st->narrow_redone = (int64_t)hc->redo64;
 }
 
 int64_t Session::ctr_bytes() const { return (int64_t)sizeof(McfCtr); }
