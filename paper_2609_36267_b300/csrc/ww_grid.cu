@@ -655,6 +655,70 @@ __global__ void k_integrate_col0(const void* ifg, int is_complex, const float* c
 // phi = (float)((double)psi + (double)K * 2pi), NaN where invalid.
 constexpr int kRowThreads = 256, kRowItems = 8;
 
+// The output phi = fp32(fp64(psi) + fp64(K) * 2pi_fp64) with its three
+// roundings (product, sum, narrowing) reproduced exactly, with one fp64
+// addition per pixel: the product and both conversions are integer steps (the
+// fp64 pipe of this GPU runs at a small fraction of the integer rate).
+
+// 2pi as an fp64 number: kTwoPiSig * 2^-50 with a 53-bit significand
+constexpr uint64_t kTwoPiSig = 0x1921FB54442D18ull;
+
+// Bits of the fp64 product K * 2pi (K != 0), rounded to nearest, ties to even:
+// the exact product of |K| < 2^31 and the significand has 53..84 bits and is
+// rounded to its top 53.
+__device__ __forceinline__ uint64_t k_two_pi_bits(int32_t K) {
+  const uint32_t a = K < 0 ? 0u - (uint32_t)K : (uint32_t)K;
+  const unsigned __int128 p = (unsigned __int128)a * kTwoPiSig;
+  const uint64_t ph = (uint64_t)(p >> 64), pl = (uint64_t)p;
+  const int len = ph ? 128 - __clzll((long long)ph) : 64 - __clzll((long long)pl);  // 53..84
+  const int sh = len - 53;                                                          // 0..31
+  uint64_t sig = (uint64_t)(p >> sh);
+  if (sh > 0) {
+    const uint64_t rem = pl & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (sig & 1))) ++sig;
+  }
+  int e = sh;
+  if (sig >> 53) {  // rounded up to 2^53
+    sig >>= 1;
+    ++e;
+  }
+  // sig 2^(e - 50) with sig in [2^52, 2^53): biased exponent e - 50 + 52 + 1023
+  return ((uint64_t)(K < 0) << 63) | ((uint64_t)(e + 1025) << 52) | (sig & ((1ull << 52) - 1));
+}
+
+// Bits of the fp64 number equal to a finite fp32 value (subnormals normalised).
+__device__ __forceinline__ uint64_t f32_to_f64_bits(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  if (e != 0) return sign | ((uint64_t)(e + 896) << 52) | ((uint64_t)m << 29);
+  if (m == 0) return sign;
+  const int top = 31 - __clz((int)m);  // m 2^-149 = 1.f 2^(top - 149)
+  return sign | ((uint64_t)(top + 874) << 52) | ((uint64_t)((m << (23 - top)) & 0x7FFFFFu) << 29);
+}
+
+// The fp32 number nearest (ties to even) an fp64 value that is zero or whose
+// fp32 rounding is a normal number (every sum psi + K 2pi with K != 0: it is 0,
+// at least 2^-50 in magnitude, or within half an fp32 ulp of a finite psi).
+__device__ __forceinline__ float f64_bits_to_f32(uint64_t d) {
+  const uint32_t sign = (uint32_t)(d >> 63) << 31;
+  const uint32_t e = (uint32_t)(d >> 52) & 0x7FFu;
+  if (e == 0) return __uint_as_float(sign);
+  const uint64_t m = d & ((1ull << 52) - 1);
+  uint32_t r = ((e - 896u) << 23) | (uint32_t)(m >> 29);
+  const uint32_t rem = (uint32_t)m & 0x1FFFFFFFu;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ++r;  // a carry moves into the exponent
+  return __uint_as_float(sign | r);
+}
+
+// fp32(fp64(psi) + fp64(K) * 2pi) for a finite psi.
+__device__ __forceinline__ float unwrap_value(float psi, int32_t K) {
+  if (K == 0) return psi == 0.0f ? 0.0f : psi;  // psi + (+0): -0 becomes +0, the rest is exact
+  const double s = __dadd_rn(__longlong_as_double((long long)f32_to_f64_bits(psi)),
+                             __longlong_as_double((long long)k_two_pi_bits(K)));
+  return f64_bits_to_f32((uint64_t)__double_as_longlong(s));
+}
+
 __device__ __forceinline__ void integrate_row(const void* ifg, int is_complex, const float* coh,
                                               const uint8_t* mask, const int8_t* flows, int64_t m, int64_t n,
                                               float* unw, int32_t* cycles, int64_t i) {
@@ -741,8 +805,7 @@ __device__ __forceinline__ void integrate_row(const void* ifg, int is_complex, c
       const int32_t K = base + local[t];
       Ks[t] = K;
       if (val[t]) {
-        double tt = __dmul_rn((double)K, kTwoPiD);
-        outs[t] = __double2float_rn(__dadd_rn((double)psi[t], tt));
+        outs[t] = unwrap_value(psi[t], K);
       } else {
         outs[t] = __int_as_float(0x7fc00000);
       }

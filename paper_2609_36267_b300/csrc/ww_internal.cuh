@@ -39,6 +39,13 @@ static __constant__ int32_t kAtanQ[30] = {
     32,        16,        8,         4,        2,        1};
 constexpr int64_t kHalfPiQ = 843314857;  // round(pi/2 * 2^29)
 
+// a b + c mod 2^32 (an integer multiply-add; no overflow rules of C++ apply).
+__device__ __forceinline__ int32_t mad32(int32_t a, int32_t b, int32_t c) {
+  int32_t d;
+  asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
 // |v| = M 2^E for a finite fp32 value (M < 2^24), with its sign bit.
 __device__ __forceinline__ void f32_split(float v, int32_t* M, int* E, int* neg) {
   uint32_t b = __float_as_uint(v);
@@ -85,18 +92,21 @@ __device__ __forceinline__ float cordic_phase(float re, float im) {
   // Vectoring iterations in 32-bit registers.  With |X|, |Y| < 2^30 and X >= 0
   // here, X only grows, to at most the CORDIC gain (1.647) times |(X, Y)| <
   // 2^32 (unsigned); |Y| stays below max(|Y|, X >> i) < 2^31; |Z| <= pi 2^29.
-  // s is -1 when Y < 0 and 0 otherwise, and (v ^ s) - s is v negated when
-  // Y < 0, so each step is one branch-free sequence: X += |Y >> i| rounded
-  // as the arithmetic shift does, Y -= sign(Y) (X >> i), Z += sign(Y) atan(2^-i).
+  // Each step, branch-free with g = sign(Y) as +-1 (Y = 0 counts as +):
+  // X += g (Y >> i) (= |Y >> i| as the arithmetic shift rounds), Y -= g (X >> i),
+  // Z += g atan(2^-i).  The products by g are integer multiply-adds (wrapping
+  // mod 2^32, the same bits as negating) and X >> i a multiply-high by
+  // 2^(32-i), which keeps half of each step off the integer ALU.
   uint32_t x = (uint32_t)X;
   int32_t y = Y, z = Z;
 #pragma unroll
   for (int i = 0; i < 30; ++i) {
     const int32_t s = y >> 31;
-    const int32_t xs = (int32_t)(x >> i);
-    x += (uint32_t)(((y >> i) ^ s) - s);
-    y -= (xs ^ s) - s;
-    z += (kAtanQ[i] ^ s) - s;
+    const int32_t g = s | 1, ng = ~s | 1;
+    const uint32_t xs = i == 0 ? x : __umulhi(x, 1u << (32 - i));
+    x = (uint32_t)mad32(y >> i, g, (int32_t)x);
+    y = mad32((int32_t)xs, ng, y);
+    z = mad32(kAtanQ[i], g, z);
   }
   float psi = __fmul_rn(__int2float_rn(z), 1.0f / 536870912.0f);
   return fminf(fmaxf(psi, -kPiF), kPiF);
@@ -121,18 +131,16 @@ __device__ __forceinline__ void cordic_cos_sin(int32_t z, int32_t* c, int32_t* s
     y = -kInvGainQ30;
     z += (int32_t)kHalfPiQ;
   }
+  // each step with h = +1 for Z >= 0, -1 otherwise: X -= h (Y >> i),
+  // Y += h (X >> i), Z -= h atan(2^-i), the products as multiply-adds
 #pragma unroll
   for (int i = 0; i < 30; ++i) {
     const int32_t xs = x >> i, ys = y >> i;
-    if (z >= 0) {
-      x -= ys;
-      y += xs;
-      z -= kAtanQ[i];
-    } else {
-      x += ys;
-      y -= xs;
-      z += kAtanQ[i];
-    }
+    const int32_t s = z >> 31;
+    const int32_t h = s | 1, nh = ~s | 1;
+    x = mad32(ys, nh, x);
+    y = mad32(xs, h, y);
+    z = mad32(kAtanQ[i], nh, z);
   }
   *c = x;
   *s = y;
