@@ -84,8 +84,6 @@ __global__ void __launch_bounds__(RTX* RTT) k_residues(const void* __restrict__ 
 
 // ---------------- costs ----------------
 constexpr int CTX = 32, CTY = 16, CW = 3;  // tile, max box half-width
-constexpr int CPX = CTX + 2 * CW + 1, CPY = CTY + 2 * CW + 1;  // pixel tile
-constexpr int CEX = CTX + 2 * CW, CEY = CTY + 2 * CW;          // edge tile
 
 struct SteepCtr {
   unsigned long long valid_edges;   // [0]
@@ -105,12 +103,21 @@ __device__ __forceinline__ float edge_d(float a, float b) {
 
 // Slope estimate from the row partial sums of the fixed-point gradients: the
 // vertical sum over the window's rows, then S / (cnt 2^22) rounded once.
+template <int W>
 __device__ __forceinline__ float window_mean(const int32_t (*rs)[CTX], const uint8_t (*ns)[CTX], int R, int c, int w) {
   int32_t S = 0;
   int cnt = 0;
-  for (int d = -w; d <= w; ++d) {
-    S += rs[R + d][c];
-    cnt += ns[R + d][c];
+  if constexpr (W >= 0) {
+#pragma unroll
+    for (int d = -W; d <= W; ++d) {
+      S += rs[R + d][c];
+      cnt += ns[R + d][c];
+    }
+  } else {
+    for (int d = -w; d <= w; ++d) {
+      S += rs[R + d][c];
+      cnt += ns[R + d][c];
+    }
   }
   return __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
 }
@@ -118,8 +125,9 @@ __device__ __forceinline__ float window_mean(const int32_t (*rs)[CTX], const uin
 // Phasor slope estimate: integer sums of the window's edge phasors (length 2^30
 // each, at most 49 of them: below 2^36), each sum rounded once to fp32, then the
 // CORDIC atan2; 0 for an empty window.
-__device__ __forceinline__ float window_phasor(const int32_t (*xs)[CEX + 1], const int32_t (*ys)[CEX + 1],
-                                               const uint8_t (*es)[CEX + 1], int R, int C, int w) {
+template <int EXP>
+__device__ __forceinline__ float window_phasor(const int32_t (*xs)[EXP], const int32_t (*ys)[EXP],
+                                               const uint8_t (*es)[EXP], int R, int C, int w) {
   long long SX = 0, SY = 0;
   for (int d = -w; d <= w; ++d)
     for (int e = -w; e <= w; ++e)
@@ -137,7 +145,7 @@ __device__ __forceinline__ float window_phasor(const int32_t (*xs)[CEX + 1], con
 // (separable sums); SLOPE 1: argument of the sum of their unit phasors (CORDIC
 // rotation per edge, integer window sums, CORDIC atan2).  LOOKUP 0: nearest bin
 // of the int16 table; LOOKUP 1: bilinear interpolation of `ratio`.
-template <int SLOPE, int LOOKUP>
+template <int SLOPE, int LOOKUP, int W>
 __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_complex,
                                            const float* __restrict__ coh, const uint8_t* __restrict__ mask,
                                            int64_t m, int64_t n, const int16_t* __restrict__ table,
@@ -145,34 +153,40 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
                                            int16_t* __restrict__ costs, SteepCtr* ctr, uint32_t* __restrict__ list,
                                            unsigned long long list_cap, int64_t bx, int64_t by,
                                            int8_t* __restrict__ res = nullptr, int32_t* __restrict__ ground = nullptr) {
-  __shared__ float sp[CPY][CPX];
-  __shared__ float sc[CPY][CPX];
-  __shared__ uint8_t sv[CPY][CPX];
+  // W >= 0: the window half width w is the compile-time W and the tile's halo
+  // is W wide; W < 0: any w up to CW at run time, halo CW
+  constexpr int HW = W < 0 ? CW : W;
+  constexpr int PX = CTX + 2 * HW + 1, PY = CTY + 2 * HW + 1;  // pixel tile
+  constexpr int EX = CTX + 2 * HW, EY = CTY + 2 * HW;          // edge tile
+  if constexpr (W >= 0) w = W;
+  __shared__ float sp[PY][PX];
+  __shared__ float sc[PY][PX];
+  __shared__ uint8_t sv[PY][PX];
   // SLOPE 0: fixed-point gradients; SLOPE 1: cos part of the edge phasors
-  __shared__ int32_t qh[CEY][CEX + 1], qv[CEY][CEX + 1];
-  __shared__ int32_t yh[SLOPE ? CEY : 1][CEX + 1], yv[SLOPE ? CEY : 1][CEX + 1];  // sin part (SLOPE 1)
-  __shared__ uint8_t eh[CEY][CEX + 1], ev[CEY][CEX + 1];
-  __shared__ int32_t rh[SLOPE ? 1 : CEY][CTX], rv[SLOPE ? 1 : CEY][CTX];  // row (horizontal) partial sums
-  __shared__ uint8_t nh[SLOPE ? 1 : CEY][CTX], nv[SLOPE ? 1 : CEY][CTX];  // row partial counts
+  __shared__ int32_t qh[EY][EX + 1], qv[EY][EX + 1];
+  __shared__ int32_t yh[SLOPE ? EY : 1][EX + 1], yv[SLOPE ? EY : 1][EX + 1];  // sin part (SLOPE 1)
+  __shared__ uint8_t eh[EY][EX + 1], ev[EY][EX + 1];
+  __shared__ int32_t rh[SLOPE ? 1 : EY][CTX], rv[SLOPE ? 1 : EY][CTX];  // row (horizontal) partial sums
+  __shared__ uint8_t nh[SLOPE ? 1 : EY][CTX], nv[SLOPE ? 1 : EY][CTX];  // row partial counts
   const int64_t i0 = by * CTY, j0 = bx * CTX;
   const int tid = threadIdx.x;
-  // 1. prepared pixels, tile origin (i0 - CW, j0 - CW); every load of a thread
+  // 1. prepared pixels, tile origin (i0 - HW, j0 - HW); every load of a thread
   // is issued before its first store
   {
-    constexpr int kU = (CPY * CPX + 255) / 256;
+    constexpr int kU = (PY * PX + 255) / 256;
     Pix px[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int q = tid + 256 * u;
-      const int64_t i = i0 - CW + q / CPX, j = j0 - CW + q % CPX;
+      const int64_t i = i0 - HW + q / PX, j = j0 - HW + q % PX;
       px[u] = Pix{0.0f, 0.0f, false};
-      if (q < CPY * CPX && i >= 0 && i < m && j >= 0 && j < n) px[u] = load_pixel(ifg, is_complex, coh, mask, i * n + j);
+      if (q < PY * PX && i >= 0 && i < m && j >= 0 && j < n) px[u] = load_pixel(ifg, is_complex, coh, mask, i * n + j);
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int q = tid + 256 * u;
-      if (q >= CPY * CPX) continue;
-      const int r = q / CPX, c = q % CPX;
+      if (q >= PY * PX) continue;
+      const int r = q / PX, c = q % PX;
       sp[r][c] = px[u].psi;
       sc[r][c] = px[u].coh;
       sv[r][c] = px[u].valid ? 1 : 0;
@@ -180,9 +194,9 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   }
   __syncthreads();
   // 2. fixed-point wrapped gradients of every edge in the extended tile
-  for (int q = tid; q < CEY * CEX; q += 256) {
-    int r = q / CEX, c = q % CEX;
-    int64_t i = i0 - CW + r, j = j0 - CW + c;
+  for (int q = tid; q < EY * EX; q += 256) {
+    int r = q / EX, c = q % EX;
+    int64_t i = i0 - HW + r, j = j0 - HW + c;
     int32_t a = 0, b = 0, ya = 0, yb = 0;
     uint8_t ea = 0, eb = 0;
     if (i >= 0 && i < m && j >= 0) {
@@ -214,16 +228,27 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   }
   __syncthreads();
   // 3. horizontal window sums for the output columns, every extended row
-  for (int q = tid; q < (SLOPE ? 0 : CEY * CTX); q += 256) {
+  for (int q = tid; q < (SLOPE ? 0 : EY * CTX); q += 256) {
     int r = q / CTX, c = q % CTX;
     int32_t sa = 0, sb = 0;
     int ca = 0, cb = 0;
-    for (int d = -w; d <= w; ++d) {
-      int cc = c + CW + d;
-      sa += qh[r][cc];
-      ca += eh[r][cc];
-      sb += qv[r][cc];
-      cb += ev[r][cc];
+    if constexpr (W >= 0) {
+#pragma unroll
+      for (int d = -W; d <= W; ++d) {
+        const int cc = c + HW + d;
+        sa += qh[r][cc];
+        ca += eh[r][cc];
+        sb += qv[r][cc];
+        cb += ev[r][cc];
+      }
+    } else {
+      for (int d = -w; d <= w; ++d) {
+        const int cc = c + HW + d;
+        sa += qh[r][cc];
+        ca += eh[r][cc];
+        sb += qv[r][cc];
+        cb += ev[r][cc];
+      }
     }
     rh[r][c] = sa;
     nh[r][c] = (uint8_t)ca;
@@ -246,7 +271,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     int64_t i = i0 + r, j = j0 + c;
     bool hcand = false, vcand = false;
     const bool inside = i < m && j < n;
-    int R = r + CW, C = c + CW;
+    int R = r + HW, C = c + HW;
     int64_t k = i * n + j;
     if (inside) {
     // h edge (i,j)
@@ -254,7 +279,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     if (eh[R][C]) {
       float ah;
       if constexpr (SLOPE == 0)
-        ah = window_mean(rh, nh, R, c, w);
+        ah = window_mean<W>(rh, nh, R, c, w);
       else
         ah = window_phasor(qh, yh, eh, R, C, w);
       const float ge = fminf(sc[R][C], sc[R][C + 1]);
@@ -275,7 +300,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     if (ev[R][C]) {
       float av;
       if constexpr (SLOPE == 0)
-        av = window_mean(rv, nv, R, c, w);
+        av = window_mean<W>(rv, nv, R, c, w);
       else
         av = window_phasor(qv, yv, ev, R, C, w);
       const float ge = fminf(sc[R][C], sc[R + 1][C]);
@@ -349,7 +374,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   }
 }
 
-template <int SLOPE, int LOOKUP>
+template <int SLOPE, int LOOKUP, int W>
 __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int is_complex,
                                                const float* __restrict__ coh,
                                                const uint8_t* __restrict__ mask, int64_t m, int64_t n,
@@ -359,17 +384,22 @@ __global__ void __launch_bounds__(256) k_costs(const void* __restrict__ ifg, int
                                                int32_t* ground) {
   // one-dimensional grid of tiles (gridDim.y would cap the rows at 65535 tiles)
   const int64_t gx = (n + CTX - 1) / CTX, b = blockIdx.x;
-  costs_tile<SLOPE, LOOKUP>(ifg, is_complex, coh, mask, m, n, table, ratio, w, steep_rad, costs, ctr, list, list_cap,
-                            b % gx, b / gx, res, ground);
+  costs_tile<SLOPE, LOOKUP, W>(ifg, is_complex, coh, mask, m, n, table, ratio, w, steep_rad, costs, ctr, list, list_cap,
+                               b % gx, b / gx, res, ground);
 }
 
 // the k_costs variant for a parameter set
 using CostsKernel = void (*)(const void*, int, const float*, const uint8_t*, int64_t, int64_t, const int16_t*,
                              const float*, int, float, int16_t*, SteepCtr*, uint32_t*, unsigned long long, int8_t*,
                              int32_t*);
+// (the default 5 x 5 window has its own instances)
 CostsKernel costs_kernel(const ww_params* p) {
-  if (p->slope_estimator == 0) return p->cost_lookup == 0 ? k_costs<0, 0> : k_costs<0, 1>;
-  return p->cost_lookup == 0 ? k_costs<1, 0> : k_costs<1, 1>;
+  if (p->box_half_width == 2) {
+    if (p->slope_estimator == 0) return p->cost_lookup == 0 ? k_costs<0, 0, 2> : k_costs<0, 1, 2>;
+    return p->cost_lookup == 0 ? k_costs<1, 0, 2> : k_costs<1, 1, 2>;
+  }
+  if (p->slope_estimator == 0) return p->cost_lookup == 0 ? k_costs<0, 0, -1> : k_costs<0, 1, -1>;
+  return p->cost_lookup == 0 ? k_costs<1, 0, -1> : k_costs<1, 1, -1>;
 }
 
 // number of k_costs tiles (one block each) of an m x n image
@@ -887,7 +917,7 @@ __global__ void __launch_bounds__(256) k_costs_b(const GridItem* __restrict__ it
   const GridItem& it = items[item_of_block<kBlkCost>(items, count, b)];
   const int64_t local = b - it.blk[kBlkCost];
   const int64_t gx = (it.n + CTX - 1) / CTX;
-  costs_tile<SLOPE, LOOKUP>(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, it.table, it.ratio, w, steep_rad,
+  costs_tile<SLOPE, LOOKUP, -1>(it.ifg, it.is_complex, it.coh, it.mask, it.m, it.n, it.table, it.ratio, w, steep_rad,
              it.costs,
              reinterpret_cast<SteepCtr*>(it.steep), it.cand_list, (unsigned long long)it.cand_cap, local % gx,
              local / gx);
@@ -1445,7 +1475,7 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   WW_CUDA_TRY(cudaMemcpyAsync(dtable, src ? src : lut_host_table(lut), kNoAllocTableBytes, cudaMemcpyHostToDevice, s));
   WW_CUDA_TRY(cudaMemsetAsync(hist, 0, 65536 * sizeof(uint32_t), s));
   WW_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SteepCtr), s));
-  k_costs<0, 0><<<cost_tiles(m, n), 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, nullptr, p->box_half_width,
+  costs_kernel(p)<<<cost_tiles(m, n), 256, 0, s>>>(ifg, c, coh, mask, m, n, dtable, nullptr, p->box_half_width,
                                                  p->steep_rad, costs, ctr, nullptr, 0ull, nullptr, nullptr);
   k_steep_plan<<<1, 1, 0, s>>>(ctr, p->steep_cap_ppm);
   const int hist_blocks = 148 * 8;
