@@ -122,6 +122,8 @@ struct McfCtr {
   uint32_t wait_polls; // polls of a worklist wait before it gives up (WW_ERR_TIMEOUT)
   unsigned long long visits32;  // tile visits relaxed in 32-bit keys
   unsigned long long redo64;    // of which redone in 64-bit keys (a candidate left the 32-bit range)
+  unsigned long long pop_cycles;  // SM cycles spent taking tiles from the worklist (waits included)
+  unsigned long long touched_total;  // distinct tiles visited, summed over passes
 };
 
 // Problems live in slots (stable ids); `order` lists the active slots sorted by
@@ -409,6 +411,53 @@ __device__ __forceinline__ bool tile_capped(const KT (*L)[LROW], const uint32_t 
   return capped;
 }
 
+// Per-pass cache of a tile's arc costs (potentials, flows and costs are fixed
+// while a pass searches, and a tile is visited several times per pass): 4 planes
+// of 32 x 32 reduced costs, stamped with the pass that wrote them.
+constexpr int64_t kRcTileBytes = 4 * TS * TS * 4;
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// smem arc-cost planes <-> the tile's cache entry, 16 bytes per access (L2 only:
+// other CTAs write entries during the launch)
+__device__ __forceinline__ void rc_from_cache(const uint32_t* __restrict__ src, uint32_t (*rc)[TS][RCOL]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int q = threadIdx.x + SEARCH_THREADS * u;  // 16-byte chunk: plane, row, 4 columns
+    const int d = q >> 8, r = (q >> 3) & 31, c = (q & 7) * 4;
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(src) + q);
+    rc[d][r][c] = v.x;
+    rc[d][r][c + 1] = v.y;
+    rc[d][r][c + 2] = v.z;
+    rc[d][r][c + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void rc_to_cache(const uint32_t (*rc)[TS][RCOL], uint32_t* __restrict__ dst) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int q = threadIdx.x + SEARCH_THREADS * u;
+    const int d = q >> 8, r = (q >> 3) & 31, c = (q & 7) * 4;
+    __stcg(reinterpret_cast<uint4*>(dst) + q, make_uint4(rc[d][r][c], rc[d][r][c + 1], rc[d][r][c + 2], rc[d][r][c + 3]));
+  }
+}
+// the planes as weight32() values (this thread's chunks, as above)
+__device__ __forceinline__ void rc_narrow(uint32_t (*rc)[TS][RCOL]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int q = threadIdx.x + SEARCH_THREADS * u;
+    const int d = q >> 8, r = (q >> 3) & 31, c = (q & 7) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rc[d][r][c + k] = weight32(rc[d][r][c + k]);
+  }
+}
+
 // Reduced costs of the four arcs of every node of a tile, edge by edge: each
 // edge's flow and two costs are read once and give the arcs of both of its
 // nodes.  rc[dir-1][node] is the arc entering the node from dir (forward search)
@@ -492,13 +541,14 @@ template <bool FWD>
 __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int64_t* __restrict__ pot,
                                                            uint64_t* labels, SearchQ* q, int32_t* slots,
                                                            int32_t* inq, McfCtr* ctr, int32_t* capped_flag,
-                                                           int32_t* touched, int32_t* tlist) {
+                                                           int32_t* touched, int32_t* tlist, uint32_t* rc_cache,
+                                                           int32_t* rc_pass) {
   __shared__ uint64_t lab[TSH][LROW];
   __shared__ uint32_t lab32[TSH][LROW];  // the same labels as 32-bit cells (a 32-bit visit)
   __shared__ uint32_t rc[4][TS][RCOL];
   __shared__ int64_t spot[TSH][TSH];  // potentials with halo (the ground outside the grid)
   __shared__ int side[4];
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_hit;
   // smallest / largest distance and hop count of the finite labels of the tile and its halo
   __shared__ uint32_t s_dmin, s_dmax, s_hmin, s_hmax;
   __shared__ unsigned s_mask[2][8];  // change masks of the relaxation rounds
@@ -512,9 +562,18 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
                         : (cap == 0xFFFFFFFFu ? KINF : ((uint64_t)cap << 29));
   const bool gsink = ctr->gsink != 0;
   const uint32_t wait_polls = ctr->wait_polls;
+  const int stamp = ctr->passes + 1;  // this pass in the arc-cost cache
   int err = 0;
   for (;;) {
-    if (tid == 0) s_tile = q_pop(ring, q, slots, inq, wait_polls);
+    if (tid == 0) {
+      const long long t_pop = clock64();
+      const int t = q_pop(ring, q, slots, inq, wait_polls);
+      s_tile = t;
+      // a cache entry of this pass holds every arc cost of the tile (acquire:
+      // the entry's stores are seen before its stamp)
+      s_hit = t >= 0 && ld_acquire(&rc_pass[t]) == stamp;
+      atomicAdd(&ctr->pop_cycles, (unsigned long long)(clock64() - t_pop));
+    }
     __syncthreads();
     const int tile = s_tile;
     if (tile < 0) {
@@ -542,6 +601,8 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       else err |= kErrInternal;
     }
     const long long t_start = clock64();
+    const bool hit = s_hit != 0;
+    uint32_t* rc_entry = rc_cache + (int64_t)tile * (kRcTileBytes / 4);
     uint32_t dmin = 0xFFFFFFFFu, dmax = 0, hmin = 0xFFFFFFFFu, hmax = 0;
     // labels with halo; directly outside the grid stands G, a root (label 0)
     for (int qd = tid; qd < TSH * TSH; qd += SEARCH_THREADS) {
@@ -555,7 +616,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
         pv = pG;
       } else {
         v = *((volatile const uint64_t*)&plab[i * p.C + j]);
-        pv = ppot[i * p.C + j];
+        pv = hit ? 0 : ppot[i * p.C + j];  // potentials only to build the arc costs
       }
       lab[r][c] = v;
       spot[r][c] = pv;
@@ -603,8 +664,21 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
     uint64_t orig[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) orig[k] = lab[warp + 8 * k + 1][lane + 1];
+    // arc costs: from this pass's cache entry, or built and stored there
+    if (hit) {
+      rc_from_cache(rc_entry, rc);
+    } else {
+      build_rc<FWD, false>(p, i0, j0, spot, rc, &err);
+      __syncthreads();
+      rc_to_cache(rc, rc_entry);
+      __threadfence();
+    }
+    if (narrow) rc_narrow(rc);  // the same chunks this thread moved: no barrier needed
+    if (!hit) {
+      __syncthreads();
+      if (tid == 0 && err == 0) st_release(&rc_pass[tile], stamp);
+    }
     if (narrow) {
-      build_rc<FWD, true>(p, i0, j0, spot, rc, &err);
       for (int qd = tid; qd < TSH * TSH; qd += SEARCH_THREADS) {
         const int r = qd / TSH, c = qd % TSH;
         const uint64_t v = lab[r][c];
@@ -615,8 +689,6 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
         }
         lab32[r][c] = x;
       }
-    } else {
-      build_rc<FWD, false>(p, i0, j0, spot, rc, &err);
     }
     __syncthreads();
     const long long t_loaded = clock64();
@@ -630,7 +702,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
         narrow = false;
         guard = false;
         if (tid == 0) atomicAdd(&ctr->redo64, 1ull);
-        build_rc<FWD, false>(p, i0, j0, spot, rc, &err);
+        rc_from_cache(rc_entry, rc);  // the reduced costs again (the entry holds them either way)
         __syncthreads();
       }
     }
@@ -1195,6 +1267,7 @@ __global__ void k_compact(Batch b, const int32_t* excess, int32_t* cand_base, ui
 
 // End of a pass: swap the candidate lists and decide whether to go on.
 __global__ void k_finish_pass(McfCtr* ctr) {
+  ctr->touched_total += (unsigned long long)ctr->ntouched;
   ctr->ntouched = 0;  // the list was reset with the labels
   if (!ctr->go_on) return;
   ctr->ncand = ctr->ncand_next;
@@ -1298,7 +1371,8 @@ bool trace_enabled() {
 // ---------------- host side ----------------
 
 int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
-  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 + (kMaxSearchGrid + 64) * 4 +
+  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8) + (n_nodes + 1) * 8 + n_tiles * (4 * 8 + kRcTileBytes + 4) +
+         (kMaxSearchGrid + 64) * 4 +
          n_probs * (sizeof(ProbDev) + 4 + 8 + 8 + 16 + 12) + (int64_t)sizeof(McfCtr) + 4096;
 }
 
@@ -1315,6 +1389,8 @@ ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n
             cudaMalloc(&sv->slots, (n_tiles + kMaxSearchGrid + 64) * 4) == cudaSuccess &&
             cudaMalloc(&sv->capped, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tile_prob, n_tiles * 4) == cudaSuccess &&
             cudaMalloc(&sv->touched, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tlist, n_tiles * 4) == cudaSuccess &&
+            cudaMalloc(&sv->rc_cache, n_tiles * kRcTileBytes) == cudaSuccess &&
+            cudaMalloc(&sv->rc_pass, n_tiles * 4) == cudaSuccess &&
             cudaMalloc(&sv->border, nb * 4) == cudaSuccess && cudaMalloc(&sv->probs, n_probs * sizeof(ProbDev)) == cudaSuccess &&
             cudaMalloc(&sv->prob_left, n_probs * 4) == cudaSuccess && cudaMalloc(&sv->g_net, n_probs * 8) == cudaSuccess &&
             cudaMalloc(&sv->tc, n_probs * 8) == cudaSuccess && cudaMalloc(&sv->ctr, sizeof(McfCtr)) == cudaSuccess &&
@@ -1349,6 +1425,8 @@ void solver_free(SolverWs* sv) {
   cudaFree(sv->capped);
   cudaFree(sv->touched);
   cudaFree(sv->tlist);
+  cudaFree(sv->rc_cache);
+  cudaFree(sv->rc_pass);
   cudaFree(sv->tile_prob);
   cudaFree(sv->border);
   cudaFree(sv->probs);
@@ -1484,6 +1562,7 @@ Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params
                 cudaMemsetAsync(sv->slots, 0, ring * 4, s) == cudaSuccess &&
                 cudaMemsetAsync(sv->capped, 0, sv->t_cap * 4, s) == cudaSuccess &&
                 cudaMemsetAsync(sv->touched, 0, sv->t_cap * 4, s) == cudaSuccess &&
+                cudaMemsetAsync(sv->rc_pass, 0, sv->t_cap * 4, s) == cudaSuccess &&  // pass numbers restart
                 (keep_ground_pot || cudaMemsetAsync(pot + g_index, 0, 8, s) == cudaSuccess)
             ? WW_OK
             : WW_ERR_CUDA;
@@ -1631,7 +1710,7 @@ ww_status Session::enqueue_pass() {
   const int bands = staged_zero ? kBandsStaged : kBands;
   for (int band = 0; band < bands; ++band) {
     k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped,
-                                                         sv->touched, sv->tlist);
+                                                         sv->touched, sv->tlist, sv->rc_cache, sv->rc_pass);
     k_ground_dist<FWD><<<ga, 256, 0, s>>>(b, sv->labels, pot, ctr);
     k_count_found<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->labels, sv->cand, 0, ctr);
     k_band_decide<<<1, 1, 0, s>>>(ctr, q, band == bands - 2 ? 1 : 0);
@@ -1667,10 +1746,11 @@ ww_status Session::pass(ww_solve_stats* st) {
   if (trace_enabled()) {
     std::fprintf(stderr,
                  "[ww] pass %d: cap %u, search %.3f ms, augment %d (D %u), left %d, visits %llu (32-bit %llu, redone "
-                 "%llu), status %d, go_on %d, ground sink %d (dG %u)\n",
+                 "%llu), tiles %lld, cycles visit %llu pop %llu, status %d, go_on %d, ground sink %d (dG %u)\n",
                  hc->passes, hc->cap, ms, hc->naug, hc->D, hc->ncand, (unsigned long long)hc->tile_visits,
-                 (unsigned long long)hc->visits32, (unsigned long long)hc->redo64, hc->status, hc->go_on, hc->gsink,
-                 hc->dG);
+                 (unsigned long long)hc->visits32, (unsigned long long)hc->redo64, (long long)hc->touched_total,
+                 (unsigned long long)hc->visit_cycles, (unsigned long long)hc->pop_cycles, hc->status, hc->go_on,
+                 hc->gsink, hc->dG);
     if (hc->err)
       std::fprintf(stderr, "[ww]   error flags %d; first negative reduced cost: node %lld dir %d value %lld (pass %d)\n",
                    hc->err, hc->dbg_node, hc->dbg_dir, hc->dbg_red, hc->dbg_pass);
