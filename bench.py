@@ -798,8 +798,9 @@ def run_served(args, summary=False):
     results = {}
     costs_alone = {}
     for load in args.loads:
+        saturated = not np.isfinite(load)
         rate = load * plain_px_s / (total_px / len(reqs))  # requests per second
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+        arrivals = np.zeros(len(reqs)) if saturated else np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
         srv = ww.Server(hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_request_pixels=biggest,
                         max_active=args.max_active)
         tickets = [None] * len(reqs)
@@ -834,6 +835,16 @@ def run_served(args, summary=False):
         st = srv.stats()
         srv.close()
         assert not bad, bad[:4]
+        if saturated and len(costs_alone) == len(reqs):
+            # every request at once: the plain loop's rate is the one measured above
+            mism = sum(1 for k in range(len(reqs)) if costs[k] != costs_alone[k])
+            results["saturated"] = {
+                "offered": "every request at t = 0 (above the server's capacity)",
+                "served": {"Mpixel_per_s": total_px / span / 1e6, "p50_ms": float(np.percentile(lat, 50)),
+                           "p99_ms": float(np.percentile(lat, 99)), "span_s": span, "stats": st},
+                "plain_loop_Mpixel_per_s": plain_px_s / 1e6,
+                "total_cost_mismatches_vs_alone": mism}
+            continue
         # plain loop on the same arrivals (FIFO, one at a time); check equality of costs
         plat = [0.0] * len(reqs)
         same_px = cmp_px = 0
@@ -915,7 +926,8 @@ def main():
                     help="headline line only (no components, bridging, variants, preprocessing, batched, served)")
     ap.add_argument("--served-pool", type=int, default=3, help="served: generated 4096x8192 scenes to crop")
     ap.add_argument("--distinct", type=int, default=64, help="served: distinct crops kept on the device")
-    ap.add_argument("--loads", type=float, nargs="+", default=[0.7, 1.5], help="served: offered load vs plain")
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.7, 1.5, float("inf")],
+                    help="served: offered load vs plain (inf: every request arrives at once, the server's capacity)")
     ap.add_argument("--tune-items", type=int, default=64, help="batched: autotuner sample size (0 = defaults)")
     ap.add_argument("--params", default="{}", help="solver schedule overrides, JSON (e.g. '{\"full_passes\": 0}')")
     ap.add_argument("--skip-plain", action="store_true", help="batched: no one-at-a-time comparison (profiling)")

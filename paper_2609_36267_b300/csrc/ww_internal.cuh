@@ -236,8 +236,11 @@ struct SolverWs {
   int32_t* capped;     // [t_cap] tile dropped a candidate at the distance cap
   int32_t* touched;    // [t_cap] 1 once the search visited the tile in this pass
   int32_t* tlist;      // [t_cap] tiles the search visited in this pass
-  uint32_t* rc_cache;  // [t_cap][4][32][32] reduced arc costs of each tile in the current pass
-  int32_t* rc_pass;    // [t_cap] pass + 1 whose arc costs rc_cache holds for the tile (0: none)
+  // reduced arc costs of tiles 0 .. rc_entries-1 in the current pass ([rc_entries][4][32][32]),
+  // and the pass + 1 whose costs an entry holds (0: none); tiles beyond are not cached
+  int64_t rc_entries;
+  uint32_t* rc_cache;
+  int32_t* rc_pass;
   int32_t* tile_prob;  // [t_cap] tile -> problem
   int32_t* border;     // border tiles of every problem
   void* probs;         // ProbDev [p_cap]

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
                                                            uint64_t* labels, SearchQ* q, int32_t* slots,
                                                            int32_t* inq, McfCtr* ctr, int32_t* capped_flag,
                                                            int32_t* touched, int32_t* tlist, uint32_t* rc_cache,
-                                                           int32_t* rc_pass) {
+                                                           int32_t* rc_pass, int32_t rc_entries) {
   __shared__ uint64_t lab[TSH][LROW];
   __shared__ uint32_t lab32[TSH][LROW];  // the same labels as 32-bit cells (a 32-bit visit)
   __shared__ uint32_t rc[4][TS][RCOL];
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       s_tile = t;
       // a cache entry of this pass holds every arc cost of the tile (acquire:
       // the entry's stores are seen before its stamp)
-      s_hit = t >= 0 && ld_acquire(&rc_pass[t]) == stamp;
+      s_hit = t >= 0 && t < rc_entries && ld_acquire(&rc_pass[t]) == stamp;
       atomicAdd(&ctr->pop_cycles, (unsigned long long)(clock64() - t_pop));
     }
     __syncthreads();
@@ -601,7 +602,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       else err |= kErrInternal;
     }
     const long long t_start = clock64();
-    const bool hit = s_hit != 0;
+    const bool hit = s_hit != 0, cached = tile < rc_entries;
     uint32_t* rc_entry = rc_cache + (int64_t)tile * (kRcTileBytes / 4);
     uint32_t dmin = 0xFFFFFFFFu, dmax = 0, hmin = 0xFFFFFFFFu, hmax = 0;
     // labels with halo; directly outside the grid stands G, a root (label 0)
@@ -670,11 +671,13 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
     } else {
       build_rc<FWD, false>(p, i0, j0, spot, rc, &err);
       __syncthreads();
-      rc_to_cache(rc, rc_entry);
-      __threadfence();
+      if (cached) {
+        rc_to_cache(rc, rc_entry);
+        __threadfence();
+      }
     }
-    if (narrow) rc_narrow(rc);  // the same chunks this thread moved: no barrier needed
-    if (!hit) {
+    if (narrow) rc_narrow(rc);  // the same chunks this thread moved (cache and conversion): no barrier needed
+    if (!hit && cached) {
       __syncthreads();
       if (tid == 0 && err == 0) st_release(&rc_pass[tile], stamp);
     }
@@ -702,7 +705,10 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
         narrow = false;
         guard = false;
         if (tid == 0) atomicAdd(&ctr->redo64, 1ull);
-        rc_from_cache(rc_entry, rc);  // the reduced costs again (the entry holds them either way)
+        // the reduced costs again: from the cache entry (written above on a miss),
+        // else built anew (potentials are loaded on every uncached visit)
+        if (cached) rc_from_cache(rc_entry, rc);
+        else build_rc<FWD, false>(p, i0, j0, spot, rc, &err);
         __syncthreads();
       }
     }
@@ -1370,9 +1376,20 @@ bool trace_enabled() {
 }
 // ---------------- host side ----------------
 
+// Arc-cost cache entries: the tiles that problems with n_nodes nodes in all
+// cover, by area plus their ragged edges for aspect ratios up to 16:1 (an R x C
+// problem has at most RC/1024 + (R + C)/32 + 1 tiles, R + C <= 4.25 sqrt(RC),
+// and the sum of sqrt(RC) over the problems is at most sqrt(n_probs n_nodes)).
+// Tile ids are handed out from 0, so these entries cover the tiles in use; the
+// tile capacity itself is a looser bound, and tiles past the entries go uncached.
+int64_t rc_cache_entries(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
+  const int64_t edges = (int64_t)std::ceil(4.25 / TS * std::sqrt((double)n_probs * (double)n_nodes));
+  return std::min<int64_t>(n_tiles, n_nodes / (TS * TS) + edges + 4 * n_probs + 64);
+}
+
 int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
-  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8) + (n_nodes + 1) * 8 + n_tiles * (4 * 8 + kRcTileBytes + 4) +
-         (kMaxSearchGrid + 64) * 4 +
+  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 +
+         rc_cache_entries(n_nodes, n_tiles, n_probs) * (kRcTileBytes + 4) + (kMaxSearchGrid + 64) * 4 +
          n_probs * (sizeof(ProbDev) + 4 + 8 + 8 + 16 + 12) + (int64_t)sizeof(McfCtr) + 4096;
 }
 
@@ -1389,8 +1406,8 @@ ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n
             cudaMalloc(&sv->slots, (n_tiles + kMaxSearchGrid + 64) * 4) == cudaSuccess &&
             cudaMalloc(&sv->capped, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tile_prob, n_tiles * 4) == cudaSuccess &&
             cudaMalloc(&sv->touched, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tlist, n_tiles * 4) == cudaSuccess &&
-            cudaMalloc(&sv->rc_cache, n_tiles * kRcTileBytes) == cudaSuccess &&
-            cudaMalloc(&sv->rc_pass, n_tiles * 4) == cudaSuccess &&
+            cudaMalloc(&sv->rc_cache, rc_cache_entries(n_nodes, n_tiles, n_probs) * kRcTileBytes) == cudaSuccess &&
+            cudaMalloc(&sv->rc_pass, rc_cache_entries(n_nodes, n_tiles, n_probs) * 4) == cudaSuccess &&
             cudaMalloc(&sv->border, nb * 4) == cudaSuccess && cudaMalloc(&sv->probs, n_probs * sizeof(ProbDev)) == cudaSuccess &&
             cudaMalloc(&sv->prob_left, n_probs * 4) == cudaSuccess && cudaMalloc(&sv->g_net, n_probs * 8) == cudaSuccess &&
             cudaMalloc(&sv->tc, n_probs * 8) == cudaSuccess && cudaMalloc(&sv->ctr, sizeof(McfCtr)) == cudaSuccess &&
@@ -1401,6 +1418,7 @@ ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n
             cudaMallocHost(&sv->host_probs, n_probs * sizeof(ProbDev)) == cudaSuccess &&
             cudaMallocHost(&sv->h_lists, (4 * n_probs + nb) * 4) == cudaSuccess;
   sv->nb_cap = nb;
+  sv->rc_entries = rc_cache_entries(n_nodes, n_tiles, n_probs);
   if (!ok) return WW_ERR_OOM;
   // best labels start unreached; worklist flags, ring slots, cap flags and visit
   // flags start (and end every search or pass) zero
@@ -1562,7 +1580,7 @@ Session::Session(SolverWs* sv_, int64_t* pot_, int64_t g_index_, const ww_params
                 cudaMemsetAsync(sv->slots, 0, ring * 4, s) == cudaSuccess &&
                 cudaMemsetAsync(sv->capped, 0, sv->t_cap * 4, s) == cudaSuccess &&
                 cudaMemsetAsync(sv->touched, 0, sv->t_cap * 4, s) == cudaSuccess &&
-                cudaMemsetAsync(sv->rc_pass, 0, sv->t_cap * 4, s) == cudaSuccess &&  // pass numbers restart
+                cudaMemsetAsync(sv->rc_pass, 0, sv->rc_entries * 4, s) == cudaSuccess &&  // pass numbers restart
                 (keep_ground_pot || cudaMemsetAsync(pot + g_index, 0, 8, s) == cudaSuccess)
             ? WW_OK
             : WW_ERR_CUDA;
@@ -1710,7 +1728,8 @@ ww_status Session::enqueue_pass() {
   const int bands = staged_zero ? kBandsStaged : kBands;
   for (int band = 0; band < bands; ++band) {
     k_search<FWD><<<search_grid, SEARCH_THREADS, 0, s>>>(b, pot, sv->labels, q, sv->slots, sv->inq, ctr, sv->capped,
-                                                         sv->touched, sv->tlist, sv->rc_cache, sv->rc_pass);
+                                                         sv->touched, sv->tlist, sv->rc_cache, sv->rc_pass,
+                                                         (int32_t)sv->rc_entries);
     k_ground_dist<FWD><<<ga, 256, 0, s>>>(b, sv->labels, pot, ctr);
     k_count_found<FWD><<<grid_cand, 256, 0, s>>>(sv->excess, sv->labels, sv->cand, 0, ctr);
     k_band_decide<<<1, 1, 0, s>>>(ctr, q, band == bands - 2 ? 1 : 0);

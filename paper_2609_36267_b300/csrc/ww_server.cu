@@ -105,6 +105,8 @@ struct ww_server {
   std::mutex mu;
   std::condition_variable cv, done_cv;
   std::deque<Request*> waiting;
+  const Request* head_blocked = nullptr;  // the queue's head while it does not fit
+  int head_rounds = 0;                    // worker rounds it has waited for room
   std::map<int64_t, Request*> tickets;
   std::vector<Request*> by_slot;
   int64_t next_ticket = 1;
@@ -164,12 +166,34 @@ void worker_loop(ww_server* S) {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv.wait(lk, [&] { return S->stop || !S->waiting.empty() || active > 0; });
       if (S->stop && S->waiting.empty() && active == 0) break;
-      // FIFO admission against the rings and the slot limit
-      while (!S->waiting.empty() && active + (int)admitted.size() < std::min<int>(max_slots, S->cfg.max_active)) {
-        Request* r = S->waiting.front();
-        if (!admit_one(S, r)) break;
-        S->waiting.pop_front();
-        admitted.push_back(r);
+      // Admission in arrival order against the rings and the slot limit.  A
+      // request that does not fit yet lets up to kAdmitLookahead later ones that
+      // do fit pass it; once the head has waited kHeadPatience rounds nothing
+      // passes it until the requests in flight free its room.
+      constexpr int kAdmitLookahead = 64, kHeadPatience = 16;
+      const int limit = std::min<int>(max_slots, S->cfg.max_active);
+      size_t k = 0;
+      int skipped = 0;
+      while (k < S->waiting.size() && active + (int)admitted.size() < limit) {
+        Request* r = S->waiting[k];
+        if (admit_one(S, r)) {
+          S->waiting.erase(S->waiting.begin() + (std::ptrdiff_t)k);
+          admitted.push_back(r);
+          if (k == 0) {
+            S->head_blocked = nullptr;
+            S->head_rounds = 0;
+          }
+          continue;
+        }
+        if (k == 0) {
+          if (S->head_blocked != r) {
+            S->head_blocked = r;
+            S->head_rounds = 0;
+          }
+          if (++S->head_rounds > kHeadPatience) break;
+        }
+        if (++skipped > kAdmitLookahead) break;
+        ++k;
       }
     }
     auto t_busy = Clock::now();
