@@ -227,6 +227,19 @@ __device__ int q_pop(int ring, SearchQ* q, int32_t* slots, int32_t* inq, uint32_
   return -2;
 }
 
+// Takes the tile at the worklist's head only if one is already published there
+// (never waits): -1 if none is, or another CTA took it first.
+__device__ int q_try_pop(int ring, SearchQ* q, int32_t* slots, int32_t* inq) {
+  const int h = ld_volatile(&q->head);
+  int* slot = &slots[h % ring];
+  const int v = ld_volatile(slot);
+  if (v == 0 || atomicCAS(&q->head, h, h + 1) != h) return -1;
+  atomicExch(slot, 0);
+  atomicExch(&inq[v - 1], 0);
+  __threadfence();
+  return v - 1;
+}
+
 constexpr uint64_t KINF = kInf >> 3;                  // (distance, hops) part of an unreached label
 constexpr uint64_t KDIST_INF = 0xFFFFFFFFull << 29;   // distance field all ones
 
@@ -341,8 +354,10 @@ __device__ __forceinline__ unsigned sweep_line(KT (*L)[LROW], const uint32_t (*W
 // so any interleaving leaves valid labels, and a round in which no sweep writes
 // leaves the fixed point.  A line is swept again only if another sweep wrote one
 // of its cells.  L is the label tile with its halo, rc the four arc-weight
-// planes, s_mask two rounds of change masks.  Returns the rounds run; *guard is
-// set when the fixed point was not reached within Keys<KT>::kRounds rounds.
+// planes, s_mask two rounds of change masks.  Run by warps 0..3 only (their own
+// barrier), so the other warps of the block are free meanwhile.  Returns the
+// rounds run; *guard is set when the fixed point was not reached within
+// Keys<KT>::kRounds rounds.
 template <class KT>
 __device__ __forceinline__ int relax_tile(KT (*L)[LROW], const uint32_t (*rc)[TS][RCOL], KT capK,
                                           unsigned (*s_mask)[8], bool* guard, int* err) {
@@ -355,23 +370,21 @@ __device__ __forceinline__ int relax_tile(KT (*L)[LROW], const uint32_t (*rc)[TS
       *guard = true;
       break;
     }
-    if (warp < 4) {
-      unsigned ch = 0;
-      if ((mine >> lane) & 1u) {
-        if (warp == 0) ch = sweep_line<KT, true, true>(L, rc[kDirLeft - 1], lane, capK8, kDirLeft, err);
-        else if (warp == 1) ch = sweep_line<KT, true, false>(L, rc[kDirRight - 1], lane, capK8, kDirRight, err);
-        else if (warp == 2) ch = sweep_line<KT, false, true>(L, rc[kDirUp - 1], lane, capK8, kDirUp, err);
-        else ch = sweep_line<KT, false, false>(L, rc[kDirDown - 1], lane, capK8, kDirDown, err);
-      }
-      // lines this warp wrote, and the lines of the other orientation it crossed
-      const unsigned lines = __ballot_sync(0xffffffffu, ch != 0);
-      const unsigned cross = __reduce_or_sync(0xffffffffu, ch);
-      if (lane == 0) {
-        s_mask[par][warp] = lines;
-        s_mask[par][4 + warp] = cross;
-      }
+    unsigned ch = 0;
+    if ((mine >> lane) & 1u) {
+      if (warp == 0) ch = sweep_line<KT, true, true>(L, rc[kDirLeft - 1], lane, capK8, kDirLeft, err);
+      else if (warp == 1) ch = sweep_line<KT, true, false>(L, rc[kDirRight - 1], lane, capK8, kDirRight, err);
+      else if (warp == 2) ch = sweep_line<KT, false, true>(L, rc[kDirUp - 1], lane, capK8, kDirUp, err);
+      else ch = sweep_line<KT, false, false>(L, rc[kDirDown - 1], lane, capK8, kDirDown, err);
     }
-    __syncthreads();
+    // lines this warp wrote, and the lines of the other orientation it crossed
+    const unsigned lines = __ballot_sync(0xffffffffu, ch != 0);
+    const unsigned cross = __reduce_or_sync(0xffffffffu, ch);
+    if (lane == 0) {
+      s_mask[par][warp] = lines;
+      s_mask[par][4 + warp] = cross;
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // warps 0..3
     const unsigned* m = s_mask[par];
     if ((m[0] | m[1] | m[2] | m[3]) == 0) break;
     // rows: written by the other row sweep or crossed by a column sweep; columns alike
@@ -550,6 +563,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
   __shared__ int64_t spot[TSH][TSH];  // potentials with halo (the ground outside the grid)
   __shared__ int side[4];
   __shared__ int s_tile, s_hit;
+  __shared__ int s_next;  // a tile taken from the worklist during the previous visit (-1: none)
   // smallest / largest distance and hop count of the finite labels of the tile and its halo
   __shared__ uint32_t s_dmin, s_dmax, s_hmin, s_hmax;
   __shared__ unsigned s_mask[2][8];  // change masks of the relaxation rounds
@@ -565,10 +579,13 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
   const uint32_t wait_polls = ctr->wait_polls;
   const int stamp = ctr->passes + 1;  // this pass in the arc-cost cache
   int err = 0;
+  if (tid == 0) s_next = -1;
   for (;;) {
     if (tid == 0) {
       const long long t_pop = clock64();
-      const int t = q_pop(ring, q, slots, inq, wait_polls);
+      int t = s_next;
+      s_next = -1;
+      if (t < 0) t = q_pop(ring, q, slots, inq, wait_polls);
       s_tile = t;
       // a cache entry of this pass holds every arc cost of the tile (acquire:
       // the entry's stores are seen before its stamp)
@@ -698,7 +715,9 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
     bool capped = false, guard = false;
     int rounds = 0;
     if (narrow) {
-      rounds = relax_tile<uint32_t>(lab32, rc, capK32, s_mask, &guard, &err);
+      if (warp < 4) rounds = relax_tile<uint32_t>(lab32, rc, capK32, s_mask, &guard, &err);
+      else if (tid == 4 * 32) s_next = q_try_pop(ring, q, slots, inq);  // the next tile, if one is waiting
+      __syncthreads();
       capped = tile_capped<uint32_t>(lab32, rc, capK32);
       if (__syncthreads_or((local && capped) || guard)) {
         // a candidate left the 32-bit range: the 64-bit visit from the loaded labels
@@ -713,7 +732,9 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
       }
     }
     if (!narrow) {
-      rounds += relax_tile<uint64_t>(lab, rc, capK, s_mask, &guard, &err);
+      if (warp < 4) rounds += relax_tile<uint64_t>(lab, rc, capK, s_mask, &guard, &err);
+      else if (tid == 4 * 32 && s_next < 0) s_next = q_try_pop(ring, q, slots, inq);
+      __syncthreads();
       capped = tile_capped<uint64_t>(lab, rc, capK);
       if (guard) err |= kErrInternal;  // no fixed point within the round limit
     }
@@ -751,22 +772,23 @@ __global__ void __launch_bounds__(SEARCH_THREADS, 5) k_search(Batch b, const int
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) {
-      bool ok = true;
-      if (side[0] && ti > 0) ok &= q_push(tile - p.tiles_x, ring, q, slots, inq, wait_polls);
-      if (side[1] && ti + 1 < p.tiles_y) ok &= q_push(tile + p.tiles_x, ring, q, slots, inq, wait_polls);
-      if (side[2] && tj > 0) ok &= q_push(tile - 1, ring, q, slots, inq, wait_polls);
-      if (side[3] && tj + 1 < p.tiles_x) ok &= q_push(tile + 1, ring, q, slots, inq, wait_polls);
-      if (!ok) err |= kErrSpin;
+    // the neighbours across the changed sides, one thread each (0 above, 1 below,
+    // 2 left, 3 right); each push is made visible before the visit counts as done
+    if (tid < 4 && side[tid]) {
+      const bool exists = tid == 0 ? ti > 0 : tid == 1 ? ti + 1 < p.tiles_y : tid == 2 ? tj > 0 : tj + 1 < p.tiles_x;
+      const int nb = tid == 0 ? tile - (int)p.tiles_x : tid == 1 ? tile + (int)p.tiles_x : tid == 2 ? tile - 1 : tile + 1;
+      if (exists && !q_push(nb, ring, q, slots, inq, wait_polls)) err |= kErrSpin;
+      __threadfence();
+    }
+    if (tid == 32) {
       atomicAdd(&ctr->tile_visits, 1ull);
       atomicAdd(&ctr->local_rounds, (unsigned long long)rounds);
       atomicAdd(&ctr->visit_cycles, (unsigned long long)(clock64() - t_start));
       atomicAdd(&ctr->load_cycles, (unsigned long long)(t_loaded - t_start));
       atomicAdd(&ctr->relax_cycles, (unsigned long long)(t_relaxed - t_loaded));
-      __threadfence();
-      atomicSub(&q->pending, 1);
     }
     __syncthreads();
+    if (tid == 0) atomicSub(&q->pending, 1);
   }
   if (err) atomicOr(&ctr->err, err);
 }
