@@ -827,8 +827,15 @@ __global__ void k_init_state(Batch b, const int32_t* slots, int32_t* excess, int
     }
     excess[p.node_off + v] = r;
     labels[p.node_off + v] = kInf;
+    // one list append per warp: the warp's imbalanced nodes take consecutive
+    // slots in lane order (the list order does not matter to the solver)
+    const unsigned act = __activemask(), bal = __ballot_sync(act, r != 0);
+    const int lead = __ffs((int)act) - 1, lane = (int)(threadIdx.x & 31);
+    int base = 0;
+    if (lane == lead && bal) base = atomicAdd(&ctr->ncand, __popc(bal));
+    base = __shfl_sync(act, base, lead);
     if (r != 0) {
-      cand[atomicAdd(&ctr->ncand, 1)] = (int32_t)(p.node_off + v);
+      cand[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)(p.node_off + v);
       ++cnt;
     }
   }
@@ -1283,12 +1290,22 @@ __global__ void k_compact(Batch b, const int32_t* excess, int32_t* cand_base, ui
   const int nc = ctr->ncand;
   const int32_t* cand = cand_cur(cand_base, ctr, b.n_total);
   int32_t* next = cand_nxt(cand_base, ctr, b.n_total);
+  const int lane = (int)(threadIdx.x & 31);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
     int32_t v = cand[q];
     labels[v] = kInf;  // a root on a tile the search did not reach (an aborted search)
-    if (excess[v] != 0) {
-      next[atomicAdd(&ctr->ncand_next, 1)] = v;
-      atomicAdd(&prob_left[prob_of_node(b, v)], 1);
+    const bool keep = excess[v] != 0;
+    // one list append per warp (slots in lane order), one count per problem in the warp
+    const unsigned act = __activemask(), bal = __ballot_sync(act, keep);
+    const int lead = __ffs((int)act) - 1;
+    int base = 0;
+    if (lane == lead && bal) base = atomicAdd(&ctr->ncand_next, __popc(bal));
+    base = __shfl_sync(act, base, lead);
+    const int slot = keep ? prob_of_node(b, v) : -1;
+    const unsigned same = __match_any_sync(act, slot);
+    if (keep) {
+      next[base + __popc(bal & ((1u << lane) - 1u))] = v;
+      if (lane == __ffs((int)same) - 1) atomicAdd(&prob_left[slot], __popc(same));
     }
   }
 }
