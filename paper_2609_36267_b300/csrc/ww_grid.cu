@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(RTX* RTT) k_residues(const void* __restrict__ 
 }
 
 // ---------------- costs ----------------
-constexpr int CTX = 32, CTY = 16, CW = 3;  // tile, max box half-width
+constexpr int CTX = 32, CTY = 32, CW = 3;  // tile, max box half-width
 
 struct SteepCtr {
   unsigned long long valid_edges;   // [0]
@@ -103,6 +103,11 @@ __device__ __forceinline__ float edge_d(float a, float b) {
 
 // Slope estimate from the row partial sums of the fixed-point gradients: the
 // vertical sum over the window's rows, then S / (cnt 2^22) rounded once.
+// S / (cnt 2^22) rounded once: the fixed-point window sum of the gradients as a slope
+__device__ __forceinline__ float slope_of_sum(int32_t S, int cnt) {
+  return __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
+}
+
 template <int W>
 __device__ __forceinline__ float window_mean(const int32_t (*rs)[CTX], const uint8_t (*ns)[CTX], int R, int c, int w) {
   int32_t S = 0;
@@ -256,30 +261,49 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     nv[r][c] = (uint8_t)cb;
   }
   __syncthreads();
-  // 4. vertical sums, slope estimate, LUT gather, mask rule; steep candidates
+  // 4. vertical sums, slope estimate, LUT gather, mask rule; steep candidates.
+  // A thread takes column c of the tile and a strip of kStrip consecutive rows,
+  // so the vertical window sums of the mean slope slide down the strip (the
+  // same integer sums as summing each window anew).
   const int64_t P = m * n;
   unsigned cnt_valid = 0;
   int charge = 0;  // sum of this thread's residues (Eq. 1), when res is given
   const unsigned lane = tid & 31, warp = tid >> 5;
-  // block-level counting: one global atomic per block and iteration, not per warp
-  __shared__ unsigned s_wtot[2][8];
-  __shared__ unsigned long long s_base[2];
-  __shared__ unsigned s_valid[8];
-  int it = 0;
-  for (int q = tid; q < CTY * CTX; q += 256, it ^= 1) {  // every thread runs the same number of iterations
-    int r = q / CTX, c = q % CTX;
-    int64_t i = i0 + r, j = j0 + c;
-    bool hcand = false, vcand = false;
-    const bool inside = i < m && j < n;
-    int R = r + HW, C = c + HW;
-    int64_t k = i * n + j;
-    if (inside) {
+  constexpr int kStrip = CTY / 8;  // 8 warps of 32 columns cover the tile's rows
+  const int c = (int)lane, r0 = (int)warp * kStrip, C = c + HW;
+  unsigned hcand = 0, vcand = 0;  // steep candidates of the strip: bit t for row r0 + t
+  int32_t wsh = 0, wsv = 0;       // SLOPE 0: window sums of the h and v gradients
+  int wch = 0, wcv = 0;           // and of their valid counts
+  if constexpr (SLOPE == 0) {
+    for (int d = -w; d <= w; ++d) {
+      const int RR = r0 + HW + d;
+      wsh += rh[RR][c];
+      wch += nh[RR][c];
+      wsv += rv[RR][c];
+      wcv += nv[RR][c];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kStrip; ++t) {
+    const int r = r0 + t, R = r + HW;
+    if constexpr (SLOPE == 0) {
+      if (t > 0) {  // the window moves down one row
+        const int in = R + w, out = R - w - 1;
+        wsh += rh[in][c] - rh[out][c];
+        wch += (int)nh[in][c] - (int)nh[out][c];
+        wsv += rv[in][c] - rv[out][c];
+        wcv += (int)nv[in][c] - (int)nv[out][c];
+      }
+    }
+    const int64_t i = i0 + r, j = j0 + c;
+    if (i >= m || j >= n) continue;
+    const int64_t k = i * n + j;
     // h edge (i,j)
     int16_t hp = 0, hm = 0;
     if (eh[R][C]) {
       float ah;
       if constexpr (SLOPE == 0)
-        ah = window_mean<W>(rh, nh, R, c, w);
+        ah = slope_of_sum(wsh, wch);
       else
         ah = window_phasor(qh, yh, eh, R, C, w);
       const float ge = fminf(sc[R][C], sc[R][C + 1]);
@@ -292,7 +316,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
         hm = bilinear_cost(ratio, -ah, ge);
       }
       ++cnt_valid;
-      hcand = fabsf(edge_d(sp[R][C], sp[R][C + 1])) > steep_rad;
+      if (fabsf(edge_d(sp[R][C], sp[R][C + 1])) > steep_rad) hcand |= 1u << t;
     }
     costs[k] = hp;
     costs[P + k] = hm;
@@ -300,7 +324,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     if (ev[R][C]) {
       float av;
       if constexpr (SLOPE == 0)
-        av = window_mean<W>(rv, nv, R, c, w);
+        av = slope_of_sum(wsv, wcv);
       else
         av = window_phasor(qv, yv, ev, R, C, w);
       const float ge = fminf(sc[R][C], sc[R + 1][C]);
@@ -313,7 +337,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
         vm = bilinear_cost(ratio, -av, ge);
       }
       ++cnt_valid;
-      vcand = fabsf(edge_d(sp[R][C], sp[R + 1][C])) > steep_rad;
+      if (fabsf(edge_d(sp[R][C], sp[R + 1][C])) > steep_rad) vcand |= 1u << t;
     }
     costs[2 * P + k] = vp;
     costs[3 * P + k] = vm;
@@ -327,49 +351,57 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
       res[i * (n - 1) + j] = (int8_t)rr;
       charge += rr;
     }
-    }
-    // count the candidates (warp ballots, then the block); the block's base in the
-    // list plus the earlier warps' counts place each warp's keys
-    const unsigned bh = __ballot_sync(0xffffffffu, hcand), bv = __ballot_sync(0xffffffffu, vcand);
-    const unsigned n_h = __popc(bh), tot = n_h + __popc(bv);
-    if (lane == 0) s_wtot[it][warp] = tot;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned bt = 0;
-      for (int w2 = 0; w2 < 8; ++w2) bt += s_wtot[it][w2];
-      s_base[it] = bt ? atomicAdd(&ctr->candidates, (unsigned long long)bt) : 0ull;
-    }
-    __syncthreads();
-    unsigned long long base = s_base[it];
-    for (unsigned w2 = 0; w2 < warp; ++w2) base += s_wtot[it][w2];
-    if (list) {
-      const unsigned below = (1u << lane) - 1u;
-      if (hcand) {
-        const unsigned long long at = base + __popc(bh & below);
-        if (at < list_cap) list[at] = (uint32_t)k;
-      }
-      if (vcand) {
-        const unsigned long long at = base + n_h + __popc(bv & below);
-        if (at < list_cap) list[at] = (uint32_t)(P + k);
-      }
-    }
   }
+  // count the candidates of the block (one global atomic) and place each thread's
+  // keys after the earlier threads' (an exclusive scan of the per-thread counts)
+  const unsigned mine = __popc(hcand) + __popc(vcand);
+  unsigned incl = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  __shared__ unsigned s_wsum[8];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned s_valid[8];
+  __shared__ int s_charge[8];
+  if (lane == 31) s_wsum[warp] = incl;
   for (int o = 16; o > 0; o >>= 1) cnt_valid += __shfl_xor_sync(0xffffffffu, cnt_valid, o);
   if (lane == 0) s_valid[warp] = cnt_valid;
-  __shared__ int s_charge[8];
   if (res) {
     for (int o = 16; o > 0; o >>= 1) charge += __shfl_xor_sync(0xffffffffu, charge, o);
     if (lane == 0) s_charge[warp] = charge;
   }
   __syncthreads();
   if (tid == 0) {
+    unsigned tot = 0;
     unsigned long long v = 0;
-    for (int w2 = 0; w2 < 8; ++w2) v += s_valid[w2];
+    for (int w2 = 0; w2 < 8; ++w2) {
+      tot += s_wsum[w2];
+      v += s_valid[w2];
+    }
+    s_base = tot ? atomicAdd(&ctr->candidates, (unsigned long long)tot) : 0ull;
     if (v) atomicAdd(&ctr->valid_edges, v);
     if (res) {
       int t = 0;
       for (int w2 = 0; w2 < 8; ++w2) t += s_charge[w2];
       if (t) atomicAdd(ground, -t);  // the ground takes minus the total charge
+    }
+  }
+  __syncthreads();
+  if (list && mine) {
+    unsigned long long at = s_base + (incl - mine);
+    for (unsigned w2 = 0; w2 < warp; ++w2) at += s_wsum[w2];
+#pragma unroll
+    for (int t = 0; t < kStrip; ++t) {
+      const int64_t k = (i0 + r0 + t) * n + (j0 + c);
+      if ((hcand >> t) & 1u) {
+        if (at < list_cap) list[at] = (uint32_t)k;
+        ++at;
+      }
+      if ((vcand >> t) & 1u) {
+        if (at < list_cap) list[at] = (uint32_t)(P + k);
+        ++at;
+      }
     }
   }
 }
