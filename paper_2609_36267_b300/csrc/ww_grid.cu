@@ -171,6 +171,8 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
   __shared__ int32_t qh[EY][EX + 1], qv[EY][EX + 1];
   __shared__ int32_t yh[SLOPE ? EY : 1][EX + 1], yv[SLOPE ? EY : 1][EX + 1];  // sin part (SLOPE 1)
   __shared__ uint8_t eh[EY][EX + 1], ev[EY][EX + 1];
+  // per edge: its wrap count + 1 (bits 0-1, for the residues) and the steep test (bit 2)
+  __shared__ uint8_t fh[EY][EX + 1], fv[EY][EX + 1];
   __shared__ int32_t rh[SLOPE ? 1 : EY][CTX], rv[SLOPE ? 1 : EY][CTX];  // row (horizontal) partial sums
   __shared__ uint8_t nh[SLOPE ? 1 : EY][CTX], nv[SLOPE ? 1 : EY][CTX];  // row partial counts
   const int64_t i0 = by * CTY, j0 = bx * CTX;
@@ -203,29 +205,45 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
     int r = q / EX, c = q % EX;
     int64_t i = i0 - HW + r, j = j0 - HW + c;
     int32_t a = 0, b = 0, ya = 0, yb = 0;
-    uint8_t ea = 0, eb = 0;
+    uint8_t ea = 0, eb = 0, fa = 0, fb = 0;
     if (i >= 0 && i < m && j >= 0) {
-      if (j + 1 < n && sv[r][c] && sv[r][c + 1]) {
-        const float d = edge_d(sp[r][c], sp[r][c + 1]);
-        if constexpr (SLOPE == 0)
-          a = __float2int_rn(__fmul_rn(d, kQScale));
-        else
-          cordic_cos_sin(__float2int_rn(__fmul_rn(d, 536870912.0f)), &a, &ya);
-        ea = 1;
+      // the wrapped difference of edge_d, kept apart: its wrap count serves the
+      // residues whether or not the pixels are valid (invalid phases are 0)
+      if (j + 1 < n) {
+        const float dp = __fsub_rn(sp[r][c + 1], sp[r][c]);
+        const int wc = wrap_count(dp);
+        fa = (uint8_t)(wc + 1);
+        if (sv[r][c] && sv[r][c + 1]) {
+          const float d = __fsub_rn(dp, __fmul_rn(kTwoPiF, (float)wc));
+          if constexpr (SLOPE == 0)
+            a = __float2int_rn(__fmul_rn(d, kQScale));
+          else
+            cordic_cos_sin(__float2int_rn(__fmul_rn(d, 536870912.0f)), &a, &ya);
+          ea = 1;
+          if (fabsf(d) > steep_rad) fa |= 4;
+        }
       }
-      if (i + 1 < m && j < n && sv[r][c] && sv[r + 1][c]) {
-        const float d = edge_d(sp[r][c], sp[r + 1][c]);
-        if constexpr (SLOPE == 0)
-          b = __float2int_rn(__fmul_rn(d, kQScale));
-        else
-          cordic_cos_sin(__float2int_rn(__fmul_rn(d, 536870912.0f)), &b, &yb);
-        eb = 1;
+      if (i + 1 < m && j < n) {
+        const float dp = __fsub_rn(sp[r + 1][c], sp[r][c]);
+        const int wc = wrap_count(dp);
+        fb = (uint8_t)(wc + 1);
+        if (sv[r][c] && sv[r + 1][c]) {
+          const float d = __fsub_rn(dp, __fmul_rn(kTwoPiF, (float)wc));
+          if constexpr (SLOPE == 0)
+            b = __float2int_rn(__fmul_rn(d, kQScale));
+          else
+            cordic_cos_sin(__float2int_rn(__fmul_rn(d, 536870912.0f)), &b, &yb);
+          eb = 1;
+          if (fabsf(d) > steep_rad) fb |= 4;
+        }
       }
     }
     qh[r][c] = a;
     eh[r][c] = ea;
     qv[r][c] = b;
     ev[r][c] = eb;
+    fh[r][c] = fa;
+    fv[r][c] = fb;
     if constexpr (SLOPE == 1) {
       yh[r][c] = ya;
       yv[r][c] = yb;
@@ -316,7 +334,7 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
         hm = bilinear_cost(ratio, -ah, ge);
       }
       ++cnt_valid;
-      if (fabsf(edge_d(sp[R][C], sp[R][C + 1])) > steep_rad) hcand |= 1u << t;
+      if (fh[R][C] & 4) hcand |= 1u << t;
     }
     costs[k] = hp;
     costs[P + k] = hm;
@@ -337,17 +355,15 @@ __device__ __forceinline__ void costs_tile(const void* __restrict__ ifg, int is_
         vm = bilinear_cost(ratio, -av, ge);
       }
       ++cnt_valid;
-      if (fabsf(edge_d(sp[R][C], sp[R + 1][C])) > steep_rad) vcand |= 1u << t;
+      if (fv[R][C] & 4) vcand |= 1u << t;
     }
     costs[2 * P + k] = vp;
     costs[3 * P + k] = vm;
     // residue of the node whose top-left pixel is (i,j), from the same prepared phases
     if (res && i < m - 1 && j < n - 1) {
-      const int n_top = wrap_count(__fsub_rn(sp[R][C + 1], sp[R][C]));
-      const int n_right = wrap_count(__fsub_rn(sp[R + 1][C + 1], sp[R][C + 1]));
-      const int n_bottom = wrap_count(__fsub_rn(sp[R + 1][C + 1], sp[R + 1][C]));
-      const int n_left = wrap_count(__fsub_rn(sp[R + 1][C], sp[R][C]));
-      const int rr = -(n_top + n_right - n_bottom - n_left);
+      // -(top + right - bottom - left) of the four wrap counts around the node
+      // (the +1 of the stored counts cancels)
+      const int rr = -((fh[R][C] & 3) + (fv[R][C + 1] & 3) - (fh[R + 1][C] & 3) - (fv[R][C] & 3));
       res[i * (n - 1) + j] = (int8_t)rr;
       charge += rr;
     }
