@@ -241,6 +241,7 @@ struct SolverWs {
   int64_t rc_entries;
   uint32_t* rc_cache;
   int32_t* rc_pass;
+  uint16_t* exits;     // [n_cap] per node reached in the pass: tile-local index where its parent chain leaves the tile
   int32_t* tile_prob;  // [t_cap] tile -> problem
   int32_t* border;     // border tiles of every problem
   void* probs;         // ProbDev [p_cap]

@@ -1003,17 +1003,75 @@ __device__ __forceinline__ bool step_parent(const ProbDev& p, int d, int64_t* i,
   }
 }
 
-// Walk from local node v along the forest to its tree root (local index), or
-// -1 after more steps than nodes (reported as an internal error).  The walk
-// keeps the node's row and column, so a step costs one label load.
-__device__ __forceinline__ int64_t walk_root(const ProbDev& p, const uint64_t* plab, int64_t v) {
+// The root of local node v's search tree: the end of its parent chain, a root
+// (direction kDirRoot) or the node whose parent is the ground.  The walk crosses
+// a tile per step: from a node to the last node of its parent chain inside its
+// tile (k_tile_exits), then one step to that node's parent.  Every node on the
+// chain holds a label of this pass, so its tile was visited and its exit is
+// current.  -1 if the chain is longer than the grid (corrupt labels).
+__device__ __forceinline__ int64_t walk_root_tiles(const ProbDev& p, const uint64_t* plab, const uint16_t* pexit,
+                                                   int64_t v) {
   int64_t i = v / p.C, j = v - (v / p.C) * p.C;
   for (int64_t steps = 0; steps <= p.N; ++steps) {
+    const int ex = pexit[i * p.C + j];
+    i = (i / TS) * TS + ex / TS;
+    j = (j / TS) * TS + ex % TS;
     const int d = label_dir(plab[i * p.C + j]);
     if (d == kDirRoot) return i * p.C + j;
-    if (!step_parent(p, d, &i, &j)) return i * p.C + j;  // parent is the ground: (i, j) roots a subtree of it
+    if (!step_parent(p, d, &i, &j)) return i * p.C + j;  // parent is the ground
   }
   return -1;
+}
+
+// After a pass's search: for every node of a tile the pass visited, the
+// tile-local index of the node where its parent chain leaves the tile (the node
+// itself when its parent lies outside the tile or is the ground, or when it is
+// a root or unreached), by pointer jumping in shared memory: a chain inside a
+// tile has at most 1024 nodes, so 10 rounds.  Labels are final here (the
+// search has converged), and parent chains have no cycles.
+__global__ void __launch_bounds__(256) k_tile_exits(Batch b, const uint64_t* labels, const int32_t* tlist,
+                                                    uint16_t* exits, const McfCtr* ctr) {
+  if (!ctr->go_on || ctr->err) return;
+  __shared__ uint16_t e[2][TS * TS];
+  const int nt = ctr->ntouched;
+  for (int k = blockIdx.x; k < nt; k += gridDim.x) {
+    const int tile = tlist[k];
+    const ProbDev& p = b.probs[b.tile_prob[tile]];
+    const int64_t lt = tile - p.tile_off;
+    const int64_t i0 = (lt / p.tiles_x) * TS, j0 = (lt % p.tiles_x) * TS;
+    const uint64_t* plab = labels + p.node_off;
+    for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
+      const int r = q / TS, c = q % TS;
+      int nx = q;
+      if (i0 + r < p.R && j0 + c < p.C) {
+        const uint64_t lab = plab[(i0 + r) * p.C + j0 + c];
+        if (lab != kInf) {
+          int rr = r, cc = c;
+          switch (label_dir(lab)) {
+            case kDirUp: --rr; break;
+            case kDirDown: ++rr; break;
+            case kDirLeft: --cc; break;
+            case kDirRight: ++cc; break;
+            default: rr = -1; break;  // a root
+          }
+          if (rr >= 0 && rr < TS && cc >= 0 && cc < TS && i0 + rr < p.R && j0 + cc < p.C) nx = rr * TS + cc;
+        }
+      }
+      e[0][q] = (uint16_t)nx;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int round = 0; round < 10; ++round) {
+      for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) e[cur ^ 1][q] = e[cur][e[cur][q]];
+      cur ^= 1;
+      __syncthreads();
+    }
+    for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
+      const int r = q / TS, c = q % TS;
+      if (i0 + r < p.R && j0 + c < p.C) exits[p.node_off + (i0 + r) * p.C + j0 + c] = e[cur][q];
+    }
+    __syncthreads();
+  }
 }
 
 // Ground arc k of a problem (k < 2C + 2R): its border node (local) and the side
@@ -1084,7 +1142,8 @@ __device__ __forceinline__ uint32_t ground_vid(const ProbDev& p, int64_t k) {
 // Trees that reach the ground at exactly dG propose it (ground candidates farther
 // away could not augment: the pass radius is at most dG).
 template <bool FWD>
-__global__ void k_select_ground(Batch b, const uint64_t* labels, const int64_t* pot, uint64_t* best, McfCtr* ctr) {
+__global__ void k_select_ground(Batch b, const uint64_t* labels, const uint16_t* exits, const int64_t* pot,
+                                uint64_t* best, McfCtr* ctr) {
   if (!ctr->go_on || ctr->err || !ctr->gsink || ctr->dG == 0xFFFFFFFFu) return;
   const ProbDev& p = b.probs[b.order[blockIdx.y]];
   const int64_t na = 2 * (p.C + p.R), pG = pot[b.g_index];
@@ -1094,7 +1153,7 @@ __global__ void k_select_ground(Batch b, const uint64_t* labels, const int64_t* 
     int side;
     const uint32_t d = ground_arc_dist<FWD>(p, plab, pot + p.node_off, pG, k, &v, &side);
     if (d != ctr->dG) continue;
-    const int64_t r = walk_root(p, plab, v);
+    const int64_t r = walk_root_tiles(p, plab, exits + p.node_off, v);
     if (r < 0) {
       atomicOr(&ctr->err, kErrWalk);
       continue;
@@ -1104,8 +1163,8 @@ __global__ void k_select_ground(Batch b, const uint64_t* labels, const int64_t* 
 }
 
 template <bool FWD>
-__global__ void k_select(Batch b, const int32_t* excess, const uint64_t* labels, int32_t* cand_base,
-                         int32_t* cand_root, uint64_t* best, McfCtr* ctr) {
+__global__ void k_select(Batch b, const int32_t* excess, const uint64_t* labels, const uint16_t* exits,
+                         int32_t* cand_base, int32_t* cand_root, uint64_t* best, McfCtr* ctr) {
   if (!ctr->go_on) return;
   // a search that stopped on an error left labels that are not shortest
   // distances: the pass then augments nothing, so flows and potentials stay
@@ -1122,7 +1181,7 @@ __global__ void k_select(Batch b, const int32_t* excess, const uint64_t* labels,
     uint64_t l = labels[t];
     if (l == kInf) continue;
     const ProbDev& p = b.probs[prob_of_node(b, t)];
-    int64_t r = walk_root(p, labels + p.node_off, t - p.node_off);
+    int64_t r = walk_root_tiles(p, labels + p.node_off, exits + p.node_off, t - p.node_off);
     if (r < 0) {
       atomicOr(&ctr->err, kErrWalk);
       continue;
@@ -1211,8 +1270,8 @@ __global__ void k_reset_best(Batch b, const int32_t* cand_root, uint64_t* best, 
 // Trees whose best candidate is the ground: one unit through the ground arc
 // (forward: root -> ... -> v -> G, the ground absorbs; reverse: G -> v -> ... -> root).
 template <bool FWD>
-__global__ void k_augment_ground(Batch b, int32_t* excess, const uint64_t* labels, const int64_t* pot,
-                                 uint64_t* best, long long* g_net, McfCtr* ctr) {
+__global__ void k_augment_ground(Batch b, int32_t* excess, const uint64_t* labels, const uint16_t* exits,
+                                 const int64_t* pot, uint64_t* best, long long* g_net, McfCtr* ctr) {
   if (!ctr->go_on || ctr->err || !ctr->gsink || ctr->dG == 0xFFFFFFFFu) return;
   const int slot = b.order[blockIdx.y];
   const ProbDev& p = b.probs[slot];
@@ -1223,7 +1282,7 @@ __global__ void k_augment_ground(Batch b, int32_t* excess, const uint64_t* label
     int side;
     const uint32_t d = ground_arc_dist<FWD>(p, plab, pot + p.node_off, pG, k, &v, &side);
     if (d != ctr->dG) continue;
-    const int64_t r = walk_root(p, plab, v);
+    const int64_t r = walk_root_tiles(p, plab, exits + p.node_off, v);
     if (r < 0 || best[p.node_off + r] != (((uint64_t)d << 32) | ground_vid(p, k))) continue;
     // clear the tree's word here: once the ground arc is flipped it is no longer
     // residual, so no later pass over the arcs could tell which trees proposed it
@@ -1427,7 +1486,7 @@ int64_t rc_cache_entries(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
 }
 
 int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
-  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 +
+  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8 + 2) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 +
          rc_cache_entries(n_nodes, n_tiles, n_probs) * (kRcTileBytes + 4) + (kMaxSearchGrid + 64) * 4 +
          n_probs * (sizeof(ProbDev) + 4 + 8 + 8 + 16 + 12) + (int64_t)sizeof(McfCtr) + 4096;
 }
@@ -1447,6 +1506,7 @@ ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n
             cudaMalloc(&sv->touched, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tlist, n_tiles * 4) == cudaSuccess &&
             cudaMalloc(&sv->rc_cache, rc_cache_entries(n_nodes, n_tiles, n_probs) * kRcTileBytes) == cudaSuccess &&
             cudaMalloc(&sv->rc_pass, rc_cache_entries(n_nodes, n_tiles, n_probs) * 4) == cudaSuccess &&
+            cudaMalloc(&sv->exits, n_nodes * 2) == cudaSuccess &&
             cudaMalloc(&sv->border, nb * 4) == cudaSuccess && cudaMalloc(&sv->probs, n_probs * sizeof(ProbDev)) == cudaSuccess &&
             cudaMalloc(&sv->prob_left, n_probs * 4) == cudaSuccess && cudaMalloc(&sv->g_net, n_probs * 8) == cudaSuccess &&
             cudaMalloc(&sv->tc, n_probs * 8) == cudaSuccess && cudaMalloc(&sv->ctr, sizeof(McfCtr)) == cudaSuccess &&
@@ -1484,6 +1544,7 @@ void solver_free(SolverWs* sv) {
   cudaFree(sv->tlist);
   cudaFree(sv->rc_cache);
   cudaFree(sv->rc_pass);
+  cudaFree(sv->exits);
   cudaFree(sv->tile_prob);
   cudaFree(sv->border);
   cudaFree(sv->probs);
@@ -1777,11 +1838,13 @@ ww_status Session::enqueue_pass() {
   }
   if (!capturing) WW_CUDA_TRY(cudaEventRecord(ev[1], s));
   k_clear_capped<<<grid_tiles, 256, 0, s>>>(b, sv->capped, ctr);
-  k_select<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, ctr);
-  k_select_ground<FWD><<<ga, 256, 0, s>>>(b, sv->labels, pot, sv->best, ctr);
+  k_tile_exits<<<sm_count * 8, 256, 0, s>>>(b, sv->labels, sv->tlist, sv->exits, ctr);
+  k_select<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->exits, sv->cand, sv->cand_root, sv->best,
+                                          ctr);
+  k_select_ground<FWD><<<ga, 256, 0, s>>>(b, sv->labels, sv->exits, pot, sv->best, ctr);
   k_augment<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, sv->g_net,
                                            ctr);
-  k_augment_ground<FWD><<<ga, 256, 0, s>>>(b, sv->excess, sv->labels, pot, sv->best, sv->g_net, ctr);
+  k_augment_ground<FWD><<<ga, 256, 0, s>>>(b, sv->excess, sv->labels, sv->exits, pot, sv->best, sv->g_net, ctr);
   k_reset_best<<<grid_cand, 256, 0, s>>>(b, sv->cand_root, sv->best, sv->prob_left, (int)sv->p_cap, ctr);
   k_potentials<FWD><<<sm_count * 8, 256, 0, s>>>(b, sv->labels, pot, sv->touched, sv->tlist, ctr);
   k_potential_ground<FWD><<<1, 1, 0, s>>>(b, pot, ctr);
