@@ -903,9 +903,9 @@ def launch_count(st, steps, prm):
     # bands per pass: 4, or 6 when the zero band's hop radius grows in stages
     bands = 6 if prm.zero_band_hops_min < prm.zero_band_hops else 4
     # pass_setup, set_roots, seed_tiles, bands x (search, ground_dist, count_found, band_decide)
-    # + (bands - 1) reseeds, clear_capped, tile_exits, select, select_ground, augment, augment_ground,
-    # reset_best, potentials, potential_ground, compact, finish_pass
-    per_pass = 3 + bands * 4 + (bands - 1) + 11
+    # + (bands - 1) reseeds, clear_capped, tile_exits, select, select_ground, augment, flip_segments,
+    # augment_ground, reset_best, potentials, potential_ground, compact, finish_pass
+    per_pass = 3 + bands * 4 + (bands - 1) + 12
     return int((grid + solver_fixed + st["passes"] * per_pass) * steps)
 
 

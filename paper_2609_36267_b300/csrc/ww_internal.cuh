@@ -242,6 +242,7 @@ struct SolverWs {
   uint32_t* rc_cache;
   int32_t* rc_pass;
   uint16_t* exits;     // [n_cap] per node reached in the pass: tile-local index where its parent chain leaves the tile
+  int32_t* segs;       // [n_cap] first nodes of the tile segments of a pass's augmenting paths
   int32_t* tile_prob;  // [t_cap] tile -> problem
   int32_t* border;     // border tiles of every problem
   void* probs;         // ProbDev [p_cap]

@@ -125,6 +125,8 @@ struct McfCtr {
   unsigned long long redo64;    // of which redone in 64-bit keys (a candidate left the 32-bit range)
   unsigned long long pop_cycles;  // SM cycles spent taking tiles from the worklist (waits included)
   unsigned long long touched_total;  // distinct tiles visited, summed over passes
+  int32_t nseg;        // tile segments of this pass's augmenting paths (k_augment -> k_flip_segments)
+  int32_t nseg_pad;
 };
 
 // Problems live in slots (stable ids); `order` lists the active slots sorted by
@@ -848,6 +850,7 @@ __global__ void k_init_state(Batch b, const int32_t* slots, int32_t* excess, int
 // counters and the worklist.
 __global__ void k_pass_setup(McfCtr* ctr, SearchQ* q) {
   if (!ctr->go_on) return;
+  ctr->nseg = 0;
   ctr->D = 0;
   ctr->naug = 0;
   ctr->found = 0;
@@ -1225,9 +1228,15 @@ __device__ __forceinline__ void flip_path(const ProbDev& p, const uint64_t* plab
   }
 }
 
+// The winner of every tree: its unit of flow runs along its path (forward: root
+// -> t; reverse: t -> root).  The paths of one pass lie in different trees, so
+// they share no node; each is cut into its tile segments (from a node to the
+// end of its chain inside the tile, k_tile_exits), whose first nodes are listed
+// for k_flip_segments, which flips every segment at once.
 template <bool FWD>
-__global__ void k_augment(Batch b, int32_t* excess, const uint64_t* labels, int32_t* cand_base,
-                          const int32_t* cand_root, const uint64_t* best, long long* g_net, McfCtr* ctr) {
+__global__ void k_augment(Batch b, int32_t* excess, const uint64_t* labels, const uint16_t* exits, int32_t* cand_base,
+                          const int32_t* cand_root, const uint64_t* best, long long* g_net, int32_t* segs,
+                          McfCtr* ctr) {
   if (!ctr->go_on) return;
   const int nc = ctr->ncand;
   const int32_t* cand = cand_cur(cand_base, ctr, b.n_total);
@@ -1242,7 +1251,18 @@ __global__ void k_augment(Batch b, int32_t* excess, const uint64_t* labels, int3
     atomicAdd(&ctr->naug, 1);
     const int pi = prob_of_node(b, t);
     const ProbDev& p = b.probs[pi];
-    flip_path<FWD>(p, labels + p.node_off, t - p.node_off);
+    const uint64_t* plab = labels + p.node_off;
+    const uint16_t* pexit = exits + p.node_off;
+    int64_t v = t - p.node_off;
+    int64_t i = v / p.C, j = v - (v / p.C) * p.C;
+    for (int64_t steps = 0; steps <= p.N; ++steps) {
+      segs[atomicAdd(&ctr->nseg, 1)] = (int32_t)(p.node_off + i * p.C + j);
+      const int ex = pexit[i * p.C + j];
+      i = (i / TS) * TS + ex / TS;
+      j = (j / TS) * TS + ex % TS;
+      const int d = label_dir(plab[i * p.C + j]);
+      if (d == kDirRoot || !step_parent(p, d, &i, &j)) break;  // the root, or the ground past the exit
+    }
     bool real_root = label_dir(labels[r]) == kDirRoot;
     if (FWD) {
       excess[t] += 1;
@@ -1252,6 +1272,40 @@ __global__ void k_augment(Batch b, int32_t* excess, const uint64_t* labels, int3
       excess[t] -= 1;
       if (real_root) excess[r] += 1;
       else atomicAdd((unsigned long long*)&g_net[pi], ~0ull);  // the ground node absorbed a unit
+    }
+  }
+}
+
+// Flip dk along every listed tile segment: from its first node along the parent
+// directions to the end of its chain inside the tile, including the edge from
+// that node to its parent (the next segment's first node, or the ground), but
+// not past a root.  The parent's label is loaded before the flow of the
+// current edge is updated, so that the two memory round trips of a step overlap.
+template <bool FWD>
+__global__ void k_flip_segments(Batch b, const uint64_t* labels, const uint16_t* exits, const int32_t* segs,
+                                const McfCtr* ctr) {
+  if (!ctr->go_on) return;
+  const int ns = ctr->nseg;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ns; q += gridDim.x * blockDim.x) {
+    const int32_t g = segs[q];
+    const ProbDev& p = b.probs[prob_of_node(b, g)];
+    const uint64_t* plab = labels + p.node_off;
+    const uint16_t* pexit = exits + p.node_off;
+    const int64_t P = p.m * p.n, v = g - p.node_off;
+    int64_t i = v / p.C, j = v - (v / p.C) * p.C;
+    uint64_t lab = plab[v];
+    for (int64_t steps = 0; steps <= TS * TS; ++steps) {
+      const int d = label_dir(lab);
+      if (d == kDirRoot) break;
+      // the end of the chain inside the tile: its own exit
+      const bool last = pexit[i * p.C + j] == (uint16_t)((i % TS) * TS + (j % TS));
+      int64_t e;
+      int plane, s;
+      dir_edge(p, i, j, d, &e, &plane, &s);
+      const bool inside = step_parent(p, d, &i, &j);
+      if (inside && !last) lab = plab[i * p.C + j];
+      p.flows[plane * P + e] += (int8_t)(FWD ? s : -s);
+      if (!inside || last) break;
     }
   }
 }
@@ -1486,7 +1540,7 @@ int64_t rc_cache_entries(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
 }
 
 int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
-  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8 + 2) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 +
+  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8 + 2 + 4) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 +
          rc_cache_entries(n_nodes, n_tiles, n_probs) * (kRcTileBytes + 4) + (kMaxSearchGrid + 64) * 4 +
          n_probs * (sizeof(ProbDev) + 4 + 8 + 8 + 16 + 12) + (int64_t)sizeof(McfCtr) + 4096;
 }
@@ -1506,7 +1560,7 @@ ww_status solver_alloc(SolverWs* sv, int64_t n_nodes, int64_t n_tiles, int64_t n
             cudaMalloc(&sv->touched, n_tiles * 4) == cudaSuccess && cudaMalloc(&sv->tlist, n_tiles * 4) == cudaSuccess &&
             cudaMalloc(&sv->rc_cache, rc_cache_entries(n_nodes, n_tiles, n_probs) * kRcTileBytes) == cudaSuccess &&
             cudaMalloc(&sv->rc_pass, rc_cache_entries(n_nodes, n_tiles, n_probs) * 4) == cudaSuccess &&
-            cudaMalloc(&sv->exits, n_nodes * 2) == cudaSuccess &&
+            cudaMalloc(&sv->exits, n_nodes * 2) == cudaSuccess && cudaMalloc(&sv->segs, n_nodes * 4) == cudaSuccess &&
             cudaMalloc(&sv->border, nb * 4) == cudaSuccess && cudaMalloc(&sv->probs, n_probs * sizeof(ProbDev)) == cudaSuccess &&
             cudaMalloc(&sv->prob_left, n_probs * 4) == cudaSuccess && cudaMalloc(&sv->g_net, n_probs * 8) == cudaSuccess &&
             cudaMalloc(&sv->tc, n_probs * 8) == cudaSuccess && cudaMalloc(&sv->ctr, sizeof(McfCtr)) == cudaSuccess &&
@@ -1545,6 +1599,7 @@ void solver_free(SolverWs* sv) {
   cudaFree(sv->rc_cache);
   cudaFree(sv->rc_pass);
   cudaFree(sv->exits);
+  cudaFree(sv->segs);
   cudaFree(sv->tile_prob);
   cudaFree(sv->border);
   cudaFree(sv->probs);
@@ -1842,8 +1897,9 @@ ww_status Session::enqueue_pass() {
   k_select<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->exits, sv->cand, sv->cand_root, sv->best,
                                           ctr);
   k_select_ground<FWD><<<ga, 256, 0, s>>>(b, sv->labels, sv->exits, pot, sv->best, ctr);
-  k_augment<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->cand, sv->cand_root, sv->best, sv->g_net,
-                                           ctr);
+  k_augment<FWD><<<grid_cand, 256, 0, s>>>(b, sv->excess, sv->labels, sv->exits, sv->cand, sv->cand_root, sv->best,
+                                           sv->g_net, sv->segs, ctr);
+  k_flip_segments<FWD><<<sm_count * 16, 256, 0, s>>>(b, sv->labels, sv->exits, sv->segs, ctr);
   k_augment_ground<FWD><<<ga, 256, 0, s>>>(b, sv->excess, sv->labels, sv->exits, pot, sv->best, sv->g_net, ctr);
   k_reset_best<<<grid_cand, 256, 0, s>>>(b, sv->cand_root, sv->best, sv->prob_left, (int)sv->p_cap, ctr);
   k_potentials<FWD><<<sm_count * 8, 256, 0, s>>>(b, sv->labels, pot, sv->touched, sv->tlist, ctr);
