@@ -789,11 +789,9 @@ __device__ __forceinline__ float f64_bits_to_f32(uint64_t d) {
   return __uint_as_float(sign | r);
 }
 
-// fp32(fp64(psi) + fp64(K) * 2pi) for a finite psi.
-__device__ __forceinline__ float unwrap_value(float psi, int32_t K) {
-  if (K == 0) return psi == 0.0f ? 0.0f : psi;  // psi + (+0): -0 becomes +0, the rest is exact
-  const double s = __dadd_rn(__longlong_as_double((long long)f32_to_f64_bits(psi)),
-                             __longlong_as_double((long long)k_two_pi_bits(K)));
+// fp32(fp64(psi) + t) for a finite psi, t = the bits of fp64(K) * 2pi (K != 0).
+__device__ __forceinline__ float unwrap_value(float psi, uint64_t t) {
+  const double s = __dadd_rn(__longlong_as_double((long long)f32_to_f64_bits(psi)), __longlong_as_double((long long)t));
   return f64_bits_to_f32((uint64_t)__double_as_longlong(s));
 }
 
@@ -878,14 +876,23 @@ __device__ __forceinline__ void integrate_row(const void* ifg, int is_complex, c
     int32_t base = carry_s + add + (v - s);
     int32_t Ks[kRowItems];
     float outs[kRowItems];
+    // the product K 2pi once per run of equal K (neighbours mostly share it)
+    int32_t lastK = 0;
+    uint64_t tK = 0;
 #pragma unroll
     for (int t = 0; t < kRowItems; ++t) {
       const int32_t K = base + local[t];
       Ks[t] = K;
-      if (val[t]) {
-        outs[t] = unwrap_value(psi[t], K);
-      } else {
+      if (!val[t]) {
         outs[t] = __int_as_float(0x7fc00000);
+      } else if (K == 0) {
+        outs[t] = psi[t] == 0.0f ? 0.0f : psi[t];  // psi + (+0): -0 becomes +0, the rest is exact
+      } else {
+        if (K != lastK) {
+          lastK = K;
+          tK = k_two_pi_bits(K);
+        }
+        outs[t] = unwrap_value(psi[t], tK);
       }
     }
     if (vec && j0 + kRowItems <= n) {
@@ -1252,12 +1259,32 @@ namespace {
 // the phase alone for validity.
 __global__ void k_phase(const float2* __restrict__ z, const float* __restrict__ coh, const uint8_t* __restrict__ mask,
                         int64_t P, float* __restrict__ psi) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = __ldg(z + k);
-    bool ok = isfinite(v.x) && isfinite(v.y);
-    if (coh) ok = ok && isfinite(__ldg(coh + k));
-    if (mask) ok = ok && __ldg(mask + k) != 0;
+  // grid-stride loop with the next pixel's loads issued before this pixel's CORDIC
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float2 v = make_float2(0.0f, 0.0f);
+  float cv = 0.0f;
+  uint8_t mv = 1;
+  if (k < P) {
+    v = __ldg(z + k);
+    if (coh) cv = __ldg(coh + k);
+    if (mask) mv = __ldg(mask + k);
+  }
+  for (; k < P; k += stride) {
+    const int64_t kn = k + stride;
+    float2 vn = make_float2(0.0f, 0.0f);
+    float cn = 0.0f;
+    uint8_t mn = 1;
+    if (kn < P) {
+      vn = __ldg(z + kn);
+      if (coh) cn = __ldg(coh + kn);
+      if (mask) mn = __ldg(mask + kn);
+    }
+    const bool ok = isfinite(v.x) && isfinite(v.y) && isfinite(cv) && mv != 0;
     psi[k] = ok ? cordic_phase(v.x, v.y) : __int_as_float(0x7fc00000);
+    v = vn;
+    cv = cn;
+    mv = mn;
   }
 }
 }  // namespace
