@@ -42,6 +42,9 @@ WORKLOADS = {
 # holding a finite label at the end of a tile visit, counted on the device):
 # cost planes 8, flow planes 2, potential 8, label write 8, worklist 2.
 SEARCH_BYTES_PER_SETTLED_VISIT = 28
+# end-to-end leg: each step's upload is split by rows over this many streams, so
+# that two copy engines move it (measured on B300: 2 and 3 equal, 4 slower)
+UPLOAD_STREAMS = 2
 # Bytes a tile visit moves for every node of the tile, reached or not: labels
 # read and written 16, potential 8, four cost planes 8, two flow planes 2.
 SEARCH_TILE_BYTES_PER_NODE = 34
@@ -334,8 +337,9 @@ def run_ours(args, rank, world, local):
     ms_host_loop = max_over_ranks(h0.elapsed_time(h1) / args.steps, world)
     # ---- end to end through the public call with host buffers ----
     # Every step copies its inputs from pinned host memory and reads its unwrapped
-    # phase back; the copies run on a second stream with two buffer sets, so step
-    # k+1's upload and step k-1's read-back overlap step k's unwrap.
+    # phase back; the copies run on streams of their own with two buffer sets
+    # (the upload split over UPLOAD_STREAMS streams, the read-back after it on the
+    # first), so step k+1's upload and step k-1's read-back overlap step k's unwrap.
     # both on streams of their own: work on the legacy default stream would wait
     # for every copy in flight on a blocking stream
     cs = torch.cuda.Stream()
@@ -343,14 +347,22 @@ def run_ours(args, rank, world, local):
     dev_in = [(ifg, coh, mask), (torch.empty_like(ifg), torch.empty_like(coh), torch.empty_like(mask))]
     dev_out = [(unw, cyc), (torch.empty_like(unw), torch.empty_like(cyc))]
     host_out = [host_unw, torch.empty_like(host_unw).pin_memory()]
-    in_ready = [torch.cuda.Event(), torch.cuda.Event()]
     read_done = [torch.cuda.Event(), torch.cuda.Event()]
 
+    # every upload split by rows over UPLOAD_STREAMS streams (several copy engines)
+    up = [cs] + [torch.cuda.Stream() for _ in range(UPLOAD_STREAMS - 1)]
+    up_ready = [[torch.cuda.Event() for _ in up], [torch.cuda.Event() for _ in up]]
+
     def upload(slot):
-        with torch.cuda.stream(cs):
-            for d, h in zip(dev_in[slot], (host_ifg, host_coh, host_mask)):
-                d.copy_(h, non_blocking=True)
-            in_ready[slot].record(cs)
+        for st_ in up[1:]:
+            st_.wait_stream(cs)
+        for part, st_ in enumerate(up):
+            with torch.cuda.stream(st_):
+                for d, h in zip(dev_in[slot], (host_ifg, host_coh, host_mask)):
+                    lo = d.shape[0] * part // len(up)
+                    hi = d.shape[0] * (part + 1) // len(up)
+                    d[lo:hi].copy_(h[lo:hi], non_blocking=True)
+            up_ready[slot][part].record(st_)
 
     barrier(world)
     torch.cuda.synchronize()
@@ -364,7 +376,8 @@ def run_ours(args, rank, world, local):
         sl = k % 2
         if k + 1 < args.steps:
             upload((k + 1) % 2)  # the other set's last user (step k-1) has returned
-        comp.wait_event(in_ready[sl])
+        for ev_ in up_ready[sl]:
+            comp.wait_event(ev_)
         if k >= 2:
             comp.wait_event(read_done[sl])  # step k-2's result has been read back
         a, c, mk = dev_in[sl]
@@ -375,7 +388,8 @@ def run_ours(args, rank, world, local):
             cs.wait_stream(comp)
             host_out[sl].copy_(dev_out[sl][0], non_blocking=True)
             read_done[sl].record(cs)
-    comp.wait_stream(cs)
+    for st_ in up:
+        comp.wait_stream(st_)
     t1.record(comp)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
