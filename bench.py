@@ -926,7 +926,10 @@ def launch_count(st, steps, prm):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    # default: 60 timed unwraps (about 0.7 s, so that several nvidia-smi clock
+    # samples land inside the timed region); 5 steps of the reference arm, whose
+    # step is a ~10 s oracle unwrap of a crop
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="earthquake")
@@ -948,6 +951,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--max-active", type=int, default=256)
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5 if args.impl == "reference" else 60
     if args.impl == "ours" and args.workload == "batched":
         return run_batched(args)
     if args.impl == "ours" and args.workload == "served":
