@@ -594,22 +594,26 @@ __global__ void k_steep_ties(const void* ifg, int is_complex, const float* coh, 
                              int64_t m, int64_t n, float steep_rad, const SteepCtr* ctr,
                              uint32_t* blocksum) {
   if (ctr->mode != 1) return;
-  const int64_t E = 2 * m * n;
-  int64_t base = (int64_t)blockIdx.x * kSteepChunk;
-  unsigned c = 0;
-  for (int64_t key = base + threadIdx.x; key < min(E, base + kSteepChunk); key += blockDim.x) {
-    uint32_t b;
-    if (steep_edge(ifg, is_complex, coh, mask, m, n, key, steep_rad, &b) && b == (uint32_t)ctr->threshold)
-      ++c;
-  }
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  const int64_t E = 2 * m * n, chunks = (E + kSteepChunk - 1) / kSteepChunk;
   __shared__ unsigned s[32];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned t = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s[k];
-    blocksum[blockIdx.x] = t;
+  // a fixed grid walks the chunks (the usual case, within the cap, returns at once)
+  for (int64_t chunk = blockIdx.x; chunk < chunks; chunk += gridDim.x) {
+    const int64_t base = chunk * kSteepChunk;
+    unsigned c = 0;
+    for (int64_t key = base + threadIdx.x; key < min(E, base + kSteepChunk); key += blockDim.x) {
+      uint32_t b;
+      if (steep_edge(ifg, is_complex, coh, mask, m, n, key, steep_rad, &b) && b == (uint32_t)ctr->threshold)
+        ++c;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned t = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s[k];
+      blocksum[chunk] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -648,9 +652,11 @@ __global__ void k_steep_zero(const void* ifg, int is_complex, const float* coh, 
   if (mode == 0 && ctr->candidates <= list_cap) return;  // the candidate list covered it
   const uint32_t thr = (uint32_t)ctr->threshold;
   const unsigned long long take = ctr->take_at_thr;
-  int64_t base = (int64_t)blockIdx.x * kSteepChunk;
   __shared__ unsigned warp_ties[32];
-  unsigned running = mode == 1 ? blocksum[blockIdx.x] : 0;
+  const int64_t chunks = (E + kSteepChunk - 1) / kSteepChunk;
+  for (int64_t chunk = blockIdx.x; chunk < chunks; chunk += gridDim.x) {
+  const int64_t base = chunk * kSteepChunk;
+  unsigned running = mode == 1 ? blocksum[chunk] : 0;
   for (int64_t off = 0; off < kSteepChunk; off += blockDim.x) {
     int64_t key = base + off + threadIdx.x;
     uint32_t b = 0;
@@ -681,6 +687,7 @@ __global__ void k_steep_zero(const void* ifg, int is_complex, const float* coh, 
       costs[(2 * plane) * P + k] = 0;
       costs[(2 * plane + 1) * P + k] = 0;
     }
+  }
   }
 }
 
@@ -1327,9 +1334,10 @@ ww_status launch_costs(const void* ifg, int is_complex, const float* coh, const 
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->hist, 1);
   k_steep_find<<<1, kFindThreads, 0, s>>>(ctr, ws->hist, 1);
   int64_t nb = (E + kSteepChunk - 1) / kSteepChunk;
-  k_steep_ties<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum);
+  const unsigned nb_grid = (unsigned)std::min<int64_t>(nb, 148 * 16);
+  k_steep_ties<<<nb_grid, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum);
   k_steep_scan<<<1, kFindThreads, 0, s>>>(ctr, ws->blocksum, nb);
-  k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum,
+  k_steep_zero<<<nb_grid, 256, 0, s>>>(ifg, is_complex, coh, mask, m, n, p->steep_rad, ctr, ws->blocksum,
                                             costs, list_cap);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
@@ -1559,9 +1567,10 @@ extern "C" ww_status ww_costs_noalloc(const void* ifg, int32_t is_complex, const
   k_steep_hist<<<hist_blocks, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, hist, 1);
   k_steep_find<<<1, kFindThreads, 0, s>>>(ctr, hist, 1);
   const int64_t nb = (2 * m * n + kSteepChunk - 1) / kSteepChunk;
-  k_steep_ties<<<(unsigned)nb, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum);
+  const unsigned nb_grid = (unsigned)std::min<int64_t>(nb, 148 * 16);
+  k_steep_ties<<<nb_grid, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum);
   k_steep_scan<<<1, kFindThreads, 0, s>>>(ctr, blocksum, nb);
-  k_steep_zero<<<(unsigned)nb, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum, costs, 0ull);
+  k_steep_zero<<<nb_grid, 256, 0, s>>>(ifg, c, coh, mask, m, n, p->steep_rad, ctr, blocksum, costs, 0ull);
   WW_CUDA_TRY(cudaGetLastError());
   return WW_OK;
 }
