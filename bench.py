@@ -727,24 +727,28 @@ def run_batched(args, summary=False):
     items_identical = sum(1 for o, k1 in zip(out, plain_K) if bool(torch.equal(o[1], k1)))
     del plain_K
     # the served form on the same items, every request queued at once, with the
-    # same schedule: its wall time against the batched form's time per batch
+    # same schedule: its wall time (from the first submit to the last result; the
+    # better of two runs, both listed) against the batched form's time per batch
     del batch, ws, out
     torch.cuda.empty_cache()
-    srv = ww.Server(hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_request_pixels=biggest,
-                    max_active=args.max_active, params=prm)
-    t = time.perf_counter()
-    tickets = [srv.submit(*r) for r in reqs]
-    served = []
-    for k in tickets:
-        o = srv.wait(k)
-        served.append((o[2], o[3]))
-    span = time.perf_counter() - t
-    sst = srv.stats()
-    srv.close()
-    mism = sum(1 for (tc, sc), c in zip(served, costs) if tc != c or sc != 0)
+    spans, mism, sst = [], 0, None
+    for _ in range(2):
+        srv = ww.Server(hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_request_pixels=biggest,
+                        max_active=args.max_active, params=prm)
+        t = time.perf_counter()
+        tickets = [srv.submit(*r) for r in reqs]
+        served = []
+        for k in tickets:
+            o = srv.wait(k)
+            served.append((o[2], o[3]))
+        spans.append(time.perf_counter() - t)
+        sst = srv.stats()
+        srv.close()
+        mism += sum(1 for (tc, sc), c in zip(served, costs) if tc != c or sc != 0)
+    span = min(spans)
     same_items = {"offered": f"all {len(reqs)} items at t = 0", "max_active": args.max_active,
-                  "ms": span * 1e3, "Mpixel_per_s": px / span / 1e6, "vs_batched": ms / (span * 1e3),
-                  "passes": sst["passes"], "peak_active": sst["peak_active"],
+                  "ms": span * 1e3, "ms_runs": [x * 1e3 for x in spans], "Mpixel_per_s": px / span / 1e6,
+                  "vs_batched": ms / (span * 1e3), "passes": sst["passes"], "peak_active": sst["peak_active"],
                   "total_cost_mismatches_vs_batched": mism}
     assert mism == 0, mism
     if summary:
