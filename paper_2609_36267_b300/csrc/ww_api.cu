@@ -260,7 +260,8 @@ void ww_lut_free(ww_lut* lut) {
 int64_t ww_workspace_bytes(int64_t m, int64_t n) {
   if (!grid_ok(m, n)) return -1;
   int64_t P = m * n, N = (m - 1) * (n - 1);
-  int64_t grid = N /*residues*/ + 4 * P * 2 /*costs*/ + 2 * P /*flows*/ + (N + 1) * 8 /*potentials*/ + 64;
+  // the potentials are the solver's own array (counted in solver_bytes)
+  int64_t grid = N /*residues*/ + 4 * P * 2 /*costs*/ + 2 * P /*flows*/ + 64;
   int64_t steep = 65536 * 4 + 64 + ((2 * P + 1023) / 1024) * 4 + ww::steep_list_capacity(P, 30000) * 4;
   return grid + steep + 4 * P /*phase*/ + ww::solver_bytes(N, ww::tiles_for(m, n), 1);
 }
@@ -278,7 +279,6 @@ ww_status ww_workspace_create(int64_t max_rows, int64_t max_cols, ww_workspace**
   ws->steep_list_cap = ww::steep_list_capacity(P, 30000);  // the default 3% cap
   bool ok = cudaMalloc(&ws->residues, N) == cudaSuccess && cudaMalloc(&ws->ground, 64) == cudaSuccess &&
             cudaMalloc(&ws->costs, 4 * P * 2) == cudaSuccess && cudaMalloc(&ws->flows, 2 * P) == cudaSuccess &&
-            cudaMalloc(&ws->potentials, (N + 1) * 8) == cudaSuccess &&
             cudaMalloc(&ws->total_cost, 64) == cudaSuccess && cudaMalloc(&ws->dev_status, 64) == cudaSuccess &&
             cudaMalloc(&ws->hist, 65536 * 4) == cudaSuccess && cudaMalloc(&ws->steep_ctr, 64) == cudaSuccess &&
             cudaMalloc(&ws->blocksum, ws->blocksum_len * 4) == cudaSuccess &&
@@ -291,6 +291,8 @@ ww_status ww_workspace_create(int64_t max_rows, int64_t max_cols, ww_workspace**
     ww_workspace_free(ws);
     return st;
   }
+  // the unwrap's potentials (N + 1, ground last) live in the solver's array
+  ws->potentials = ws->sv.pot;
   *out = ws;
   return WW_OK;
 }
@@ -301,7 +303,6 @@ void ww_workspace_free(ww_workspace* ws) {
   cudaFree(ws->ground);
   cudaFree(ws->costs);
   cudaFree(ws->flows);
-  cudaFree(ws->potentials);
   cudaFree(ws->total_cost);
   cudaFree(ws->dev_status);
   cudaFree(ws->hist);

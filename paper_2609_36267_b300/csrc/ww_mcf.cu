@@ -1540,7 +1540,7 @@ int64_t rc_cache_entries(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
 }
 
 int64_t solver_bytes(int64_t n_nodes, int64_t n_tiles, int64_t n_probs) {
-  return n_nodes * (4 + 8 + 8 + 8 + 4 + 8 + 2 + 4) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 +
+  return n_nodes * (4 + 8 + 8 + 8 + 4 + 2 + 4) + (n_nodes + 1) * 8 + n_tiles * 4 * 8 +
          rc_cache_entries(n_nodes, n_tiles, n_probs) * (kRcTileBytes + 4) + (kMaxSearchGrid + 64) * 4 +
          n_probs * (sizeof(ProbDev) + 4 + 8 + 8 + 16 + 12) + (int64_t)sizeof(McfCtr) + 4096;
 }
