@@ -101,29 +101,10 @@ __device__ __forceinline__ float edge_d(float a, float b) {
   return __fsub_rn(dp, __fmul_rn(kTwoPiF, (float)wrap_count(dp)));
 }
 
-// Slope estimate from the row partial sums of the fixed-point gradients: the
-// vertical sum over the window's rows, then S / (cnt 2^22) rounded once.
-// S / (cnt 2^22) rounded once: the fixed-point window sum of the gradients as a slope
+// Slope estimate from the window sum S of the fixed-point (2^22) gradients of
+// its cnt valid edges: fp32(S) / (cnt 2^22) with the divisor exact and the
+// quotient correctly rounded (fp32(S) itself rounds once |S| exceeds 2^24).
 __device__ __forceinline__ float slope_of_sum(int32_t S, int cnt) {
-  return __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
-}
-
-template <int W>
-__device__ __forceinline__ float window_mean(const int32_t (*rs)[CTX], const uint8_t (*ns)[CTX], int R, int c, int w) {
-  int32_t S = 0;
-  int cnt = 0;
-  if constexpr (W >= 0) {
-#pragma unroll
-    for (int d = -W; d <= W; ++d) {
-      S += rs[R + d][c];
-      cnt += ns[R + d][c];
-    }
-  } else {
-    for (int d = -w; d <= w; ++d) {
-      S += rs[R + d][c];
-      cnt += ns[R + d][c];
-    }
-  }
   return __fdiv_rn(__int2float_rn(S), __fmul_rn((float)cnt, kQScale));
 }
 
