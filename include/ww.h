@@ -232,17 +232,18 @@ ww_status ww_solve_mcf_resume(const int8_t* residues, const int32_t* ground, con
                               int8_t* flows, int64_t* potentials, int64_t* total_cost,
                               int32_t* dev_status, ww_stream stream);
 
-/* Solver statistics of the last ww_solve_mcf on this workspace (host struct). */
+/* Solver statistics of the last solve (ww_solve_mcf, ww_solve_mcf_resume or
+ * ww_unwrap) on this workspace (host struct). */
 typedef struct ww_solve_stats {
   int64_t passes, augmentations, search_iterations, tile_visits;
   int64_t residues, ground_net;
-  double ms_search;      /* host wall time in the search loops */
-  double ms_other;       /* host wall time in select/augment/update */
-  double ms_search_gpu;  /* device time of the search kernel launches (CUDA events) */
-  int64_t local_rounds;  /* directional-scan rounds summed over tile visits */
+  double ms_search;      /* host wall time of the pass loop (searches, selection, augmentation, potentials) */
+  double ms_other;       /* host wall time of the rest of the solve (session setup, finalisation) */
+  double ms_search_gpu;  /* device time of the search launches (CUDA events; host-driven pass loop only, 0 with graph_loop) */
+  int64_t local_rounds;  /* local fixed-point rounds (four concurrent line sweeps each) summed over tile visits */
   int64_t visit_cycles;  /* SM clock cycles summed over tile visits */
   int64_t load_cycles;   /* of which: loading labels and computing reduced arc costs */
-  int64_t relax_cycles;  /* of which: the local fixed point (directional scans) */
+  int64_t relax_cycles;  /* of which: the local fixed point (line sweeps) */
   int64_t settled_visits; /* nodes reached (finite label) at the end of a tile visit, summed over visits */
   int64_t narrow_visits;  /* tile visits relaxed in 32-bit keys (label spans small enough) */
   int64_t narrow_redone;  /* of which redone in 64-bit keys (a candidate left the 32-bit range) */

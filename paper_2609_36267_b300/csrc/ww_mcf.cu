@@ -2137,7 +2137,8 @@ ww_status solve_problems(const ProbHost* ph, int nprob, SolverWs* sv, const ww_p
     e = S.pass(&st);
     if (e != WW_OK) return e;
   }
-  st.ms_other = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  const auto t1 = std::chrono::steady_clock::now();
+  st.ms_search = std::chrono::duration<double, std::milli>(t1 - t0).count();
   std::vector<int32_t> sts;
   e = S.finalize(all, &sts);
   if (e != WW_OK) return e;
@@ -2145,6 +2146,7 @@ ww_status solve_problems(const ProbHost* ph, int nprob, SolverWs* sv, const ww_p
   WW_CUDA_TRY(cudaMemcpyAsync(&g0, sv->g_net + all[0], 8, cudaMemcpyDeviceToHost, s));
   WW_CUDA_TRY(cudaStreamSynchronize(s));
   st.ground_net = g0;
+  st.ms_other = std::chrono::duration<double, std::milli>(t0 - t_setup + (std::chrono::steady_clock::now() - t1)).count();
   if (stats) *stats = st;
   for (int32_t x : sts)
     if (x != WW_OK) return x;
