@@ -388,6 +388,10 @@ int64_t ww_batch_bytes(int64_t max_items, int64_t max_pixels, int64_t max_item_p
 /* Synchronises the stream; returns the first non-OK item status, else WW_OK. */
 ww_status ww_unwrap_batch(ww_batch_item* items, int64_t count, const ww_params* params, ww_batch* b,
                           ww_stream stream);
+/* Solver statistics of the last ww_unwrap_batch (all items together).  With
+ * params->graph_loop (and WW_TRACE unset) the whole batch is one graph launch:
+ * the three timing fields are then 0 and residues is 0 (only the device
+ * counters are read back after the launch). */
 ww_status ww_batch_stats(const ww_batch* b, ww_solve_stats* out);
 
 /* Autotuner of the search schedule (no counterpart in the paper, whose CPU
